@@ -1,0 +1,170 @@
+/*
+ * pencil.h -- C ABI of libpencilgpu, the GB300 (sm_103a) implementation of
+ * the two loop nests PENCIL-style DSL compilers lower image-processing and CFD
+ * code to (PENCIL, arXiv:1302.5586, Sec. 1 and Sec. 2): a 2-D convolution with
+ * clamp-to-edge borders and an iterated 5-point Jacobi stencil with an FP64
+ * residual norm.
+ *
+ * Calling conventions (the paper's coding rules, Sec. 2.2.1):
+ *   - Array arguments follow the C99 VLA rule: each array is a separate,
+ *     non-aliasing region ("restrict"); the library checks the byte ranges of
+ *     the arrays it writes against those it reads and returns
+ *     PENCIL_ERR_ALIAS on overlap.  Under C99 the prototypes below spell the
+ *     VLA form; C++ and CUDA callers see the ABI-identical pointer form.
+ *   - Images are dense row-major [h][w] (pitch = w elements); multi-channel
+ *     images are planar [c][h][w]; filters are row-major [kh][kw] FP32.
+ *   - Plain calls (no suffix) are synchronous and keep the sequential meaning
+ *     of the loop nest (Sec. 2): they accept host or device memory for every
+ *     array and return when the result is in place.
+ *   - _ex calls are stream-ordered: every array must be device memory
+ *     (PENCIL_ERR_PTR otherwise), the work is queued on `stream` (a
+ *     cudaStream_t passed as void*, NULL = the legacy default stream) and the
+ *     call returns without waiting.
+ *   - Ownership: the caller owns every array; the library never frees them.
+ *     Scratch for plain calls comes from a library pool released by
+ *     pencil_shutdown(); _ex calls take caller-provided workspace.
+ *   - Errors: every call returns 0 (PENCIL_OK) or a negative pencil_status.
+ *     Nothing aborts or traps.  After PENCIL_ERR_CUDA the CUDA error code is
+ *     kept per thread and readable with pencil_last_cuda_error().
+ */
+#ifndef PENCIL_H
+#define PENCIL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+/* PENCIL_ARR2(T, name, n, m): a [n][m] array parameter.  C99 sees the
+ * PENCIL form `T name[restrict const static n][m]`; C++/CUDA see `T *name`,
+ * which has the same ABI. */
+#ifdef __cplusplus
+extern "C" {
+#define PENCIL_ARR2(T, name, n, m) T *name
+#else
+#define PENCIL_ARR2(T, name, n, m) T name[restrict const static n][m]
+#endif
+
+typedef enum pencil_status {
+    PENCIL_OK = 0,
+    PENCIL_ERR_ARG = -1,         /* a size is <= 0, too large, or a flag is unknown */
+    PENCIL_ERR_NULL = -2,        /* a required pointer is NULL */
+    PENCIL_ERR_ALIAS = -3,       /* an output overlaps an input (restrict rule, Sec. 2.2.1) */
+    PENCIL_ERR_PTR = -4,         /* host memory where device memory is required */
+    PENCIL_ERR_NOMEM = -5,       /* workspace too small or device allocation failed */
+    PENCIL_ERR_CUDA = -6,        /* a CUDA call failed; see pencil_last_cuda_error() */
+    PENCIL_ERR_TIMEOUT = -7,     /* a bounded wait expired */
+    PENCIL_ERR_UNSUPPORTED = -8  /* a valid request this build does not implement */
+} pencil_status;
+
+/* Storage types of images (filters are always FP32; arithmetic is FP32). */
+enum { PENCIL_F32 = 0, PENCIL_F16 = 1 };
+
+/* pencil_conv2d_ex flag: run the generic (any-size) kernel even where a
+ * specialised one exists.  The result is the same bits; the flag exists so
+ * that the fixed per-pixel order can be checked across kernels. */
+#define PENCIL_CONV_GENERIC 1
+
+/* Largest filter side the specialised kernels handle; larger (or non-square)
+ * filters take the generic kernel, which has no size limit. */
+#define PENCIL_MAX_SPECIALISED_K 15
+
+/* ------------------------------------------------------------------ conv2d
+ * out[i][j] = sum_{a<kh} sum_{b<kw} k[a][b] * in[clamp(i+a-kh/2)][clamp(j+b-kw/2)]
+ * with clamp(x) = min(max(x, 0), side-1) applied per axis: a correlation (no
+ * filter flip) anchored at (kh/2, kw/2), borders replicated ("clamp to
+ * edge").  The pixel loops are independent (Sec. 2.2.3, `independent`); the
+ * per-pixel sum is a map over output pixels (Sec. 3.2, vector construction).
+ * Each output is accumulated in FP32 in one fixed order -- per filter row a
+ * chain of fused multiply-adds over b, then the row sums added in order of a
+ * -- that does not depend on tiling, batching or stream, so every kernel of
+ * this library returns the same bits for the same pixel (Sec. 3.1 on
+ * floating-point order and reproducibility).
+ */
+
+/* Synchronous, one FP32 channel.  in: h*w, k: kh*kw, out: h*w; each may be
+ * host or device memory.  Errors: ARG (h, w, kh, kw <= 0), NULL, ALIAS (out
+ * overlaps in or k), NOMEM, CUDA. */
+int pencil_conv2d(int h, int w, PENCIL_ARR2(const float, in, h, w), int kh, int kw,
+                  PENCIL_ARR2(const float, k, kh, kw), PENCIL_ARR2(float, out, h, w));
+
+/* Stream-ordered, c planar channels, storage dtype PENCIL_F32 or PENCIL_F16
+ * (binary16 images; FP32 accumulation; binary16 results rounded to nearest
+ * even).  in, out: c*h*w elements of dtype, device memory; k: kh*kw FP32,
+ * device memory.  flags: 0 or PENCIL_CONV_GENERIC.  Errors: ARG, NULL, ALIAS,
+ * PTR, CUDA. */
+int pencil_conv2d_ex(int c, int h, int w, const void *in, int kh, int kw, const float *k,
+                     void *out, int dtype, int flags, void *stream);
+
+/* Separable filter: the 2-D weights are gy[a] * gx[b] (kx taps along rows,
+ * ky taps along columns).  Computed as a row pass then a column pass fused
+ * through shared memory (no intermediate in HBM); per pixel the row pass is a
+ * chain over b and the column pass a chain over a.  Sides
+ * 1..PENCIL_MAX_SPECIALISED_K (odd or even).
+ * Synchronous, one FP32 channel; in, gx, gy, out may be host or device memory.
+ * Errors: ARG, NULL, ALIAS, UNSUPPORTED (a side above the maximum), NOMEM, CUDA. */
+int pencil_conv2d_sep(int h, int w, PENCIL_ARR2(const float, in, h, w), int kx, const float *gx,
+                      int ky, const float *gy, PENCIL_ARR2(float, out, h, w));
+
+/* Stream-ordered separable filter over c planar channels of dtype
+ * PENCIL_F32 or PENCIL_F16; every array is device memory.
+ * Errors: ARG, NULL, ALIAS, PTR, UNSUPPORTED, CUDA. */
+int pencil_conv2d_sep_ex(int c, int h, int w, const void *in, int kx, const float *gx, int ky,
+                         const float *gy, void *out, int dtype, void *stream);
+
+/* ------------------------------------------------------------------ jacobi
+ * One sweep: v[i][j] = 0.25f * ((u[i-1][j] + u[i+1][j]) + (u[i][j-1] + u[i][j+1]))
+ * on the interior 1 <= i <= h-2, 1 <= j <= w-2, in FP32 in exactly that order;
+ * the boundary ring never changes; u and v are two buffers (a Jacobi step).
+ * The sweeps form the sequential outer loop of `untilconverged` (Sec. 3.2);
+ * the points of one sweep are independent (Sec. 2.2.3).
+ *
+ * Residual of an iterate: sqrt(sum over the interior of r^2),
+ * r = 4u[i][j] - ((u[i-1][j] + u[i+1][j]) + (u[i][j-1] + u[i][j+1])), r in FP32,
+ * r^2 formed exactly and summed per thread with compensation, then across
+ * threads and blocks in FP64 in a fixed order (the `reduction` directive,
+ * Sec. 2.2.3).  Grids with h < 3 or w < 3 have no interior: sweeps change
+ * nothing and residuals are 0.
+ */
+
+/* Synchronous: iters sweeps of u (h*w FP32, host or device) in place.
+ * Errors: ARG (h, w <= 0, iters < 0), NULL, NOMEM, CUDA. */
+int pencil_jacobi2d(int h, int w, PENCIL_ARR2(float, u, h, w), int iters);
+
+/* Bytes of workspace pencil_jacobi2d_ex needs for an h x w grid. */
+size_t pencil_jacobi2d_workspace_size(int h, int w);
+
+/* Stream-ordered: iters sweeps of u (device memory) in place.  When
+ * check_every > 0, the residual of the iterate after sweep m*check_every is
+ * written to res_out[m-1] (device memory, iters/check_every doubles).
+ * workspace: device memory of at least pencil_jacobi2d_workspace_size(h, w)
+ * bytes, 256-byte aligned, not overlapping u or res_out.  temporal_t selects
+ * how many sweeps one kernel pass performs per HBM round trip (0 = library
+ * choice, 1 = one sweep per pass); the iterate is the same bits for every
+ * choice.  Errors: ARG, NULL, ALIAS, PTR, NOMEM (workspace too small), CUDA. */
+int pencil_jacobi2d_ex(int h, int w, float *u, int iters, int check_every, double *res_out,
+                       void *workspace, size_t ws_bytes, int temporal_t, void *stream);
+
+/* Stream-ordered residual of one grid (device memory) into *res_out (device).
+ * workspace as for pencil_jacobi2d_ex.  Errors: ARG, NULL, PTR, NOMEM, CUDA. */
+int pencil_residual2d(int h, int w, const float *u, double *res_out, void *workspace,
+                      size_t ws_bytes, void *stream);
+
+/* ----------------------------------------------------------------- utility */
+
+/* Human-readable text of a pencil_status (static storage). */
+const char *pencil_strerror(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int pencil_version(void);
+
+/* The cudaError_t of the calling thread's most recent PENCIL_ERR_CUDA, or 0. */
+int pencil_last_cuda_error(void);
+
+/* Release the library's device pool (plain calls' scratch). Safe to call
+ * more than once; later plain calls allocate again. */
+void pencil_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PENCIL_H */

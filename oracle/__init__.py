@@ -68,6 +68,8 @@ def lib():
     L.oracle_conv2d_sep.restype = i32
     L.oracle_conv2d_points.argtypes = [i64, i64, i64, vp, i32, i32, i32, vp, i64, vp, dp, dp]
     L.oracle_conv2d_points.restype = i32
+    L.oracle_conv2d_sep_points.argtypes = [i64, i64, i64, vp, i32, i32, vp, i32, vp, i64, vp, dp, dp]
+    L.oracle_conv2d_sep_points.restype = i32
     L.oracle_residual2d_f64.argtypes = [i64, i64, vp]
     L.oracle_residual2d_f64.restype = ctypes.c_double
     L.oracle_residual2d_f32.argtypes = [i64, i64, vp]
@@ -167,6 +169,22 @@ def conv2d_points(img: np.ndarray, k: np.ndarray, pts: np.ndarray):
                                     _ptr(out), _ptr(bound))
     if rc != 0:
         raise ValueError("oracle_conv2d_points rejected its arguments")
+    return out, bound
+
+
+def conv2d_sep_points(img: np.ndarray, gx: np.ndarray, gy: np.ndarray, pts: np.ndarray):
+    """The separable definition evaluated at sampled (ch, i, j) points: (out, bound)."""
+    x, dt = _image(img)
+    gx = np.ascontiguousarray(gx, dtype=np.float32).ravel()
+    gy = np.ascontiguousarray(gy, dtype=np.float32).ravel()
+    p = np.ascontiguousarray(pts, dtype=np.int64).reshape(-1, 3)
+    c, h, w = x.shape
+    out = np.empty(p.shape[0], dtype=np.float64)
+    bound = np.empty(p.shape[0], dtype=np.float64)
+    rc = lib().oracle_conv2d_sep_points(c, h, w, _ptr(x), dt, gx.size, _ptr(gx), gy.size, _ptr(gy),
+                                        p.shape[0], _ptr(p), _ptr(out), _ptr(bound))
+    if rc != 0:
+        raise ValueError("oracle_conv2d_sep_points rejected its arguments")
     return out, bound
 
 

@@ -223,6 +223,27 @@ int oracle_conv2d_points(int64_t nc, int64_t h, int64_t w, const void *in, int d
     return bad ? -1 : 0;
 }
 
+/* The separable definition (weights gy[a] * gx[b] in FP64) at sampled points. */
+int oracle_conv2d_sep_points(int64_t nc, int64_t h, int64_t w, const void *in, int dtype,
+                             int kx, const float *gx, int ky, const float *gy, int64_t npts,
+                             const int64_t *pts, double *out, double *bound)
+{
+    if (nc <= 0 || h <= 0 || w <= 0 || kx <= 0 || ky <= 0 || npts < 0) return -1;
+    double *kd = (double *)malloc(sizeof(double) * (size_t)kx * (size_t)ky);
+    if (!kd) return -1;
+    for (int a = 0; a < ky; ++a)
+        for (int b = 0; b < kx; ++b) kd[a * kx + b] = (double)gy[a] * (double)gx[b];
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (int64_t p = 0; p < npts; ++p) {
+        const int64_t ch = pts[3 * p], i = pts[3 * p + 1], j = pts[3 * p + 2];
+        if (ch < 0 || ch >= nc || i < 0 || i >= h || j < 0 || j >= w) { bad = 1; continue; }
+        conv_pixel(h, w, in, dtype, ch * h * w, ky, kx, kd, i, j, out + p, bound ? bound + p : NULL);
+    }
+    free(kd);
+    return bad ? -1 : 0;
+}
+
 /* ------------------------------------------------------- Jacobi + residual */
 
 /* sqrt(sum over interior points of (4u - up - down - left - right)^2), summed

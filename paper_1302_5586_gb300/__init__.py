@@ -1,0 +1,32 @@
+"""GB300-native (sm_103a) clamp-to-edge conv2d and 5-point Jacobi stencil.
+
+The computation is the data-parallel loop nest that PENCIL (arXiv:1302.5586)
+lets DSL compilers hand to an optimiser: a 2-D convolution over independent
+pixel loops (Sec. 2.2.3) and the sweeps of an `untilconverged` loop with an
+FP64 reduction for its residual (Sec. 3.2).  The work runs in hand-written
+CUDA kernels behind the C ABI in include/pencil.h; this package is the thin
+Python binding of that ABI plus the batching and serving layers built on it.
+"""
+from ._binding import (  # noqa: F401
+    HEADER,
+    LIB_PATH,
+    PENCIL_CONV_GENERIC,
+    PENCIL_F16,
+    PENCIL_F32,
+    PENCIL_MAX_SPECIALISED_K,
+    PencilError,
+    declared_symbols,
+    lib,
+    pencil_conv2d,
+    pencil_conv2d_ex,
+    pencil_conv2d_sep,
+    pencil_conv2d_sep_ex,
+    pencil_jacobi2d,
+    pencil_jacobi2d_ex,
+    pencil_jacobi2d_workspace_size,
+    pencil_last_cuda_error,
+    pencil_residual2d,
+    pencil_shutdown,
+    pencil_strerror,
+    pencil_version,
+)

@@ -1,0 +1,162 @@
+"""ctypes binding of libpencilgpu: the C ABI's functions under the same names.
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  Array arguments may be torch tensors (device or
+host), numpy arrays (host) or raw integer addresses; `stream` may be a
+torch.cuda.Stream, a raw cudaStream_t integer, or None for torch's current
+stream.  A non-zero status raises PencilError.  If the shared library has not
+been built this module raises on first use; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpencilgpu.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "pencil.h")
+
+PENCIL_F32 = 0
+PENCIL_F16 = 1
+PENCIL_CONV_GENERIC = 1
+PENCIL_MAX_SPECIALISED_K = 15
+
+STATUS = {
+    0: "PENCIL_OK", -1: "PENCIL_ERR_ARG", -2: "PENCIL_ERR_NULL", -3: "PENCIL_ERR_ALIAS",
+    -4: "PENCIL_ERR_PTR", -5: "PENCIL_ERR_NOMEM", -6: "PENCIL_ERR_CUDA",
+    -7: "PENCIL_ERR_TIMEOUT", -8: "PENCIL_ERR_UNSUPPORTED",
+}
+
+
+class PencilError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        msg = f"{what}: {self.name}"
+        if status == -6:
+            msg += f" (cudaError {lib().pencil_last_cuda_error()})"
+        super().__init__(msg)
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    i, vp, sz, d = ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p
+    sig = {
+        "pencil_conv2d": (i, [i, i, vp, i, i, vp, vp]),
+        "pencil_conv2d_ex": (i, [i, i, i, vp, i, i, vp, vp, i, i, vp]),
+        "pencil_conv2d_sep": (i, [i, i, vp, i, vp, i, vp, vp]),
+        "pencil_conv2d_sep_ex": (i, [i, i, i, vp, i, vp, i, vp, vp, i, vp]),
+        "pencil_jacobi2d": (i, [i, i, vp, i]),
+        "pencil_jacobi2d_workspace_size": (sz, [i, i]),
+        "pencil_jacobi2d_ex": (i, [i, i, vp, i, i, d, vp, sz, i, vp]),
+        "pencil_residual2d": (i, [i, i, vp, d, vp, sz, vp]),
+        "pencil_strerror": (ctypes.c_char_p, [i]),
+        "pencil_version": (i, []),
+        "pencil_last_cuda_error": (i, []),
+        "pencil_shutdown": (None, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def declared_symbols() -> list[str]:
+    """Names of the functions include/pencil.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pencil_[a-z0-9_]+)\s*\(", text)))
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)!r}")
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise PencilError(st, what)
+
+
+def pencil_conv2d(h, w, in_, kh, kw, k, out):
+    _check(lib().pencil_conv2d(h, w, _ptr(in_), kh, kw, _ptr(k), _ptr(out)), "pencil_conv2d")
+
+
+def pencil_conv2d_ex(c, h, w, in_, kh, kw, k, out, dtype, flags=0, stream=None):
+    _check(lib().pencil_conv2d_ex(c, h, w, _ptr(in_), kh, kw, _ptr(k), _ptr(out), dtype, flags,
+                                  _stream(stream)), "pencil_conv2d_ex")
+
+
+def pencil_conv2d_sep(h, w, in_, kx, gx, ky, gy, out):
+    _check(lib().pencil_conv2d_sep(h, w, _ptr(in_), kx, _ptr(gx), ky, _ptr(gy), _ptr(out)),
+           "pencil_conv2d_sep")
+
+
+def pencil_conv2d_sep_ex(c, h, w, in_, kx, gx, ky, gy, out, dtype, stream=None):
+    _check(lib().pencil_conv2d_sep_ex(c, h, w, _ptr(in_), kx, _ptr(gx), ky, _ptr(gy), _ptr(out), dtype,
+                                      _stream(stream)), "pencil_conv2d_sep_ex")
+
+
+def pencil_jacobi2d(h, w, u, iters):
+    _check(lib().pencil_jacobi2d(h, w, _ptr(u), iters), "pencil_jacobi2d")
+
+
+def pencil_jacobi2d_workspace_size(h, w) -> int:
+    return int(lib().pencil_jacobi2d_workspace_size(h, w))
+
+
+def pencil_jacobi2d_ex(h, w, u, iters, check_every, res_out, workspace, ws_bytes, temporal_t=0,
+                       stream=None):
+    _check(lib().pencil_jacobi2d_ex(h, w, _ptr(u), iters, check_every, _ptr(res_out), _ptr(workspace),
+                                    ws_bytes, temporal_t, _stream(stream)), "pencil_jacobi2d_ex")
+
+
+def pencil_residual2d(h, w, u, res_out, workspace, ws_bytes, stream=None):
+    _check(lib().pencil_residual2d(h, w, _ptr(u), _ptr(res_out), _ptr(workspace), ws_bytes,
+                                   _stream(stream)), "pencil_residual2d")
+
+
+def pencil_strerror(status: int) -> str:
+    return lib().pencil_strerror(status).decode()
+
+
+def pencil_version() -> int:
+    return lib().pencil_version()
+
+
+def pencil_last_cuda_error() -> int:
+    return lib().pencil_last_cuda_error()
+
+
+def pencil_shutdown() -> None:
+    lib().pencil_shutdown()

@@ -1,0 +1,310 @@
+// api.cu -- the C ABI of libpencilgpu: argument checks, the restrict rule,
+// memory-kind checks, the scratch pool of the plain calls, and dispatch.
+#include <mutex>
+#include <string.h>
+
+#include "internal.cuh"
+
+namespace pencil {
+
+static thread_local int g_last_cuda = 0;
+
+int cuda_fail(cudaError_t e) {
+    g_last_cuda = (int)e;
+    return PENCIL_ERR_CUDA;
+}
+
+namespace {
+
+// Where a pointer lives.  Unregistered host memory is reported as
+// cudaMemoryTypeUnregistered by cudaPointerGetAttributes.
+enum class Mem { Device, Host, Invalid };
+
+Mem kind_of(const void *p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return Mem::Invalid;
+    }
+    switch (a.type) {
+        case cudaMemoryTypeDevice:
+        case cudaMemoryTypeManaged: return Mem::Device;
+        default: return Mem::Host;
+    }
+}
+
+bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return na && nb && x < y + nb && y < x + na;
+}
+
+size_t elem_size(int dtype) { return dtype == PENCIL_F16 ? 2 : 4; }
+
+// Plain calls' scratch: a few grow-only device buffers, one mutex.
+struct Pool {
+    std::mutex mu;
+    void *buf[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t cap[4] = {0, 0, 0, 0};
+
+    // Returns a device buffer of >= bytes in slot i, or nullptr.
+    void *get(int i, size_t bytes) {
+        if (cap[i] >= bytes) return buf[i];
+        if (buf[i]) cudaFree(buf[i]);
+        buf[i] = nullptr;
+        cap[i] = 0;
+        if (cudaMalloc(&buf[i], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            buf[i] = nullptr;
+            return nullptr;
+        }
+        cap[i] = bytes;
+        return buf[i];
+    }
+    void release() {
+        for (int i = 0; i < 4; ++i) {
+            if (buf[i]) cudaFree(buf[i]);
+            buf[i] = nullptr;
+            cap[i] = 0;
+        }
+    }
+};
+
+Pool &pool() {
+    static Pool p;
+    return p;
+}
+
+int check_dims(int h, int w) {
+    if (h <= 0 || w <= 0) return PENCIL_ERR_ARG;
+    if ((int64_t)h * (int64_t)w > ((int64_t)1 << 40)) return PENCIL_ERR_ARG;
+    return PENCIL_OK;
+}
+
+}  // namespace
+}  // namespace pencil
+
+using namespace pencil;
+
+extern "C" {
+
+const char *pencil_strerror(int status) {
+    switch (status) {
+        case PENCIL_OK: return "ok";
+        case PENCIL_ERR_ARG: return "invalid size or flag";
+        case PENCIL_ERR_NULL: return "null pointer";
+        case PENCIL_ERR_ALIAS: return "output overlaps an input (restrict rule)";
+        case PENCIL_ERR_PTR: return "host memory where device memory is required";
+        case PENCIL_ERR_NOMEM: return "workspace too small or device allocation failed";
+        case PENCIL_ERR_CUDA: return "CUDA error (see pencil_last_cuda_error)";
+        case PENCIL_ERR_TIMEOUT: return "bounded wait expired";
+        case PENCIL_ERR_UNSUPPORTED: return "not supported by this build";
+        default: return "unknown status";
+    }
+}
+
+int pencil_version(void) { return 100; }
+
+int pencil_last_cuda_error(void) { return g_last_cuda; }
+
+void pencil_shutdown(void) {
+    std::lock_guard<std::mutex> lk(pool().mu);
+    pool().release();
+}
+
+int pencil_conv2d_ex(int c, int h, int w, const void *in, int kh, int kw, const float *k, void *out,
+                     int dtype, int flags, void *stream) {
+    if (c <= 0 || kh <= 0 || kw <= 0 || (flags & ~PENCIL_CONV_GENERIC) != 0) return PENCIL_ERR_ARG;
+    if (dtype != PENCIL_F32 && dtype != PENCIL_F16) return PENCIL_ERR_ARG;
+    int st = check_dims(h, w);
+    if (st) return st;
+    if (!in || !k || !out) return PENCIL_ERR_NULL;
+    const size_t nb = (size_t)c * h * w * elem_size(dtype);
+    if (overlaps(out, nb, in, nb) || overlaps(out, nb, k, sizeof(float) * (size_t)kh * kw))
+        return PENCIL_ERR_ALIAS;
+    if (kind_of(in) != Mem::Device || kind_of(out) != Mem::Device || kind_of(k) != Mem::Device)
+        return PENCIL_ERR_PTR;
+    cudaError_t e = (flags & PENCIL_CONV_GENERIC)
+                        ? launch_conv2d_generic(dtype, c, h, w, in, kh, kw, k, out, (cudaStream_t)stream)
+                        : launch_conv2d(dtype, c, h, w, in, kh, kw, k, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
+}
+
+int pencil_conv2d_sep_ex(int c, int h, int w, const void *in, int kx, const float *gx, int ky,
+                         const float *gy, void *out, int dtype, void *stream) {
+    if (c <= 0 || kx <= 0 || ky <= 0) return PENCIL_ERR_ARG;
+    if (dtype != PENCIL_F32 && dtype != PENCIL_F16) return PENCIL_ERR_ARG;
+    int st = check_dims(h, w);
+    if (st) return st;
+    if (!in || !gx || !gy || !out) return PENCIL_ERR_NULL;
+    if (kx > PENCIL_MAX_SPECIALISED_K || ky > PENCIL_MAX_SPECIALISED_K) return PENCIL_ERR_UNSUPPORTED;
+    const size_t nb = (size_t)c * h * w * elem_size(dtype);
+    if (overlaps(out, nb, in, nb) || overlaps(out, nb, gx, sizeof(float) * kx) ||
+        overlaps(out, nb, gy, sizeof(float) * ky))
+        return PENCIL_ERR_ALIAS;
+    if (kind_of(in) != Mem::Device || kind_of(out) != Mem::Device || kind_of(gx) != Mem::Device ||
+        kind_of(gy) != Mem::Device)
+        return PENCIL_ERR_PTR;
+    cudaError_t e = launch_conv2d_sep(dtype, c, h, w, in, kx, gx, ky, gy, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
+}
+
+int pencil_conv2d(int h, int w, const float *in, int kh, int kw, const float *k, float *out) {
+    if (kh <= 0 || kw <= 0) return PENCIL_ERR_ARG;
+    int st = check_dims(h, w);
+    if (st) return st;
+    if (!in || !k || !out) return PENCIL_ERR_NULL;
+    const size_t nb = sizeof(float) * (size_t)h * w;
+    const size_t kb = sizeof(float) * (size_t)kh * kw;
+    if (overlaps(out, nb, in, nb) || overlaps(out, nb, k, kb)) return PENCIL_ERR_ALIAS;
+    const Mem mi = kind_of(in), mk = kind_of(k), mo = kind_of(out);
+    if (mi == Mem::Invalid || mk == Mem::Invalid || mo == Mem::Invalid) return PENCIL_ERR_PTR;
+    cudaStream_t s = 0;
+    if (mi == Mem::Device && mk == Mem::Device && mo == Mem::Device) {
+        cudaError_t e = launch_conv2d(PENCIL_F32, 1, h, w, in, kh, kw, k, out, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
+    }
+    std::lock_guard<std::mutex> lk(pool().mu);
+    const float *din = in, *dk = k;
+    float *dout = out;
+    if (mi == Mem::Host) {
+        void *b = pool().get(0, nb);
+        if (!b) return PENCIL_ERR_NOMEM;
+        PENCIL_CUDA_TRY(cudaMemcpyAsync(b, in, nb, cudaMemcpyHostToDevice, s));
+        din = static_cast<const float *>(b);
+    }
+    if (mk == Mem::Host) {
+        void *b = pool().get(1, kb);
+        if (!b) return PENCIL_ERR_NOMEM;
+        PENCIL_CUDA_TRY(cudaMemcpyAsync(b, k, kb, cudaMemcpyHostToDevice, s));
+        dk = static_cast<const float *>(b);
+    }
+    if (mo == Mem::Host) {
+        void *b = pool().get(2, nb);
+        if (!b) return PENCIL_ERR_NOMEM;
+        dout = static_cast<float *>(b);
+    }
+    PENCIL_CUDA_TRY(launch_conv2d(PENCIL_F32, 1, h, w, din, kh, kw, dk, dout, s));
+    if (mo == Mem::Host) PENCIL_CUDA_TRY(cudaMemcpyAsync(out, dout, nb, cudaMemcpyDeviceToHost, s));
+    PENCIL_CUDA_TRY(cudaStreamSynchronize(s));
+    return PENCIL_OK;
+}
+
+int pencil_conv2d_sep(int h, int w, const float *in, int kx, const float *gx, int ky,
+                      const float *gy, float *out) {
+    if (kx <= 0 || ky <= 0) return PENCIL_ERR_ARG;
+    int st = check_dims(h, w);
+    if (st) return st;
+    if (!in || !gx || !gy || !out) return PENCIL_ERR_NULL;
+    if (kx > PENCIL_MAX_SPECIALISED_K || ky > PENCIL_MAX_SPECIALISED_K) return PENCIL_ERR_UNSUPPORTED;
+    const size_t nb = sizeof(float) * (size_t)h * w;
+    if (overlaps(out, nb, in, nb) || overlaps(out, nb, gx, sizeof(float) * kx) ||
+        overlaps(out, nb, gy, sizeof(float) * ky))
+        return PENCIL_ERR_ALIAS;
+    const Mem mi = kind_of(in), mx = kind_of(gx), my = kind_of(gy), mo = kind_of(out);
+    if (mi == Mem::Invalid || mx == Mem::Invalid || my == Mem::Invalid || mo == Mem::Invalid)
+        return PENCIL_ERR_PTR;
+    cudaStream_t s = 0;
+    std::lock_guard<std::mutex> lk(pool().mu);
+    const float *din = in, *dgx = gx, *dgy = gy;
+    float *dout = out;
+    if (mi == Mem::Host) {
+        void *b = pool().get(0, nb);
+        if (!b) return PENCIL_ERR_NOMEM;
+        PENCIL_CUDA_TRY(cudaMemcpyAsync(b, in, nb, cudaMemcpyHostToDevice, s));
+        din = static_cast<const float *>(b);
+    }
+    if (mx == Mem::Host || my == Mem::Host) {
+        float *b = static_cast<float *>(pool().get(1, sizeof(float) * 2 * PENCIL_MAX_SPECIALISED_K));
+        if (!b) return PENCIL_ERR_NOMEM;
+        if (mx == Mem::Host) {
+            PENCIL_CUDA_TRY(cudaMemcpyAsync(b, gx, sizeof(float) * kx, cudaMemcpyHostToDevice, s));
+            dgx = b;
+        }
+        if (my == Mem::Host) {
+            float *by = b + PENCIL_MAX_SPECIALISED_K;
+            PENCIL_CUDA_TRY(cudaMemcpyAsync(by, gy, sizeof(float) * ky, cudaMemcpyHostToDevice, s));
+            dgy = by;
+        }
+    }
+    if (mo == Mem::Host) {
+        void *b = pool().get(2, nb);
+        if (!b) return PENCIL_ERR_NOMEM;
+        dout = static_cast<float *>(b);
+    }
+    PENCIL_CUDA_TRY(launch_conv2d_sep(PENCIL_F32, 1, h, w, din, kx, dgx, ky, dgy, dout, s));
+    if (mo == Mem::Host) PENCIL_CUDA_TRY(cudaMemcpyAsync(out, dout, nb, cudaMemcpyDeviceToHost, s));
+    PENCIL_CUDA_TRY(cudaStreamSynchronize(s));
+    return PENCIL_OK;
+}
+
+size_t pencil_jacobi2d_workspace_size(int h, int w) {
+    if (check_dims(h, w)) return 0;
+    return jacobi_workspace_bytes(h, w);
+}
+
+int pencil_jacobi2d_ex(int h, int w, float *u, int iters, int check_every, double *res_out,
+                       void *workspace, size_t ws_bytes, int temporal_t, void *stream) {
+    int st = check_dims(h, w);
+    if (st) return st;
+    if (iters < 0 || check_every < 0 || temporal_t < 0) return PENCIL_ERR_ARG;
+    if (!u || !workspace) return PENCIL_ERR_NULL;
+    const int nres = check_every > 0 ? iters / check_every : 0;
+    if (nres > 0 && !res_out) return PENCIL_ERR_NULL;
+    const size_t need = jacobi_workspace_bytes(h, w);
+    if (ws_bytes < need) return PENCIL_ERR_NOMEM;
+    if ((uintptr_t)workspace % 256 != 0) return PENCIL_ERR_ARG;
+    const size_t ub = sizeof(float) * (size_t)h * w;
+    if (overlaps(workspace, ws_bytes, u, ub)) return PENCIL_ERR_ALIAS;
+    if (nres > 0 && (overlaps(res_out, sizeof(double) * nres, u, ub) ||
+                     overlaps(res_out, sizeof(double) * nres, workspace, ws_bytes)))
+        return PENCIL_ERR_ALIAS;
+    if (kind_of(u) != Mem::Device || kind_of(workspace) != Mem::Device) return PENCIL_ERR_PTR;
+    if (nres > 0 && kind_of(res_out) != Mem::Device) return PENCIL_ERR_PTR;
+    cudaError_t e = jacobi_run(h, w, u, iters, check_every, res_out, workspace, ws_bytes, temporal_t,
+                               (cudaStream_t)stream);
+    return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
+}
+
+int pencil_residual2d(int h, int w, const float *u, double *res_out, void *workspace,
+                      size_t ws_bytes, void *stream) {
+    int st = check_dims(h, w);
+    if (st) return st;
+    if (!u || !res_out || !workspace) return PENCIL_ERR_NULL;
+    if (ws_bytes < jacobi_workspace_bytes(h, w)) return PENCIL_ERR_NOMEM;
+    if ((uintptr_t)workspace % 256 != 0) return PENCIL_ERR_ARG;
+    if (kind_of(u) != Mem::Device || kind_of(res_out) != Mem::Device ||
+        kind_of(workspace) != Mem::Device)
+        return PENCIL_ERR_PTR;
+    cudaError_t e = residual_run(h, w, u, res_out, workspace, (cudaStream_t)stream);
+    return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
+}
+
+int pencil_jacobi2d(int h, int w, float *u, int iters) {
+    int st = check_dims(h, w);
+    if (st) return st;
+    if (iters < 0) return PENCIL_ERR_ARG;
+    if (!u) return PENCIL_ERR_NULL;
+    const Mem mu = kind_of(u);
+    if (mu == Mem::Invalid) return PENCIL_ERR_PTR;
+    std::lock_guard<std::mutex> lk(pool().mu);
+    const size_t ub = sizeof(float) * (size_t)h * w;
+    const size_t wsb = jacobi_workspace_bytes(h, w);
+    void *ws = pool().get(3, wsb);
+    if (!ws) return PENCIL_ERR_NOMEM;
+    cudaStream_t s = 0;
+    float *du = u;
+    if (mu == Mem::Host) {
+        void *b = pool().get(0, ub);
+        if (!b) return PENCIL_ERR_NOMEM;
+        PENCIL_CUDA_TRY(cudaMemcpyAsync(b, u, ub, cudaMemcpyHostToDevice, s));
+        du = static_cast<float *>(b);
+    }
+    PENCIL_CUDA_TRY(jacobi_run(h, w, du, iters, 0, nullptr, ws, wsb, 0, s));
+    if (mu == Mem::Host) PENCIL_CUDA_TRY(cudaMemcpyAsync(u, du, ub, cudaMemcpyDeviceToHost, s));
+    PENCIL_CUDA_TRY(cudaStreamSynchronize(s));
+    return PENCIL_OK;
+}
+
+}  // extern "C"

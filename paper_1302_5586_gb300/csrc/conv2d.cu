@@ -1,0 +1,466 @@
+// conv2d.cu -- clamp-to-edge 2-D correlation kernels for sm_103a.
+//
+// out[i][j] = sum_a sum_b k[a][b] * in[clamp(i+a-kh/2)][clamp(j+b-kw/2)]
+// (the independent pixel loops of Sec. 2.2.3; a map over output pixels,
+// Sec. 3.2).  Every kernel here accumulates one output pixel in the same FP32
+// order: for each filter row a, s = k[a][0]*x0 then s = fma(k[a][b], xb, s)
+// for b = 1..kw-1, and acc = acc + s with acc starting at +0 -- so the direct,
+// generic and batched kernels return identical bits for the same pixel.
+//
+// Design (one GPU, HBM-streaming):
+//   * a CTA owns a TH x TW output tile; it stages the clamped halo tile
+//     (TH+kh-1) x (TW+2P) in shared memory as FP32 with 16-byte vector loads
+//     (float4 for FP32, 8 x binary16 for FP16), clamping rows per row and
+//     columns only in the chunks that cross an edge;
+//   * each thread computes R rows x C=4 columns in registers; for every
+//     staged input row it loads its (C+kw-1)-wide window once (LDS.128) and
+//     applies it to every output row that uses it (register blocking along
+//     rows), with the filter row fetched by a broadcast LDS.128;
+//   * the output is written with one 16-byte (FP32) or 8-byte (FP16) store per
+//     thread and row.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace pencil {
+namespace {
+
+template <typename T>
+struct Io;
+
+template <>
+struct Io<float> {
+    static constexpr int VEC = 4;  // elements per 16-byte chunk
+    __device__ __forceinline__ static float ld(const float *p) { return __ldg(p); }
+    __device__ __forceinline__ static void ld16(const float *p, float *d) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+    }
+    __device__ __forceinline__ static void st(float *p, float v) { *p = v; }
+    __device__ __forceinline__ static void st4(float *p, const float *v) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+
+template <>
+struct Io<__half> {
+    static constexpr int VEC = 8;
+    __device__ __forceinline__ static float ld(const __half *p) { return __half2float(__ldg(p)); }
+    __device__ __forceinline__ static void ld16(const __half *p, float *d) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            __half2 hh;
+            memcpy(&hh, &w[q], 4);
+            const float2 f = __half22float2(hh);
+            d[2 * q] = f.x;
+            d[2 * q + 1] = f.y;
+        }
+    }
+    __device__ __forceinline__ static void st(__half *p, float v) { *p = __float2half_rn(v); }
+    __device__ __forceinline__ static void st4(__half *p, const float *v) {
+        const __half2 a = __floats2half2_rn(v[0], v[1]);
+        const __half2 b = __floats2half2_rn(v[2], v[3]);
+        uint2 u;
+        memcpy(&u.x, &a, 4);
+        memcpy(&u.y, &b, 4);
+        *reinterpret_cast<uint2 *>(p) = u;
+    }
+};
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+
+// Stage s[r][c] = in[clamp(y0 + r)][clamp(x0 + c)] for r < SH, c < SW (as FP32).
+// x0 is a multiple of VEC, SW a multiple of VEC.  vec_ok: rows are 16-byte
+// aligned (w % VEC == 0 and the plane base is 16-byte aligned).
+template <typename T, int SH, int SW, int NT>
+__device__ __forceinline__ void stage_tile(const T *__restrict__ src, int h, int w, int y0, int x0,
+                                           bool vec_ok, float *__restrict__ s) {
+    constexpr int V = Io<T>::VEC;
+    constexpr int CPR = SW / V;
+    for (int idx = threadIdx.x; idx < SH * CPR; idx += NT) {
+        const int r = idx / CPR;
+        const int q = idx - r * CPR;
+        const int gr = clampi(y0 + r, 0, h - 1);
+        const int gc = x0 + q * V;
+        const T *row = src + (size_t)gr * (size_t)w;
+        float v[V];
+        if (vec_ok && gc >= 0 && gc + V <= w) {
+            Io<T>::ld16(row + gc, v);
+        } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e) v[e] = Io<T>::ld(row + clampi(gc + e, 0, w - 1));
+        }
+        float *d = s + r * SW + q * V;
+#pragma unroll
+        for (int e = 0; e < V; e += 4)
+            *reinterpret_cast<float4 *>(d + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+    }
+}
+
+// Write a thread's R x 4 block (rows y, cols x..x+3), bounds-checked.
+template <typename T, int R>
+__device__ __forceinline__ void store_block(T *__restrict__ dst, int h, int w, int y, int x,
+                                            bool vec_ok, const float (&acc)[R][4]) {
+#pragma unroll
+    for (int o = 0; o < R; ++o) {
+        const int i = y + o;
+        if (i >= h) break;
+        T *row = dst + (size_t)i * (size_t)w;
+        if (vec_ok && x + 4 <= w) {
+            Io<T>::st4(row + x, acc[o]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (x + c < w) Io<T>::st(row + x + c, acc[o][c]);
+        }
+    }
+}
+
+// ------------------------------------------------------------ direct kernel
+template <int KH, int KW, int TX, int TY, int R>
+struct DirectCfg {
+    static constexpr int C = 4;
+    static constexpr int AH = KH / 2, AW = KW / 2;
+    static constexpr int NT = TX * TY;
+    static constexpr int TW = TX * C, TH = TY * R;
+    static constexpr int P = round_up(AW, 8);      // left halo, 16-byte aligned for f32 and f16
+    static constexpr int SW = TW + 2 * P;
+    static constexpr int SH = TH + KH - 1;
+    static constexpr int KWP = round_up(KW, 4);    // filter row padded to LDS.128
+    static constexpr int NX = round_up(P - AW + C + KW - 1, 4);
+    static constexpr size_t smem = sizeof(float) * (size_t)(SH * SW + KH * KWP);
+};
+
+template <typename T, int KH, int KW, int TX, int TY, int R>
+__global__ void __launch_bounds__(TX *TY)
+    conv2d_direct_kernel(const T *__restrict__ in, const float *__restrict__ k, T *__restrict__ out,
+                         int h, int w, bool vec_ok) {
+    using Cfg = DirectCfg<KH, KW, TX, TY, R>;
+    constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, SH = Cfg::SH, KWP = Cfg::KWP,
+                  NX = Cfg::NX, AW = Cfg::AW, AH = Cfg::AH;
+    extern __shared__ __align__(16) float smem[];
+    float *s_in = smem;
+    float *s_k = smem + SH * SW;
+
+    const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
+    const T *src = in + plane;
+    T *dst = out + plane;
+    const int x0 = blockIdx.x * Cfg::TW;
+    const int y0 = blockIdx.y * Cfg::TH;
+
+    for (int t = threadIdx.x; t < KH * KWP; t += Cfg::NT) {
+        const int a = t / KWP, b = t - a * KWP;
+        s_k[t] = b < KW ? __ldg(k + a * KW + b) : 0.0f;
+    }
+    stage_tile<T, SH, SW, Cfg::NT>(src, h, w, y0 - AH, x0 - P, vec_ok, s_in);
+    __syncthreads();
+
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const float *srow = s_in + (ty * R) * SW + tx * C;
+
+    float acc[R][C];
+#pragma unroll
+    for (int o = 0; o < R; ++o)
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[o][c] = 0.0f;
+
+#pragma unroll(KH <= 7 ? R + KH - 1 : 1)
+    for (int r = 0; r < R + KH - 1; ++r) {
+        float x[NX];
+#pragma unroll
+        for (int m = 0; m < NX; m += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(srow + r * SW + m);
+            x[m] = v.x; x[m + 1] = v.y; x[m + 2] = v.z; x[m + 3] = v.w;
+        }
+#pragma unroll
+        for (int o = 0; o < R; ++o) {
+            const int a = r - o;
+            if (a >= 0 && a < KH) {
+                float kr[KWP];
+#pragma unroll
+                for (int m = 0; m < KWP; m += 4) {
+                    const float4 v = *reinterpret_cast<const float4 *>(s_k + a * KWP + m);
+                    kr[m] = v.x; kr[m + 1] = v.y; kr[m + 2] = v.z; kr[m + 3] = v.w;
+                }
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    float s = __fmul_rn(kr[0], x[P - AW + c]);
+#pragma unroll
+                    for (int b = 1; b < KW; ++b) s = __fmaf_rn(kr[b], x[P - AW + c + b], s);
+                    acc[o][c] = __fadd_rn(acc[o][c], s);
+                }
+            }
+        }
+    }
+    store_block<T, R>(dst, h, w, y0 + ty * R, x0 + tx * C, vec_ok, acc);
+}
+
+// ------------------------------------------------------------ generic kernel
+// Any kh, kw: one output per thread, reads straight from global memory with
+// clamped indices (L1/L2 serve the reuse).  Same per-pixel order as above.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    conv2d_generic_kernel(const T *__restrict__ in, const float *__restrict__ k, T *__restrict__ out,
+                          int h, int w, int kh, int kw) {
+    const int j = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (i >= h || j >= w) return;
+    const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
+    const T *src = in + plane;
+    const int ah = kh / 2, aw = kw / 2;
+    float acc = 0.0f;
+    for (int a = 0; a < kh; ++a) {
+        const T *row = src + (size_t)clampi(i + a - ah, 0, h - 1) * (size_t)w;
+        const float *kr = k + (size_t)a * kw;
+        float s = __fmul_rn(__ldg(kr), Io<T>::ld(row + clampi(j - aw, 0, w - 1)));
+        for (int b = 1; b < kw; ++b)
+            s = __fmaf_rn(__ldg(kr + b), Io<T>::ld(row + clampi(j + b - aw, 0, w - 1)), s);
+        acc = __fadd_rn(acc, s);
+    }
+    Io<T>::st(out + plane + (size_t)i * w + j, acc);
+}
+
+// --------------------------------------------------------- separable kernel
+// Row pass (kx taps) of the staged halo tile into shared memory, then the
+// column pass (ky taps) from it; nothing intermediate goes to HBM.
+template <int KX, int KY, int TX, int TY, int R>
+struct SepCfg {
+    static constexpr int C = 4;
+    static constexpr int AX = KX / 2, AY = KY / 2;
+    static constexpr int NT = TX * TY;
+    static constexpr int TW = TX * C, TH = TY * R;
+    static constexpr int P = round_up(AX, 8);
+    static constexpr int SW = TW + 2 * P;
+    static constexpr int SH = TH + KY - 1;
+    static constexpr int NX = round_up(P - AX + C + KX - 1, 4);
+    static constexpr size_t smem = sizeof(float) * (size_t)(SH * SW + SH * TW);
+};
+
+template <typename T, int KX, int KY, int TX, int TY, int R>
+__global__ void __launch_bounds__(TX *TY)
+    conv2d_sep_kernel(const T *__restrict__ in, const float *__restrict__ gx,
+                      const float *__restrict__ gy, T *__restrict__ out, int h, int w, bool vec_ok) {
+    using Cfg = SepCfg<KX, KY, TX, TY, R>;
+    constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, SH = Cfg::SH, TW = Cfg::TW,
+                  NX = Cfg::NX, AX = Cfg::AX, AY = Cfg::AY;
+    extern __shared__ __align__(16) float smem[];
+    float *s_in = smem;
+    float *s_t = smem + SH * SW;
+
+    float fx[KX], fy[KY];
+#pragma unroll
+    for (int b = 0; b < KX; ++b) fx[b] = __ldg(gx + b);
+#pragma unroll
+    for (int a = 0; a < KY; ++a) fy[a] = __ldg(gy + a);
+
+    const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
+    const T *src = in + plane;
+    T *dst = out + plane;
+    const int x0 = blockIdx.x * TW;
+    const int y0 = blockIdx.y * Cfg::TH;
+    stage_tile<T, SH, SW, Cfg::NT>(src, h, w, y0 - AY, x0 - P, vec_ok, s_in);
+    __syncthreads();
+
+    // row pass: t[r][q*C + c] = sum_b gx[b] * in[r][q*C + c + b - AX]
+    constexpr int QPR = TW / C;
+    for (int idx = threadIdx.x; idx < SH * QPR; idx += Cfg::NT) {
+        const int r = idx / QPR, q = idx - r * QPR;
+        const float *sp = s_in + r * SW + q * C;
+        float x[NX];
+#pragma unroll
+        for (int m = 0; m < NX; m += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(sp + m);
+            x[m] = v.x; x[m + 1] = v.y; x[m + 2] = v.z; x[m + 3] = v.w;
+        }
+        float t[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            float s = __fmul_rn(fx[0], x[P - AX + c]);
+#pragma unroll
+            for (int b = 1; b < KX; ++b) s = __fmaf_rn(fx[b], x[P - AX + c + b], s);
+            t[c] = s;
+        }
+        *reinterpret_cast<float4 *>(s_t + r * TW + q * C) = make_float4(t[0], t[1], t[2], t[3]);
+    }
+    __syncthreads();
+
+    // column pass: out[o][c] = sum_a gy[a] * t[o + a][c]
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    float acc[R][C];
+#pragma unroll
+    for (int r = 0; r < R + KY - 1; ++r) {
+        const float4 v = *reinterpret_cast<const float4 *>(s_t + (ty * R + r) * TW + tx * C);
+        const float tv[C] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int o = 0; o < R; ++o) {
+            const int a = r - o;
+            if (a == 0) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) acc[o][c] = __fmul_rn(fy[0], tv[c]);
+            } else if (a > 0 && a < KY) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) acc[o][c] = __fmaf_rn(fy[a], tv[c], acc[o][c]);
+            }
+        }
+    }
+    store_block<T, R>(dst, h, w, y0 + ty * R, x0 + tx * C, vec_ok, acc);
+}
+
+// Separable with runtime tap counts (fallback for sides without a
+// specialisation): same order, taps read from shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    conv2d_sep_generic_kernel(const T *__restrict__ in, const float *__restrict__ gx,
+                              const float *__restrict__ gy, T *__restrict__ out, int h, int w,
+                              int kx, int ky) {
+    // tile 32 x 32 outputs, 256 threads
+    extern __shared__ __align__(16) float smem[];
+    const int SH = 32 + ky - 1;
+    float *s_t = smem;                  // SH x 32
+    const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
+    const T *src = in + plane;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    const int ax = kx / 2, ay = ky / 2;
+    for (int idx = threadIdx.x; idx < SH * 32; idx += 256) {
+        const int r = idx / 32, c = idx % 32;
+        const T *row = src + (size_t)clampi(y0 + r - ay, 0, h - 1) * (size_t)w;
+        const int j = x0 + c;
+        float s = __fmul_rn(__ldg(gx), Io<T>::ld(row + clampi(j - ax, 0, w - 1)));
+        for (int b = 1; b < kx; ++b) s = __fmaf_rn(__ldg(gx + b), Io<T>::ld(row + clampi(j + b - ax, 0, w - 1)), s);
+        s_t[idx] = s;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 32 * 32; idx += 256) {
+        const int r = idx / 32, c = idx % 32;
+        const int i = y0 + r, j = x0 + c;
+        if (i >= h || j >= w) continue;
+        float acc = __fmul_rn(__ldg(gy), s_t[r * 32 + c]);
+        for (int a = 1; a < ky; ++a) acc = __fmaf_rn(__ldg(gy + a), s_t[(r + a) * 32 + c], acc);
+        Io<T>::st(out + plane + (size_t)i * w + j, acc);
+    }
+}
+
+// ------------------------------------------------------------------ launch
+template <typename Kern>
+cudaError_t set_smem(Kern kern, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, int K, int TX, int TY, int R>
+cudaError_t run_direct(int c, int h, int w, const T *in, const float *k, T *out, bool vec_ok,
+                       cudaStream_t s) {
+    using Cfg = DirectCfg<K, K, TX, TY, R>;
+    auto kern = conv2d_direct_kernel<T, K, K, TX, TY, R>;
+    cudaError_t e = set_smem(kern, Cfg::smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((w + Cfg::TW - 1) / Cfg::TW, (h + Cfg::TH - 1) / Cfg::TH, c);
+    kern<<<grid, Cfg::NT, Cfg::smem, s>>>(in, k, out, h, w, vec_ok);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_direct_k(int K, int c, int h, int w, const T *in, const float *k, T *out,
+                         bool vec_ok, cudaStream_t s) {
+    switch (K) {
+        case 1: return run_direct<T, 1, 32, 8, 4>(c, h, w, in, k, out, vec_ok, s);
+        case 3: return run_direct<T, 3, 32, 8, 4>(c, h, w, in, k, out, vec_ok, s);
+        case 5: return run_direct<T, 5, 32, 8, 4>(c, h, w, in, k, out, vec_ok, s);
+        case 7: return run_direct<T, 7, 32, 4, 8>(c, h, w, in, k, out, vec_ok, s);
+        case 9: return run_direct<T, 9, 32, 4, 8>(c, h, w, in, k, out, vec_ok, s);
+        case 11: return run_direct<T, 11, 32, 4, 8>(c, h, w, in, k, out, vec_ok, s);
+        case 13: return run_direct<T, 13, 32, 4, 8>(c, h, w, in, k, out, vec_ok, s);
+        case 15: return run_direct<T, 15, 32, 4, 8>(c, h, w, in, k, out, vec_ok, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t run_generic(int c, int h, int w, const T *in, int kh, int kw, const float *k, T *out,
+                        cudaStream_t s) {
+    dim3 grid((w + 31) / 32, (h + 7) / 8, c);
+    conv2d_generic_kernel<T><<<grid, 256, 0, s>>>(in, k, out, h, w, kh, kw);
+    return cudaGetLastError();
+}
+
+template <typename T, int K, int TX, int TY, int R>
+cudaError_t run_sep(int c, int h, int w, const T *in, const float *gx, const float *gy, T *out,
+                    bool vec_ok, cudaStream_t s) {
+    using Cfg = SepCfg<K, K, TX, TY, R>;
+    auto kern = conv2d_sep_kernel<T, K, K, TX, TY, R>;
+    cudaError_t e = set_smem(kern, Cfg::smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((w + Cfg::TW - 1) / Cfg::TW, (h + Cfg::TH - 1) / Cfg::TH, c);
+    kern<<<grid, Cfg::NT, Cfg::smem, s>>>(in, gx, gy, out, h, w, vec_ok);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_sep_any(int c, int h, int w, const T *in, int kx, const float *gx, int ky,
+                        const float *gy, T *out, bool vec_ok, cudaStream_t s) {
+    if (kx == ky) {
+        switch (kx) {
+            case 3: return run_sep<T, 3, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
+            case 5: return run_sep<T, 5, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
+            case 7: return run_sep<T, 7, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
+            case 9: return run_sep<T, 9, 32, 4, 8>(c, h, w, in, gx, gy, out, vec_ok, s);
+            case 11: return run_sep<T, 11, 32, 4, 8>(c, h, w, in, gx, gy, out, vec_ok, s);
+            case 13: return run_sep<T, 13, 32, 4, 8>(c, h, w, in, gx, gy, out, vec_ok, s);
+            case 15: return run_sep<T, 15, 32, 4, 8>(c, h, w, in, gx, gy, out, vec_ok, s);
+            default: break;
+        }
+    }
+    const size_t smem = sizeof(float) * (size_t)(32 + ky - 1) * 32;
+    dim3 grid((w + 31) / 32, (h + 31) / 32, c);
+    conv2d_sep_generic_kernel<T><<<grid, 256, smem, s>>>(in, gx, gy, out, h, w, kx, ky);
+    return cudaGetLastError();
+}
+
+bool rows_aligned(const void *p, int w, int vec) {
+    return (w % vec == 0) && ((uintptr_t)p % 16 == 0);
+}
+
+}  // namespace
+
+cudaError_t launch_conv2d(int dtype, int c, int h, int w, const void *in, int kh, int kw,
+                          const float *k, void *out, cudaStream_t s) {
+    const bool special = (kh == kw) && (kh % 2 == 1) && kh <= PENCIL_MAX_SPECIALISED_K;
+    if (dtype == PENCIL_F32) {
+        const float *i = static_cast<const float *>(in);
+        float *o = static_cast<float *>(out);
+        const bool v = rows_aligned(in, w, 4) && rows_aligned(out, w, 4);
+        if (special) return run_direct_k<float>(kh, c, h, w, i, k, o, v, s);
+        return run_generic<float>(c, h, w, i, kh, kw, k, o, s);
+    }
+    const __half *i = static_cast<const __half *>(in);
+    __half *o = static_cast<__half *>(out);
+    const bool v = rows_aligned(in, w, 8) && rows_aligned(out, w, 8);
+    if (special) return run_direct_k<__half>(kh, c, h, w, i, k, o, v, s);
+    return run_generic<__half>(c, h, w, i, kh, kw, k, o, s);
+}
+
+cudaError_t launch_conv2d_generic(int dtype, int c, int h, int w, const void *in, int kh, int kw,
+                                  const float *k, void *out, cudaStream_t s) {
+    if (dtype == PENCIL_F32)
+        return run_generic<float>(c, h, w, static_cast<const float *>(in), kh, kw, k,
+                                  static_cast<float *>(out), s);
+    return run_generic<__half>(c, h, w, static_cast<const __half *>(in), kh, kw, k,
+                               static_cast<__half *>(out), s);
+}
+
+cudaError_t launch_conv2d_sep(int dtype, int c, int h, int w, const void *in, int kx,
+                              const float *gx, int ky, const float *gy, void *out,
+                              cudaStream_t s) {
+    if (dtype == PENCIL_F32) {
+        const bool v = rows_aligned(in, w, 4) && rows_aligned(out, w, 4);
+        return run_sep_any<float>(c, h, w, static_cast<const float *>(in), kx, gx, ky, gy,
+                                  static_cast<float *>(out), v, s);
+    }
+    const bool v = rows_aligned(in, w, 8) && rows_aligned(out, w, 8);
+    return run_sep_any<__half>(c, h, w, static_cast<const __half *>(in), kx, gx, ky, gy,
+                               static_cast<__half *>(out), v, s);
+}
+
+}  // namespace pencil

@@ -1,0 +1,43 @@
+// internal.cuh -- declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "pencil.h"
+
+namespace pencil {
+
+// Record `e` as the calling thread's last CUDA error and return PENCIL_ERR_CUDA.
+int cuda_fail(cudaError_t e);
+
+#define PENCIL_CUDA_TRY(expr)                                      \
+    do {                                                           \
+        cudaError_t _pe = (expr);                                  \
+        if (_pe != cudaSuccess) return ::pencil::cuda_fail(_pe);   \
+    } while (0)
+
+// Round x up to a multiple of a (a > 0).
+__host__ __device__ constexpr int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+// ----------------------------------------------------------------- conv2d
+// All launchers queue work on `s` and return the launch status.
+// Arrays are device memory; the host layer has validated sizes and pointers.
+cudaError_t launch_conv2d(int dtype, int c, int h, int w, const void *in, int kh, int kw,
+                          const float *k, void *out, cudaStream_t s);
+// Force the generic (any-size) kernel; used by tests of the fixed-order rule.
+cudaError_t launch_conv2d_generic(int dtype, int c, int h, int w, const void *in, int kh, int kw,
+                                  const float *k, void *out, cudaStream_t s);
+cudaError_t launch_conv2d_sep(int dtype, int c, int h, int w, const void *in, int kx,
+                              const float *gx, int ky, const float *gy, void *out,
+                              cudaStream_t s);
+
+// ----------------------------------------------------------------- jacobi
+size_t jacobi_workspace_bytes(int h, int w);
+cudaError_t jacobi_run(int h, int w, float *u, int iters, int check_every, double *res,
+                       void *ws, size_t ws_bytes, int temporal_t, cudaStream_t s);
+cudaError_t residual_run(int h, int w, const float *u, double *res, void *ws, cudaStream_t s);
+
+}  // namespace pencil

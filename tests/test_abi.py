@@ -1,0 +1,77 @@
+"""The C ABI library builds, loads, and exports every function include/pencil.h
+declares; argument checks that run before any CUDA call work without a GPU."""
+import ctypes
+import subprocess
+
+import pytest
+
+import paper_1302_5586_gb300 as pg
+from paper_1302_5586_gb300 import build as pg_build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pg_build.build()
+    return pg.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = pg.declared_symbols()
+    assert "pencil_conv2d" in names and "pencil_jacobi2d" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", pg.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        getattr(lib, n)
+
+
+def test_header_compiles_as_c99_and_cxx(tmp_path):
+    src = tmp_path / "t.c"
+    src.write_text('#include "pencil.h"\nint main(void) { return pencil_version() > 0 ? 0 : 1; }\n')
+    inc = "-I" + pg.HEADER.rsplit("/", 1)[0]
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-pedantic", inc, "-c", str(src), "-o",
+                    str(tmp_path / "a.o")], check=True)
+    subprocess.run(["g++", "-x", "c++", "-std=c++17", "-Wall", "-Werror", inc, "-c", str(src), "-o",
+                    str(tmp_path / "b.o")], check=True)
+
+
+def test_utility_calls(lib):
+    assert pg.pencil_version() >= 100
+    assert pg.pencil_strerror(0) == "ok"
+    assert "restrict" in pg.pencil_strerror(-3)
+    assert pg.pencil_strerror(-99) == "unknown status"
+
+
+@pytest.mark.parametrize("args,status", [
+    ((0, 5, 1, 3, 3, 1, 2), -1),       # h <= 0
+    ((5, 5, 1, 0, 3, 1, 2), -1),       # kh <= 0
+    ((5, 5, None, 3, 3, 1, 2), -2),    # null input
+    ((5, 5, 4096, 3, 3, 1, 4096 + 40), -3),  # out overlaps in
+])
+def test_conv2d_argument_errors_before_cuda(lib, args, status):
+    h, w, i, kh, kw, k, o = args
+    assert lib.pencil_conv2d(h, w, i, kh, kw, k, o) == status
+
+
+def test_ex_argument_errors_before_cuda(lib):
+    assert lib.pencil_conv2d_ex(1, 4, 4, 1, 3, 3, 2, 3, 7, 0, None) == -1   # bad dtype
+    assert lib.pencil_conv2d_ex(1, 4, 4, 1, 3, 3, 2, 3, 0, 4, None) == -1   # unknown flag
+    assert lib.pencil_conv2d_sep_ex(1, 4, 4, 1, 17, 2, 3, 3, 5, 0, None) == -8  # side > 15
+    assert lib.pencil_conv2d_sep(4, 4, 1, 3, 2, 16, 3, 5) == -8
+    assert lib.pencil_jacobi2d_ex(4, 4, 1, -1, 0, None, 256, 1 << 20, 0, None) == -1
+    assert lib.pencil_jacobi2d_ex(4, 4, 1, 10, 5, None, 256, 1 << 20, 0, None) == -2  # no res_out
+    assert lib.pencil_jacobi2d_ex(64, 64, 1, 10, 0, None, 256, 16, 0, None) == -5     # workspace small
+    assert lib.pencil_jacobi2d(3, 3, None, 1) == -2
+    ws = pg.pencil_jacobi2d_workspace_size(8192, 8192)
+    assert ws >= 8192 * 8192 * 4 and ws % 256 == 0
+    assert pg.pencil_jacobi2d_workspace_size(0, 5) == 0
+
+
+def test_binding_refuses_missing_library(monkeypatch, tmp_path):
+    import paper_1302_5586_gb300._binding as b
+    monkeypatch.setattr(b, "_lib", None)
+    monkeypatch.setattr(b, "LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        b.lib()

@@ -1,0 +1,236 @@
+"""GPU parity of the conv2d kernels against the FP64 oracle, through the C ABI.
+
+Tolerances (per pixel, bound = sum |k| |x| from the oracle):
+  FP32 storage: |gpu - oracle| <= 1e-6 * bound;
+  FP16 storage: |gpu - oracle(binary16 input)| <= 2^-10 * bound.
+Kernels that share the fixed per-pixel order must agree bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1302_5586_gb300 as pg
+import synth
+from gpu_util import dev, gather, sample_points, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+F32_TOL = 1e-6
+F16_TOL = 2.0 ** -10
+
+
+def run_conv(img, k, dtype=pg.PENCIL_F32, flags=0):
+    c, h, w = img.shape
+    d_in = to_dev(img)
+    d_k = to_dev(k)
+    d_out = torch.empty_like(d_in)
+    pg.pencil_conv2d_ex(c, h, w, d_in, k.shape[0], k.shape[1], d_k, d_out, dtype, flags)
+    torch.cuda.synchronize()
+    return d_out
+
+
+def assert_within(gpu, ref, bound, tol, what):
+    err = np.abs(gpu.astype(np.float64) - ref)
+    ratio = np.max(err / np.maximum(bound, 1e-300))
+    assert np.all(err <= tol * bound), f"{what}: max err/bound {ratio:.3e} > {tol:.3e}"
+    return ratio
+
+
+SHAPES = [(2, 75, 301), (1, 200, 520), (3, 33, 128), (1, 1, 1), (1, 5, 3), (2, 1, 77), (1, 64, 1)]
+
+
+@pytest.mark.parametrize("K", [1, 3, 5, 7, 9, 11, 13, 15])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_direct_f32_matches_oracle(K, shape):
+    c, h, w = shape
+    img = synth.image_f32(1000 + K, c, h, w)
+    k = synth.filter_f32(2000 + K, K, K)
+    out = run_conv(img, k).cpu().numpy()
+    ref, bound = oracle.conv2d(img, k)
+    assert_within(out, ref, bound, F32_TOL, f"K={K} shape={shape}")
+
+
+@pytest.mark.parametrize("K", [3, 7, 15])
+@pytest.mark.parametrize("shape", [(2, 75, 301), (1, 200, 520), (1, 3, 2)])
+def test_specialised_and_generic_kernels_agree_bitwise(K, shape):
+    c, h, w = shape
+    img = synth.image_f32(31 + K, c, h, w)
+    k = synth.filter_f32(41 + K, K, K)
+    a = run_conv(img, k).cpu().numpy()
+    b = run_conv(img, k, flags=pg.PENCIL_CONV_GENERIC).cpu().numpy()
+    np.testing.assert_array_equal(a.view(np.uint32), b.view(np.uint32))
+    img16 = synth.to_f16(img)
+    a16 = run_conv(img16, k, pg.PENCIL_F16).cpu().numpy()
+    b16 = run_conv(img16, k, pg.PENCIL_F16, pg.PENCIL_CONV_GENERIC).cpu().numpy()
+    np.testing.assert_array_equal(a16.view(np.uint16), b16.view(np.uint16))
+
+
+@pytest.mark.parametrize("kh,kw", [(4, 6), (2, 1), (1, 9), (31, 3), (17, 17), (3, 5)])
+def test_generic_sizes_match_oracle(kh, kw):
+    img = synth.image_f32(77, 2, 45, 70)
+    k = synth.filter_f32(78, kh, kw)
+    out = run_conv(img, k).cpu().numpy()
+    ref, bound = oracle.conv2d(img, k)
+    assert_within(out, ref, bound, F32_TOL, f"{kh}x{kw}")
+
+
+@pytest.mark.parametrize("K", [3, 7, 15])
+@pytest.mark.parametrize("shape", [(2, 75, 304), (1, 130, 257)])
+def test_direct_f16_matches_oracle(K, shape):
+    c, h, w = shape
+    img16 = synth.image_f16(300 + K, c, h, w)
+    k = synth.filter_f32(400 + K, K, K)
+    out = run_conv(img16, k, pg.PENCIL_F16).cpu().numpy()
+    ref, bound = oracle.conv2d(img16, k)
+    assert_within(out, ref, bound, F16_TOL, f"f16 K={K}")
+    # the binary16 result is the rounding of an FP32 value close to the exact sum:
+    # within one binary16 ulp of the exact sum rounded to nearest even
+    want = oracle.f64_to_f16(ref).view(np.float16).astype(np.float64)
+    ulp = np.spacing(np.abs(want).astype(np.float16)).astype(np.float64)
+    assert np.all(np.abs(out.astype(np.float64) - want) <= ulp)
+
+
+def test_delta_filter_is_identity_bitwise():
+    img = synth.image_f32(5, 2, 67, 130)
+    for K in (1, 3, 9, 15):
+        k = np.zeros((K, K), dtype=np.float32)
+        k[K // 2, K // 2] = 1.0
+        out = run_conv(img, k).cpu().numpy()
+        np.testing.assert_array_equal(out, img)
+        img16 = synth.to_f16(img)
+        out16 = run_conv(img16, k, pg.PENCIL_F16).cpu().numpy()
+        np.testing.assert_array_equal(out16.view(np.uint16), img16.view(np.uint16))
+
+
+@pytest.mark.parametrize("K,p,q", [(3, 0, 0), (7, 40, 129), (15, 13, 3), (15, 66, 131), (5, 33, 64)])
+def test_nan_footprint_matches_oracle(K, p, q):
+    """One NaN poisons exactly the pixels whose clamped window reads it."""
+    img = synth.image_f32(9, 1, 67, 132)
+    img[0, p, q] = np.nan
+    k = synth.filter_f32(10, K, K)
+    out = run_conv(img, k).cpu().numpy()
+    ref, _ = oracle.conv2d(img, k)
+    np.testing.assert_array_equal(np.isnan(out), np.isnan(ref))
+
+
+@pytest.mark.parametrize("K", [3, 5, 7, 9, 11, 13, 15])
+@pytest.mark.parametrize("shape", [(2, 75, 301), (1, 200, 520), (1, 2, 3)])
+def test_separable_matches_oracle(K, shape):
+    c, h, w = shape
+    gx = synth.gaussian_taps_f32(K // 2, 1.0 + K / 5)
+    gy = synth.filter_f32(55 + K, 1, K).ravel()
+    img = synth.image_f32(60 + K, c, h, w)
+    d_in = to_dev(img)
+    d_out = torch.empty_like(d_in)
+    pg.pencil_conv2d_sep_ex(c, h, w, d_in, K, to_dev(gx), K, to_dev(gy), d_out, pg.PENCIL_F32)
+    torch.cuda.synchronize()
+    ref, bound = oracle.conv2d_sep(img, gx, gy)
+    assert_within(d_out.cpu().numpy(), ref, bound, F32_TOL, f"sep K={K}")
+    img16 = synth.to_f16(img)
+    d16 = to_dev(img16)
+    o16 = torch.empty_like(d16)
+    pg.pencil_conv2d_sep_ex(c, h, w, d16, K, to_dev(gx), K, to_dev(gy), o16, pg.PENCIL_F16)
+    torch.cuda.synchronize()
+    ref16, bound16 = oracle.conv2d_sep(img16, gx, gy)
+    assert_within(o16.cpu().numpy(), ref16, bound16, F16_TOL, f"sep f16 K={K}")
+
+
+@pytest.mark.parametrize("kx,ky", [(3, 7), (1, 5), (15, 2)])
+def test_separable_unequal_sides(kx, ky):
+    gx = synth.filter_f32(1, 1, kx).ravel()
+    gy = synth.filter_f32(2, 1, ky).ravel()
+    img = synth.image_f32(3, 2, 70, 90)
+    d_in = to_dev(img)
+    d_out = torch.empty_like(d_in)
+    pg.pencil_conv2d_sep_ex(2, 70, 90, d_in, kx, to_dev(gx), ky, to_dev(gy), d_out, pg.PENCIL_F32)
+    torch.cuda.synchronize()
+    ref, bound = oracle.conv2d_sep(img, gx, gy)
+    assert_within(d_out.cpu().numpy(), ref, bound, F32_TOL, f"sep {kx}x{ky}")
+
+
+def test_plain_call_accepts_host_and_device_memory():
+    img = synth.image_f32(21, 1, 97, 203)[0]
+    k = synth.filter_f32(22, 5, 5)
+    out_host = np.empty_like(img)
+    pg.pencil_conv2d(97, 203, img, 5, 5, k, out_host)
+    d_in, d_k = to_dev(img), to_dev(k)
+    d_out = torch.empty_like(d_in)
+    pg.pencil_conv2d(97, 203, d_in, 5, 5, d_k, d_out)
+    np.testing.assert_array_equal(out_host, d_out.cpu().numpy())
+    pinned = torch.from_numpy(img).pin_memory()
+    out_pinned = torch.empty_like(pinned).pin_memory()
+    pg.pencil_conv2d(97, 203, pinned, 5, 5, k, out_pinned)
+    np.testing.assert_array_equal(out_host, out_pinned.numpy())
+    ref, bound = oracle.conv2d(img, k)
+    assert_within(out_host[None], ref, bound, F32_TOL, "plain host")
+
+
+def test_plain_separable_call_host_memory():
+    img = synth.image_f32(24, 1, 90, 130)[0]
+    g = synth.gaussian_taps_f32(7, 3.0)
+    out = np.empty_like(img)
+    pg.pencil_conv2d_sep(90, 130, img, 15, g, 15, g, out)
+    d_in = to_dev(img[None])
+    d_out = torch.empty_like(d_in)
+    pg.pencil_conv2d_sep_ex(1, 90, 130, d_in, 15, to_dev(g), 15, to_dev(g), d_out, pg.PENCIL_F32)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out, d_out.cpu().numpy()[0])
+
+
+def test_restrict_and_memory_kind_errors():
+    d = torch.zeros(4, 64, 64, device=dev())
+    k = torch.ones(3, 3, device=dev()) / 9
+    with pytest.raises(pg.PencilError) as e:
+        pg.pencil_conv2d_ex(1, 64, 64, d[0], 3, 3, k, d[0], pg.PENCIL_F32)
+    assert e.value.name == "PENCIL_ERR_ALIAS"
+    with pytest.raises(pg.PencilError) as e:  # partial overlap: out starts inside in
+        pg.pencil_conv2d_ex(2, 64, 64, d[0], 3, 3, k, d[1], pg.PENCIL_F32)
+    assert e.value.name == "PENCIL_ERR_ALIAS"
+    host = np.zeros((64, 64), dtype=np.float32)
+    with pytest.raises(pg.PencilError) as e:
+        pg.pencil_conv2d_ex(1, 64, 64, host, 3, 3, k, d[1], pg.PENCIL_F32)
+    assert e.value.name == "PENCIL_ERR_PTR"
+    pg.pencil_conv2d_ex(1, 64, 64, d[0], 3, 3, k, d[1], pg.PENCIL_F32)  # disjoint: fine
+    torch.cuda.synchronize()
+
+
+def test_stream_ordered_on_a_side_stream():
+    img = synth.image_f32(71, 3, 128, 256)
+    k = synth.filter_f32(72, 7, 7)
+    s = torch.cuda.Stream()
+    d_in = to_dev(img)
+    d_k = to_dev(k)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        d_out = torch.empty_like(d_in)
+        pg.pencil_conv2d_ex(3, 128, 256, d_in, 7, 7, d_k, d_out, pg.PENCIL_F32, 0, s)
+    s.synchronize()
+    ref = run_conv(img, k).cpu().numpy()
+    np.testing.assert_array_equal(d_out.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("K", [3, 7, 15])
+def test_full_size_8192x8192x3_sampled(K):
+    """The 8192 x 8192 x 3 workload in the benchmark's launch configuration,
+    checked at 50k random pixels plus every pixel of the outer two rows and
+    columns of the last channel."""
+    c, h, w = 3, 8192, 8192
+    img = synth.image_f32(synth.SEEDS["conv8192x3"], c, h, w)
+    k = synth.filter_f32(synth.SEEDS["conv8192x3"] + K, K, K)
+    out = run_conv(img, k)
+    pts = sample_points(K, c, h, w, 50000)
+    ref, bound = oracle.conv2d_points(img, k, pts)
+    assert_within(gather(out, pts), ref, bound, F32_TOL, f"full K={K}")
+
+
+def test_full_size_gaussian_separable_sampled():
+    c, h, w = 3, 8192, 8192
+    img = synth.image_f32(synth.SEEDS["conv8192x3"], c, h, w)
+    g = synth.gaussian_taps_f32(7, 3.0)
+    d_in = to_dev(img)
+    d_out = torch.empty_like(d_in)
+    pg.pencil_conv2d_sep_ex(c, h, w, d_in, 15, to_dev(g), 15, to_dev(g), d_out, pg.PENCIL_F32)
+    torch.cuda.synchronize()
+    pts = sample_points(99, c, h, w, 50000)
+    ref, bound = oracle.conv2d_sep_points(img, g, g, pts)
+    assert_within(gather(d_out, pts), ref, bound, F32_TOL, "gaussian sep full")

@@ -215,6 +215,18 @@ def test_points_match_full_image():
         oracle.conv2d_points(img, k, np.array([[0, 31, 0]]))
 
 
+def test_separable_points_match_full_image():
+    img = synth.image_f32(14, 2, 23, 19)
+    gx = synth.filter_f32(15, 1, 5).ravel()
+    gy = synth.filter_f32(16, 1, 3).ravel()
+    out, bound = oracle.conv2d_sep(img, gx, gy)
+    r = _rng(14)
+    pts = np.stack([r.integers(0, 2, 40), r.integers(0, 23, 40), r.integers(0, 19, 40)], axis=1)
+    po, pb = oracle.conv2d_sep_points(img, gx, gy, pts)
+    np.testing.assert_array_equal(po, out[pts[:, 0], pts[:, 1], pts[:, 2]])
+    np.testing.assert_array_equal(pb, bound[pts[:, 0], pts[:, 1], pts[:, 2]])
+
+
 def test_binary16_input_is_widened_exactly():
     img = synth.image_f16(8, 1, 12, 10)
     k = synth.filter_f32(8, 3, 3)
