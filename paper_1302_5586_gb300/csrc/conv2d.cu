@@ -40,6 +40,10 @@ struct Io<float> {
     __device__ __forceinline__ static void st4(float *p, const float *v) {
         *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
     }
+    __device__ __forceinline__ static void ld16s(const float *p, float *d) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+    }
 };
 
 template <>
@@ -47,7 +51,12 @@ struct Io<__half> {
     static constexpr int VEC = 8;
     __device__ __forceinline__ static float ld(const __half *p) { return __half2float(__ldg(p)); }
     __device__ __forceinline__ static void ld16(const __half *p, float *d) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        unpack(__ldg(reinterpret_cast<const uint4 *>(p)), d);
+    }
+    __device__ __forceinline__ static void ld16s(const __half *p, float *d) {
+        unpack(*reinterpret_cast<const uint4 *>(p), d);
+    }
+    __device__ __forceinline__ static void unpack(const uint4 v, float *d) {
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -73,30 +82,57 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v,
 
 // Stage s[r][c] = in[clamp(y0 + r)][clamp(x0 + c)] for r < SH, c < SW (as FP32).
 // x0 is a multiple of VEC, SW a multiple of VEC.  vec_ok: rows are 16-byte
-// aligned (w % VEC == 0 and the plane base is 16-byte aligned).
+// aligned (w % VEC == 0 and the plane base is 16-byte aligned).  Chunks that
+// lie inside the row go through cp.async (all of a CTA's copies in flight at
+// once); chunks that cross an edge are gathered with clamped scalar loads.
+// FP32 chunks land in s directly; binary16 chunks land in the staging area
+// `s16` and are widened into s afterwards.  Ends with a barrier.
 template <typename T, int SH, int SW, int NT>
 __device__ __forceinline__ void stage_tile(const T *__restrict__ src, int h, int w, int y0, int x0,
-                                           bool vec_ok, float *__restrict__ s) {
+                                           bool vec_ok, float *__restrict__ s, T *__restrict__ s16) {
     constexpr int V = Io<T>::VEC;
     constexpr int CPR = SW / V;
+    constexpr bool F16 = sizeof(T) == 2;
     for (int idx = threadIdx.x; idx < SH * CPR; idx += NT) {
         const int r = idx / CPR;
         const int q = idx - r * CPR;
         const int gr = clampi(y0 + r, 0, h - 1);
         const int gc = x0 + q * V;
         const T *row = src + (size_t)gr * (size_t)w;
-        float v[V];
         if (vec_ok && gc >= 0 && gc + V <= w) {
-            Io<T>::ld16(row + gc, v);
+            if (F16)
+                cp_async16(s16 + r * SW + q * V, row + gc);
+            else
+                cp_async16(s + r * SW + q * V, row + gc);
+        } else if (F16) {
+            T *d16 = s16 + r * SW + q * V;  // raw binary16 values, widened below
+#pragma unroll
+            for (int e = 0; e < V; ++e) d16[e] = row[clampi(gc + e, 0, w - 1)];
         } else {
+            float v[V];
 #pragma unroll
             for (int e = 0; e < V; ++e) v[e] = Io<T>::ld(row + clampi(gc + e, 0, w - 1));
-        }
-        float *d = s + r * SW + q * V;
+            float *d = s + r * SW + q * V;
 #pragma unroll
-        for (int e = 0; e < V; e += 4)
-            *reinterpret_cast<float4 *>(d + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+            for (int e = 0; e < V; e += 4)
+                *reinterpret_cast<float4 *>(d + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+        }
     }
+    cp_async_commit();
+    cp_async_wait_all();
+    if (F16) {
+        __syncthreads();
+        // widen the staged binary16 tile (exact) into the FP32 tile
+        for (int idx = threadIdx.x; idx < SH * CPR; idx += NT) {
+            float v[V];
+            Io<T>::ld16s(s16 + idx * V, v);
+            float *d = s + idx * V;
+#pragma unroll
+            for (int e = 0; e < V; e += 4)
+                *reinterpret_cast<float4 *>(d + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+        }
+    }
+    __syncthreads();
 }
 
 // Write a thread's R x 4 block (rows y, cols x..x+3), bounds-checked.
@@ -130,7 +166,9 @@ struct DirectCfg {
     static constexpr int SH = TH + KH - 1;
     static constexpr int KWP = round_up(KW, 4);    // filter row padded to LDS.128
     static constexpr int NX = round_up(P - AW + C + KW - 1, 4);
-    static constexpr size_t smem = sizeof(float) * (size_t)(SH * SW + KH * KWP);
+    static constexpr size_t smem_f32 = sizeof(float) * (size_t)(SH * SW + KH * KWP);
+    // binary16 staging area appended for FP16 images
+    static constexpr size_t smem(size_t esz) { return smem_f32 + (esz == 2 ? 2 * (size_t)SH * SW : 0); }
 };
 
 template <typename T, int KH, int KW, int TX, int TY, int R>
@@ -143,6 +181,7 @@ __global__ void __launch_bounds__(TX *TY)
     extern __shared__ __align__(16) float smem[];
     float *s_in = smem;
     float *s_k = smem + SH * SW;
+    T *s16 = reinterpret_cast<T *>(smem + SH * SW + KH * KWP);
 
     const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
     const T *src = in + plane;
@@ -154,8 +193,7 @@ __global__ void __launch_bounds__(TX *TY)
         const int a = t / KWP, b = t - a * KWP;
         s_k[t] = b < KW ? __ldg(k + a * KW + b) : 0.0f;
     }
-    stage_tile<T, SH, SW, Cfg::NT>(src, h, w, y0 - AH, x0 - P, vec_ok, s_in);
-    __syncthreads();
+    stage_tile<T, SH, SW, Cfg::NT>(src, h, w, y0 - AH, x0 - P, vec_ok, s_in, s16);
 
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const float *srow = s_in + (ty * R) * SW + tx * C;
@@ -235,7 +273,8 @@ struct SepCfg {
     static constexpr int SW = TW + 2 * P;
     static constexpr int SH = TH + KY - 1;
     static constexpr int NX = round_up(P - AX + C + KX - 1, 4);
-    static constexpr size_t smem = sizeof(float) * (size_t)(SH * SW + SH * TW);
+    static constexpr size_t smem_f32 = sizeof(float) * (size_t)(SH * SW + SH * TW);
+    static constexpr size_t smem(size_t esz) { return smem_f32 + (esz == 2 ? 2 * (size_t)SH * SW : 0); }
 };
 
 template <typename T, int KX, int KY, int TX, int TY, int R>
@@ -248,6 +287,7 @@ __global__ void __launch_bounds__(TX *TY)
     extern __shared__ __align__(16) float smem[];
     float *s_in = smem;
     float *s_t = smem + SH * SW;
+    T *s16 = reinterpret_cast<T *>(smem + SH * SW + SH * TW);
 
     float fx[KX], fy[KY];
 #pragma unroll
@@ -260,8 +300,7 @@ __global__ void __launch_bounds__(TX *TY)
     T *dst = out + plane;
     const int x0 = blockIdx.x * TW;
     const int y0 = blockIdx.y * Cfg::TH;
-    stage_tile<T, SH, SW, Cfg::NT>(src, h, w, y0 - AY, x0 - P, vec_ok, s_in);
-    __syncthreads();
+    stage_tile<T, SH, SW, Cfg::NT>(src, h, w, y0 - AY, x0 - P, vec_ok, s_in, s16);
 
     // row pass: t[r][q*C + c] = sum_b gx[b] * in[r][q*C + c + b - AX]
     constexpr int QPR = TW / C;
@@ -354,10 +393,11 @@ cudaError_t run_direct(int c, int h, int w, const T *in, const float *k, T *out,
                        cudaStream_t s) {
     using Cfg = DirectCfg<K, K, TX, TY, R>;
     auto kern = conv2d_direct_kernel<T, K, K, TX, TY, R>;
-    cudaError_t e = set_smem(kern, Cfg::smem);
+    const size_t smem = Cfg::smem(sizeof(T));
+    cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((w + Cfg::TW - 1) / Cfg::TW, (h + Cfg::TH - 1) / Cfg::TH, c);
-    kern<<<grid, Cfg::NT, Cfg::smem, s>>>(in, k, out, h, w, vec_ok);
+    kern<<<grid, Cfg::NT, smem, s>>>(in, k, out, h, w, vec_ok);
     return cudaGetLastError();
 }
 
@@ -390,10 +430,11 @@ cudaError_t run_sep(int c, int h, int w, const T *in, const float *gx, const flo
                     bool vec_ok, cudaStream_t s) {
     using Cfg = SepCfg<K, K, TX, TY, R>;
     auto kern = conv2d_sep_kernel<T, K, K, TX, TY, R>;
-    cudaError_t e = set_smem(kern, Cfg::smem);
+    const size_t smem = Cfg::smem(sizeof(T));
+    cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((w + Cfg::TW - 1) / Cfg::TW, (h + Cfg::TH - 1) / Cfg::TH, c);
-    kern<<<grid, Cfg::NT, Cfg::smem, s>>>(in, gx, gy, out, h, w, vec_ok);
+    kern<<<grid, Cfg::NT, smem, s>>>(in, gx, gy, out, h, w, vec_ok);
     return cudaGetLastError();
 }
 
@@ -405,10 +446,10 @@ cudaError_t run_sep_any(int c, int h, int w, const T *in, int kx, const float *g
             case 3: return run_sep<T, 3, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
             case 5: return run_sep<T, 5, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
             case 7: return run_sep<T, 7, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
-            case 9: return run_sep<T, 9, 32, 4, 8>(c, h, w, in, gx, gy, out, vec_ok, s);
-            case 11: return run_sep<T, 11, 32, 4, 8>(c, h, w, in, gx, gy, out, vec_ok, s);
-            case 13: return run_sep<T, 13, 32, 4, 8>(c, h, w, in, gx, gy, out, vec_ok, s);
-            case 15: return run_sep<T, 15, 32, 4, 8>(c, h, w, in, gx, gy, out, vec_ok, s);
+            case 9: return run_sep<T, 9, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
+            case 11: return run_sep<T, 11, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
+            case 13: return run_sep<T, 13, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
+            case 15: return run_sep<T, 15, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
             default: break;
         }
     }

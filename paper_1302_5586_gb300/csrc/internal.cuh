@@ -22,6 +22,16 @@ int cuda_fail(cudaError_t e);
 // Round x up to a multiple of a (a > 0).
 __host__ __device__ constexpr int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
+// ------------------------------------------------------- async copies
+// 16-byte global -> shared copy that bypasses registers and L1
+// (cp.async.cg); both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // ----------------------------------------------------------------- conv2d
 // All launchers queue work on `s` and return the launch status.
 // Arrays are device memory; the host layer has validated sizes and pointers.

@@ -23,6 +23,9 @@
 // scalar kernel with the same arithmetic.
 #include <math.h>
 
+#include <algorithm>
+#include <utility>
+
 #include "internal.cuh"
 
 namespace pencil {
@@ -59,6 +62,24 @@ __device__ __forceinline__ void block_sum_store(double d, double *dst) {
         for (int k = 1; k < JT / 32; ++k) t += wsum[k];
         *dst = t;
     }
+}
+
+// Sum one double per thread over an NT-thread block in a fixed order; thread 0
+// writes it.  Ends with a barrier, so it can be called repeatedly.
+template <int NT>
+__device__ __forceinline__ void block_sum_store_n(double d, double *dst) {
+    __shared__ double wsum[NT / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(FULL, d, off);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = wsum[0];
+#pragma unroll
+        for (int k = 1; k < NT / 32; ++k) t += wsum[k];
+        *dst = t;
+    }
+    __syncthreads();
 }
 
 template <bool RESID, bool STORE>
@@ -161,6 +182,130 @@ __global__ void __launch_bounds__(256) residual_finish_kernel(const double *__re
     }
 }
 
+// ------------------------------------------------------ temporal tiling
+// T sweeps per HBM round trip.  A CTA stages a (BH+2T) x 136 window of the
+// iterate in shared memory (twice: ping-pong buffers), runs up to T sweeps
+// over the whole window, and writes back the BH x BW core, which is still
+// exact after T sweeps because stale data at the window's edge moves inward
+// by one point per sweep.  Each warp owns RS rows; lane l owns the float4
+// column chunk [4+4l, 8+4l), with left/right neighbours from adjacent lanes.
+// Per point the update is the same FP32 expression as the one-sweep kernel,
+// so the iterate is the same bits for every T.  Residuals of iterates that
+// fall inside the pass are accumulated from the staged values of the core.
+template <int T>
+struct TileCfg {
+    static constexpr int NT = 256;
+    static constexpr int WARPS = NT / 32;
+    static constexpr int SWP = 136;                 // 4 + 32 chunks * 4 + 4
+    static constexpr int P = round_up(T + 3, 4);    // core starts at column P
+    static constexpr int BW = SWP - 2 * P;          // core width
+    static constexpr int RS = (64 + 2 * T - 2 + WARPS - 1) / WARPS;
+    static constexpr int BH = WARPS * RS - 2 * T + 2;  // core height
+    static constexpr int SH = BH + 2 * T;           // staged rows
+    static constexpr size_t smem = 2 * (size_t)SH * SWP * sizeof(float);
+};
+
+template <int T>
+__global__ void __launch_bounds__(256)
+    jacobi_tiled_kernel(const float *__restrict__ u, float *__restrict__ v, int h, int w,
+                        int nsweeps, int iter0, int check_every, double *__restrict__ partials,
+                        int nblk) {
+    using Cfg = TileCfg<T>;
+    constexpr int SWP = Cfg::SWP, SH = Cfg::SH, P = Cfg::P, BW = Cfg::BW, BH = Cfg::BH,
+                  RS = Cfg::RS;
+    extern __shared__ __align__(16) float smem[];
+    float *A = smem;
+    float *B = smem + SH * SWP;
+    const int gy0 = blockIdx.y * BH - T;  // global row of staged row 0
+    const int gx0 = blockIdx.x * BW - P;  // global column of staged column 0 (multiple of 4)
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+
+    // stage the window into A with cp.async (out-of-grid chunks are 0); B is
+    // fully rewritten on its compute region every sweep, so only its border
+    // (rows 0 and SH-1, columns 0-3 and 132-135) is set, to 0: stale values
+    // there move inward one point per sweep and never reach the core
+    for (int idx = threadIdx.x; idx < SH * (SWP / 4); idx += Cfg::NT) {
+        const int r = idx / (SWP / 4), q = idx - r * (SWP / 4);
+        const int gr = gy0 + r, gc = gx0 + 4 * q;
+        float *dst = A + r * SWP + 4 * q;
+        if (gr >= 0 && gr < h && gc >= 0 && gc < w)
+            cp_async16(dst, u + (size_t)gr * w + gc);
+        else
+            *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r == 0 || r == SH - 1 || q == 0 || q == SWP / 4 - 1)
+            *reinterpret_cast<float4 *>(B + r * SWP + 4 * q) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int c0 = 4 + 4 * lane;  // this lane's chunk
+    bool cint[4], ccore[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int gc = gx0 + c0 + e;
+        cint[e] = gc >= 1 && gc <= w - 2;
+        ccore[e] = cint[e] && (c0 + e) >= P && (c0 + e) < P + BW;
+    }
+    const int rbeg = 1 + wp * RS;
+    int slot = 0;
+    for (int t = 0; t < nsweeps; ++t) {
+        const int it = iter0 + t;
+        const bool resid = check_every > 0 && it > 0 && (it % check_every) == 0;
+        float hi = 0.f, lo = 0.f;
+        float4 up = *reinterpret_cast<const float4 *>(A + (rbeg - 1) * SWP + c0);
+        float4 cur = *reinterpret_cast<const float4 *>(A + rbeg * SWP + c0);
+#pragma unroll 3
+        for (int rr = 0; rr < RS; ++rr) {
+            const int r = rbeg + rr;
+            const float4 dn = *reinterpret_cast<const float4 *>(A + (r + 1) * SWP + c0);
+            float lf = __shfl_up_sync(FULL, cur.w, 1);
+            float rt = __shfl_down_sync(FULL, cur.x, 1);
+            if (lane == 0) lf = A[r * SWP + 3];
+            if (lane == 31) rt = A[r * SWP + 132];
+            const int gr = gy0 + r;
+            const bool rint = gr >= 1 && gr <= h - 2;
+            const float sx = nsum(up.x, dn.x, lf, cur.y);
+            const float sy = nsum(up.y, dn.y, cur.x, cur.z);
+            const float sz = nsum(up.z, dn.z, cur.y, cur.w);
+            const float sw = nsum(up.w, dn.w, cur.z, rt);
+            float4 n;
+            n.x = (rint && cint[0]) ? __fmul_rn(0.25f, sx) : cur.x;
+            n.y = (rint && cint[1]) ? __fmul_rn(0.25f, sy) : cur.y;
+            n.z = (rint && cint[2]) ? __fmul_rn(0.25f, sz) : cur.z;
+            n.w = (rint && cint[3]) ? __fmul_rn(0.25f, sw) : cur.w;
+            *reinterpret_cast<float4 *>(B + r * SWP + c0) = n;
+            if (resid && rint && r >= T && r < T + BH) {
+                if (ccore[0]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.x), sx), hi, lo);
+                if (ccore[1]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.y), sy), hi, lo);
+                if (ccore[2]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.z), sz), hi, lo);
+                if (ccore[3]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.w), sw), hi, lo);
+            }
+            up = cur;
+            cur = dn;
+        }
+        if (resid) {  // uniform across the block
+            block_sum_store_n<Cfg::NT>((double)hi + (double)lo, partials + (size_t)slot * nblk + bid);
+            ++slot;
+        }
+        __syncthreads();
+        float *tmp = A;
+        A = B;
+        B = tmp;
+    }
+
+    // write the core back
+    constexpr int CQ = BW / 4;
+    for (int idx = threadIdx.x; idx < BH * CQ; idx += Cfg::NT) {
+        const int r = idx / CQ, q = idx - r * CQ;
+        const int gr = blockIdx.y * BH + r, gc = blockIdx.x * BW + 4 * q;
+        if (gr < h && gc < w)
+            *reinterpret_cast<float4 *>(v + (size_t)gr * w + gc) =
+                *reinterpret_cast<const float4 *>(A + (T + r) * SWP + P + 4 * q);
+    }
+}
+
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct Plan {
@@ -188,9 +333,61 @@ cudaError_t sweep(const Plan &p, const float *u, float *v, int h, int w, double 
     return cudaGetLastError();
 }
 
-cudaError_t finish(const Plan &p, const double *partials, double *res, cudaStream_t s) {
-    residual_finish_kernel<<<1, 256, 0, s>>>(partials, p.nblocks, res);
+cudaError_t finish(const double *partials, int n, double *res, cudaStream_t s) {
+    residual_finish_kernel<<<1, 256, 0, s>>>(partials, n, res);
     return cudaGetLastError();
+}
+
+template <int T>
+int tiled_nblk(int h, int w) {
+    using Cfg = TileCfg<T>;
+    return ((w + Cfg::BW - 1) / Cfg::BW) * ((h + Cfg::BH - 1) / Cfg::BH);
+}
+
+// Partials capacity for every supported T (T slots per pass at most).
+size_t tiled_partials(int h, int w) {
+    size_t m = 0;
+    m = std::max(m, (size_t)tiled_nblk<2>(h, w) * 2);
+    m = std::max(m, (size_t)tiled_nblk<4>(h, w) * 4);
+    m = std::max(m, (size_t)tiled_nblk<5>(h, w) * 5);
+    m = std::max(m, (size_t)tiled_nblk<8>(h, w) * 8);
+    m = std::max(m, (size_t)tiled_nblk<10>(h, w) * 10);
+    return m;
+}
+
+// Sweeps `iters` times from u (ping-pong with v) using T-sweep passes of at
+// most `per_pass` sweeps; residuals of checkpoint iterates inside a pass go
+// to res.  Returns the buffer holding the final iterate through *final.
+template <int T>
+cudaError_t run_tiled(int h, int w, float *u, float *v, int iters, int per_pass, int ce,
+                      double *res, double *partials, cudaStream_t s, float **final) {
+    using Cfg = TileCfg<T>;
+    auto kern = jacobi_tiled_kernel<T>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg::smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((w + Cfg::BW - 1) / Cfg::BW, (h + Cfg::BH - 1) / Cfg::BH);
+    const int nblk = (int)(grid.x * grid.y);
+    float *cur = u, *nxt = v;
+    for (int iter = 0; iter < iters;) {
+        const int n = std::min(per_pass, iters - iter);
+        kern<<<grid, Cfg::NT, Cfg::smem, s>>>(cur, nxt, h, w, n, iter, ce, partials, nblk);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        int slot = 0;
+        for (int t = 0; t < n; ++t) {
+            const int it = iter + t;
+            if (ce > 0 && it > 0 && it % ce == 0) {
+                e = finish(partials + (size_t)slot * nblk, nblk, res + (it / ce - 1), s);
+                if (e != cudaSuccess) return e;
+                ++slot;
+            }
+        }
+        std::swap(cur, nxt);
+        iter += n;
+    }
+    *final = cur;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -198,7 +395,7 @@ cudaError_t finish(const Plan &p, const double *partials, double *res, cudaStrea
 size_t jacobi_workspace_bytes(int h, int w) {
     const size_t grid = align256(sizeof(float) * (size_t)h * (size_t)w);
     const size_t nb = (size_t)((w + JT - 1) / JT) * (size_t)((h + JR - 1) / JR);
-    return grid + align256(sizeof(double) * nb);
+    return grid + align256(sizeof(double) * std::max(nb, tiled_partials(h, w)));
 }
 
 static double *partials_of(void *ws, int h, int w) {
@@ -206,10 +403,16 @@ static double *partials_of(void *ws, int h, int w) {
                                       align256(sizeof(float) * (size_t)h * (size_t)w));
 }
 
+// Sweeps per pass actually used for a request (0 = library choice).
+static int choose_t(int temporal_t, bool vec) {
+    if (!vec) return 1;
+    if (temporal_t == 0) return 5;
+    return std::min(temporal_t, 10);
+}
+
 cudaError_t jacobi_run(int h, int w, float *u, int iters, int check_every, double *res, void *ws,
                        size_t ws_bytes, int temporal_t, cudaStream_t s) {
     (void)ws_bytes;
-    (void)temporal_t;
     const int nres = (check_every > 0) ? iters / check_every : 0;
     if (h < 3 || w < 3 || iters == 0) {
         if (nres > 0) return cudaMemsetAsync(res, 0, sizeof(double) * (size_t)nres, s);
@@ -218,25 +421,35 @@ cudaError_t jacobi_run(int h, int w, float *u, int iters, int check_every, doubl
     float *v = static_cast<float *>(ws);
     double *partials = partials_of(ws, h, w);
     const Plan p = make_plan(h, w, u, v);
-    float *cur = u, *nxt = v;
+    const int t = choose_t(temporal_t, p.vec);
+    float *cur = u;
     cudaError_t e = cudaSuccess;
-    for (int k = 1; k <= iters; ++k) {
-        const int prev = k - 1;  // iterate index held in cur
-        const bool want = check_every > 0 && prev > 0 && prev % check_every == 0;
-        if (want) {
-            e = sweep<true, true>(p, cur, nxt, h, w, partials, s);
-            if (e == cudaSuccess) e = finish(p, partials, res + (prev / check_every - 1), s);
-        } else {
-            e = sweep<false, true>(p, cur, nxt, h, w, partials, s);
-        }
+    if (t >= 2) {
+        if (t == 2) e = run_tiled<2>(h, w, u, v, iters, t, check_every, res, partials, s, &cur);
+        else if (t <= 4) e = run_tiled<4>(h, w, u, v, iters, t, check_every, res, partials, s, &cur);
+        else if (t == 5) e = run_tiled<5>(h, w, u, v, iters, t, check_every, res, partials, s, &cur);
+        else if (t <= 8) e = run_tiled<8>(h, w, u, v, iters, t, check_every, res, partials, s, &cur);
+        else e = run_tiled<10>(h, w, u, v, iters, t, check_every, res, partials, s, &cur);
         if (e != cudaSuccess) return e;
-        float *t = cur;
-        cur = nxt;
-        nxt = t;
+    } else {
+        float *nxt = v;
+        for (int k = 1; k <= iters; ++k) {
+            const int prev = k - 1;  // iterate index held in cur
+            const bool want = check_every > 0 && prev > 0 && prev % check_every == 0;
+            if (want) {
+                e = sweep<true, true>(p, cur, nxt, h, w, partials, s);
+                if (e == cudaSuccess) e = finish(partials, p.nblocks, res + (prev / check_every - 1), s);
+            } else {
+                e = sweep<false, true>(p, cur, nxt, h, w, partials, s);
+            }
+            if (e != cudaSuccess) return e;
+            std::swap(cur, nxt);
+        }
     }
     if (check_every > 0 && iters % check_every == 0) {
-        e = sweep<true, false>(p, cur, nullptr, h, w, partials, s);
-        if (e == cudaSuccess) e = finish(p, partials, res + (nres - 1), s);
+        const Plan q = make_plan(h, w, cur, nullptr);
+        e = sweep<true, false>(q, cur, nullptr, h, w, partials, s);
+        if (e == cudaSuccess) e = finish(partials, q.nblocks, res + (nres - 1), s);
         if (e != cudaSuccess) return e;
     }
     if (cur != u)
@@ -249,7 +462,7 @@ cudaError_t residual_run(int h, int w, const float *u, double *res, void *ws, cu
     double *partials = partials_of(ws, h, w);
     const Plan p = make_plan(h, w, u, nullptr);
     cudaError_t e = sweep<true, false>(p, u, nullptr, h, w, partials, s);
-    if (e == cudaSuccess) e = finish(p, partials, res, s);
+    if (e == cudaSuccess) e = finish(partials, p.nblocks, res, s);
     return e;
 }
 
