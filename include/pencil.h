@@ -148,6 +148,33 @@ int pencil_jacobi2d_ex(int h, int w, float *u, int iters, int check_every, doubl
 int pencil_residual2d(int h, int w, const float *u, double *res_out, void *workspace,
                       size_t ws_bytes, void *stream);
 
+/* Size of the static scratch array behind pencil_jacobi2d_noalloc: one
+ * 2048 x 2048 FP32 grid (16 MiB) plus 1 MiB for residual partials. */
+#define PENCIL_NOALLOC_SCRATCH_BYTES ((size_t)17 << 20)
+
+/* pencil_jacobi2d_ex for callers that cannot allocate device memory.  The
+ * paper has no counterpart to this entry point; it exists for callers such as
+ * a fixed-latency loop that cannot afford the device-wide synchronisation and
+ * milliseconds a cudaMalloc/cudaFree may cost, a process whose framework
+ * allocator has already reserved the device's memory (so a fresh cudaMalloc
+ * fails or fragments it), or code whose rules forbid dynamic allocation after
+ * start-up.  Instead of a workspace argument it uses one static device array
+ * of PENCIL_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds
+ * until the process exits; it never calls cudaMalloc or cudaFree.
+ * Same sweeps, residuals and results as pencil_jacobi2d_ex.  u and res_out
+ * are caller-owned device memory.  The first call on each device looks up
+ * the array's device address (with that device current) and caches it, so
+ * make that first call before any stream capture.  All calls on a device share
+ * the one array, which keeps the previous call's contents (every element a
+ * call reads it has first written, so nothing needs clearing): calls whose
+ * work overlaps on the GPU -- on different streams or from different host
+ * threads without ordering -- race and corrupt each other.
+ * Errors: ARG, NULL, PTR, NOMEM (the grid needs more scratch than
+ * PENCIL_NOALLOC_SCRATCH_BYTES: h*w above about 4.4 million points; every grid
+ * up to 2048 x 2048 fits), CUDA. */
+int pencil_jacobi2d_noalloc(int h, int w, float *u, int iters, int check_every, double *res_out,
+                            int temporal_t, void *stream);
+
 /* ----------------------------------------------------------------- utility */
 
 /* Human-readable text of a pencil_status (static storage). */

@@ -14,6 +14,7 @@ from ._binding import (  # noqa: F401
     PENCIL_F16,
     PENCIL_F32,
     PENCIL_MAX_SPECIALISED_K,
+    PENCIL_NOALLOC_SCRATCH_BYTES,
     PencilError,
     declared_symbols,
     lib,
@@ -23,6 +24,7 @@ from ._binding import (  # noqa: F401
     pencil_conv2d_sep_ex,
     pencil_jacobi2d,
     pencil_jacobi2d_ex,
+    pencil_jacobi2d_noalloc,
     pencil_jacobi2d_workspace_size,
     pencil_last_cuda_error,
     pencil_residual2d,

@@ -61,6 +61,7 @@ def lib():
         "pencil_jacobi2d_workspace_size": (sz, [i, i]),
         "pencil_jacobi2d_ex": (i, [i, i, vp, i, i, d, vp, sz, i, vp]),
         "pencil_residual2d": (i, [i, i, vp, d, vp, sz, vp]),
+        "pencil_jacobi2d_noalloc": (i, [i, i, vp, i, i, d, i, vp]),
         "pencil_strerror": (ctypes.c_char_p, [i]),
         "pencil_version": (i, []),
         "pencil_last_cuda_error": (i, []),
@@ -144,6 +145,14 @@ def pencil_jacobi2d_ex(h, w, u, iters, check_every, res_out, workspace, ws_bytes
 def pencil_residual2d(h, w, u, res_out, workspace, ws_bytes, stream=None):
     _check(lib().pencil_residual2d(h, w, _ptr(u), _ptr(res_out), _ptr(workspace), ws_bytes,
                                    _stream(stream)), "pencil_residual2d")
+
+
+def pencil_jacobi2d_noalloc(h, w, u, iters, check_every, res_out, temporal_t=0, stream=None):
+    _check(lib().pencil_jacobi2d_noalloc(h, w, _ptr(u), iters, check_every, _ptr(res_out), temporal_t,
+                                         _stream(stream)), "pencil_jacobi2d_noalloc")
+
+
+PENCIL_NOALLOC_SCRATCH_BYTES = 17 << 20
 
 
 def pencil_strerror(status: int) -> str:

@@ -24,6 +24,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <utility>
 
 #include "internal.cuh"
@@ -467,3 +468,64 @@ cudaError_t residual_run(int h, int w, const float *u, double *res, void *ws, cu
 }
 
 }  // namespace pencil
+
+// ------------------------------------------------ allocation-free entry point
+// Scratch of pencil_jacobi2d_noalloc: the second grid buffer and the residual
+// partials, laid out exactly as a caller workspace.  In host code the name
+// below is only a stand-in; the device address comes from
+// cudaGetSymbolAddress, looked up once per device with that device current.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PENCIL_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the static scratch on the current device, or the failing
+// CUDA status.
+cudaError_t noalloc_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+bool on_device(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
+extern "C" int pencil_jacobi2d_noalloc(int h, int w, float *u, int iters, int check_every,
+                                       double *res_out, int temporal_t, void *stream) {
+    if (h <= 0 || w <= 0 || iters < 0 || check_every < 0 || temporal_t < 0) return PENCIL_ERR_ARG;
+    if ((int64_t)h * (int64_t)w > ((int64_t)1 << 40)) return PENCIL_ERR_ARG;
+    if (!u) return PENCIL_ERR_NULL;
+    const int nres = check_every > 0 ? iters / check_every : 0;
+    if (nres > 0 && !res_out) return PENCIL_ERR_NULL;
+    const size_t need = pencil::jacobi_workspace_bytes(h, w);
+    if (need > PENCIL_NOALLOC_SCRATCH_BYTES) return PENCIL_ERR_NOMEM;
+    if (!on_device(u) || (nres > 0 && !on_device(res_out))) return PENCIL_ERR_PTR;
+    const uintptr_t ub = (uintptr_t)u, rb = (uintptr_t)res_out;
+    const size_t un = sizeof(float) * (size_t)h * w, rn = sizeof(double) * (size_t)nres;
+    if (nres > 0 && rb < ub + un && ub < rb + rn) return PENCIL_ERR_ALIAS;
+    void *ws = nullptr;
+    cudaError_t e = noalloc_scratch(&ws);
+    if (e != cudaSuccess) return pencil::cuda_fail(e);
+    e = pencil::jacobi_run(h, w, u, iters, check_every, res_out, ws, PENCIL_NOALLOC_SCRATCH_BYTES,
+                           temporal_t, (cudaStream_t)stream);
+    return e == cudaSuccess ? PENCIL_OK : pencil::cuda_fail(e);
+}
