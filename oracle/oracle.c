@@ -3,8 +3,8 @@
  * computes.  TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the
  * benchmark's CPU-baseline leg may load it; the library never does.
  *
- * PENCIL (arXiv:1302.5586) gives a program its sequential meaning (Sec. 2,
- * "sequential semantics"); each function here is that sequential loop nest,
+ * PENCIL (arXiv:1302.5586) defines a program's meaning as that of its
+ * sequential execution (Sec. 2); each function here is that sequential loop nest,
  * written out without blocking, fusion or reordering, accumulated in FP64 from
  * inputs widened exactly.  Loops whose iterations are independent (the
  * `independent` directive of Sec. 2.2.3) run under `omp parallel for`; that
