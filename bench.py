@@ -206,7 +206,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = flops_15 / (k15_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
     traffic = traffic_record("conv2d_direct_f32_15x15_8192x8192x3", "paper_1302_5586_gb300/csrc/conv2d.cu")
-    roofline = {"bound": "alu", "kernel": "conv2d_direct_kernel<float,15,15>", "achieved": round(achieved, 3),
+    roofline = {"bound": "alu", "kernel": "conv2d_direct_kernel<float,15,15,16,8,4,2,3>", "achieved": round(achieved, 3),
                 "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "launch_ms": round(k15_ms, 4), "algorithmic_bytes": 8 * PX_PER_PASS, "traffic": traffic}

@@ -155,29 +155,71 @@ __device__ __forceinline__ void store_block(T *__restrict__ dst, int h, int w, i
 }
 
 // ------------------------------------------------------------ direct kernel
-template <int KH, int KW, int TX, int TY, int R>
+// Tile: TH = TY*R output rows by TW = G*TX*4 columns.  A thread owns R rows and
+// G groups of 4 adjacent columns; group g starts TX*4*g columns after group 0,
+// so the loads of a warp stay contiguous (conflict-free LDS.128) in every group.
+template <int KH, int KW, int TX, int TY, int R, int G>
 struct DirectCfg {
     static constexpr int C = 4;
     static constexpr int AH = KH / 2, AW = KW / 2;
     static constexpr int NT = TX * TY;
-    static constexpr int TW = TX * C, TH = TY * R;
-    static constexpr int P = round_up(AW, 8);      // left halo, 16-byte aligned for f32 and f16
+    static constexpr int GS = TX * C;               // column stride between groups
+    static constexpr int TW = G * GS, TH = TY * R;
+    static constexpr int P = round_up(AW, 8);       // left halo, 16-byte aligned for f32 and f16
     static constexpr int SW = TW + 2 * P;
     static constexpr int SH = TH + KH - 1;
-    static constexpr int KWP = round_up(KW, 4);    // filter row padded to LDS.128
+    static constexpr int KWP = round_up(KW, 4);     // filter row padded to LDS.128
     static constexpr int NX = round_up(P - AW + C + KW - 1, 4);
     static constexpr size_t smem_f32 = sizeof(float) * (size_t)(SH * SW + KH * KWP);
     // binary16 staging area appended for FP16 images
     static constexpr size_t smem(size_t esz) { return smem_f32 + (esz == 2 ? 2 * (size_t)SH * SW : 0); }
 };
 
-template <typename T, int KH, int KW, int TX, int TY, int R>
-__global__ void __launch_bounds__(TX *TY)
+// One staged input row r applied to every output row o that uses it (filter
+// row a = r - o).  CHECK tests a against [0, KH); for a compile-time r the test
+// folds away.
+template <bool CHECK, int R, int G, int GS, int KH, int KW, int KWP, int NX, int B0>
+__device__ __forceinline__ void direct_row(int r, const float *__restrict__ xrow,
+                                           const float *__restrict__ s_k, float (&acc)[R][G * 4]) {
+    float x[G][NX];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int m = 0; m < NX; m += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(xrow + g * GS + m);
+            x[g][m] = v.x; x[g][m + 1] = v.y; x[g][m + 2] = v.z; x[g][m + 3] = v.w;
+        }
+#pragma unroll
+    for (int o = 0; o < R; ++o) {
+        const int a = r - o;
+        if (!CHECK || (a >= 0 && a < KH)) {
+            float kr[KWP];
+#pragma unroll
+            for (int m = 0; m < KWP; m += 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(s_k + a * KWP + m);
+                kr[m] = v.x; kr[m + 1] = v.y; kr[m + 2] = v.z; kr[m + 3] = v.w;
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float sum = __fmul_rn(kr[0], x[g][B0 + c]);
+#pragma unroll
+                    for (int b = 1; b < KW; ++b) sum = __fmaf_rn(kr[b], x[g][B0 + c + b], sum);
+                    acc[o][g * 4 + c] = __fadd_rn(acc[o][g * 4 + c], sum);
+                }
+        }
+    }
+}
+
+template <typename T, int KH, int KW, int TX, int TY, int R, int G, int MINB>
+__global__ void __launch_bounds__(TX *TY, MINB)
     conv2d_direct_kernel(const T *__restrict__ in, const float *__restrict__ k, T *__restrict__ out,
                          int h, int w, bool vec_ok) {
-    using Cfg = DirectCfg<KH, KW, TX, TY, R>;
+    using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
     constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, SH = Cfg::SH, KWP = Cfg::KWP,
-                  NX = Cfg::NX, AW = Cfg::AW, AH = Cfg::AH;
+                  NX = Cfg::NX, AW = Cfg::AW, AH = Cfg::AH, GS = Cfg::GS;
+    constexpr int B0 = P - AW;  // x index of tap 0 for column 0
     extern __shared__ __align__(16) float smem[];
     float *s_in = smem;
     float *s_k = smem + SH * SW;
@@ -198,41 +240,37 @@ __global__ void __launch_bounds__(TX *TY)
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const float *srow = s_in + (ty * R) * SW + tx * C;
 
-    float acc[R][C];
+    float acc[R][G * 4];
 #pragma unroll
     for (int o = 0; o < R; ++o)
 #pragma unroll
-        for (int c = 0; c < C; ++c) acc[o][c] = 0.0f;
+        for (int c = 0; c < G * 4; ++c) acc[o][c] = 0.0f;
 
-#pragma unroll(KH <= 7 ? R + KH - 1 : 1)
-    for (int r = 0; r < R + KH - 1; ++r) {
-        float x[NX];
+    // Rows r < R-1 and r >= KH feed only some output rows: fully unrolled, so
+    // the validity tests are resolved at compile time.  Rows R-1 <= r <= KH-1
+    // feed every output row: that loop has no branches.
+    constexpr int NR = R + KH - 1;
+    constexpr int PRO = (R - 1 < NR) ? R - 1 : NR;
+    constexpr int EPI = (KH > PRO) ? KH : PRO;
 #pragma unroll
-        for (int m = 0; m < NX; m += 4) {
-            const float4 v = *reinterpret_cast<const float4 *>(srow + r * SW + m);
-            x[m] = v.x; x[m + 1] = v.y; x[m + 2] = v.z; x[m + 3] = v.w;
-        }
+    for (int r = 0; r < PRO; ++r)
+        direct_row<true, R, G, GS, KH, KW, KWP, NX, B0>(r, srow + r * SW, s_k, acc);
+#pragma unroll 1
+    for (int r = PRO; r < EPI; ++r)
+        direct_row<false, R, G, GS, KH, KW, KWP, NX, B0>(r, srow + r * SW, s_k, acc);
 #pragma unroll
-        for (int o = 0; o < R; ++o) {
-            const int a = r - o;
-            if (a >= 0 && a < KH) {
-                float kr[KWP];
+    for (int r = EPI; r < NR; ++r)
+        direct_row<true, R, G, GS, KH, KW, KWP, NX, B0>(r, srow + r * SW, s_k, acc);
+
 #pragma unroll
-                for (int m = 0; m < KWP; m += 4) {
-                    const float4 v = *reinterpret_cast<const float4 *>(s_k + a * KWP + m);
-                    kr[m] = v.x; kr[m + 1] = v.y; kr[m + 2] = v.z; kr[m + 3] = v.w;
-                }
+    for (int g = 0; g < G; ++g) {
+        float blk[R][4];
 #pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    float s = __fmul_rn(kr[0], x[P - AW + c]);
+        for (int o = 0; o < R; ++o)
 #pragma unroll
-                    for (int b = 1; b < KW; ++b) s = __fmaf_rn(kr[b], x[P - AW + c + b], s);
-                    acc[o][c] = __fadd_rn(acc[o][c], s);
-                }
-            }
-        }
+            for (int c = 0; c < 4; ++c) blk[o][c] = acc[o][g * 4 + c];
+        store_block<T, R>(dst, h, w, y0 + ty * R, x0 + g * GS + tx * C, vec_ok, blk);
     }
-    store_block<T, R>(dst, h, w, y0 + ty * R, x0 + tx * C, vec_ok, acc);
 }
 
 // ------------------------------------------------------------ generic kernel
@@ -277,8 +315,8 @@ struct SepCfg {
     static constexpr size_t smem(size_t esz) { return smem_f32 + (esz == 2 ? 2 * (size_t)SH * SW : 0); }
 };
 
-template <typename T, int KX, int KY, int TX, int TY, int R>
-__global__ void __launch_bounds__(TX *TY)
+template <typename T, int KX, int KY, int TX, int TY, int R, int MINB = 1>
+__global__ void __launch_bounds__(TX *TY, MINB)
     conv2d_sep_kernel(const T *__restrict__ in, const float *__restrict__ gx,
                       const float *__restrict__ gy, T *__restrict__ out, int h, int w, bool vec_ok) {
     using Cfg = SepCfg<KX, KY, TX, TY, R>;
@@ -388,11 +426,11 @@ cudaError_t set_smem(Kern kern, size_t bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename T, int K, int TX, int TY, int R>
+template <typename T, int K, int TX, int TY, int R, int G = 1, int MINB = 1>
 cudaError_t run_direct(int c, int h, int w, const T *in, const float *k, T *out, bool vec_ok,
                        cudaStream_t s) {
-    using Cfg = DirectCfg<K, K, TX, TY, R>;
-    auto kern = conv2d_direct_kernel<T, K, K, TX, TY, R>;
+    using Cfg = DirectCfg<K, K, TX, TY, R, G>;
+    auto kern = conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB>;
     const size_t smem = Cfg::smem(sizeof(T));
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
@@ -404,15 +442,18 @@ cudaError_t run_direct(int c, int h, int w, const T *in, const float *k, T *out,
 template <typename T>
 cudaError_t run_direct_k(int K, int c, int h, int w, const T *in, const float *k, T *out,
                          bool vec_ok, cudaStream_t s) {
+    // Tile shapes and register caps per side, from timing sweeps on GB300 at
+    // 8192 x 8192 x 3 (small sides: occupancy for HBM streaming; large sides:
+    // two column groups so each filter-row load feeds eight FMA chains).
     switch (K) {
-        case 1: return run_direct<T, 1, 32, 8, 4>(c, h, w, in, k, out, vec_ok, s);
-        case 3: return run_direct<T, 3, 32, 8, 4>(c, h, w, in, k, out, vec_ok, s);
-        case 5: return run_direct<T, 5, 32, 8, 4>(c, h, w, in, k, out, vec_ok, s);
-        case 7: return run_direct<T, 7, 32, 4, 8>(c, h, w, in, k, out, vec_ok, s);
-        case 9: return run_direct<T, 9, 32, 4, 8>(c, h, w, in, k, out, vec_ok, s);
-        case 11: return run_direct<T, 11, 32, 4, 8>(c, h, w, in, k, out, vec_ok, s);
-        case 13: return run_direct<T, 13, 32, 4, 8>(c, h, w, in, k, out, vec_ok, s);
-        case 15: return run_direct<T, 15, 32, 4, 8>(c, h, w, in, k, out, vec_ok, s);
+        case 1: return run_direct<T, 1, 32, 8, 4, 1, 8>(c, h, w, in, k, out, vec_ok, s);
+        case 3: return run_direct<T, 3, 32, 8, 4, 1, 8>(c, h, w, in, k, out, vec_ok, s);
+        case 5: return run_direct<T, 5, 32, 4, 4, 2, 6>(c, h, w, in, k, out, vec_ok, s);
+        case 7: return run_direct<T, 7, 32, 4, 8, 1, 8>(c, h, w, in, k, out, vec_ok, s);
+        case 9: return run_direct<T, 9, 32, 4, 4, 2, 3>(c, h, w, in, k, out, vec_ok, s);
+        case 11: return run_direct<T, 11, 32, 4, 4, 2, 3>(c, h, w, in, k, out, vec_ok, s);
+        case 13: return run_direct<T, 13, 32, 4, 4, 2, 3>(c, h, w, in, k, out, vec_ok, s);
+        case 15: return run_direct<T, 15, 16, 8, 4, 2, 3>(c, h, w, in, k, out, vec_ok, s);
         default: return cudaErrorInvalidValue;
     }
 }
