@@ -304,7 +304,52 @@ def measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g):
             "effective_hbm_frac": round(8 * n * n * 100 / (ms * 1e-3) / 1e9 / hbm, 4)}
     jac["residuals"] = [float(x) for x in res.cpu()]
     out["jacobi_8192x8192_100sweeps"] = jac
+    del u0, u, ws
+    out["batched_512"] = measure_batched(torch, pg, dev, stream)
     return out
+
+
+def measure_batched(torch, pg, dev, stream):
+    """512 uneven images (sides log-uniform in [64, 4096], odd filter sides
+    3..15): one persistent launch per batch (graph replay, autotuned tiles)
+    against one standalone launch per image, FP32 and FP16 storage."""
+    from paper_1302_5586_gb300 import tune
+
+    seed = synth.SEEDS["batch512"]
+    h, w, k = synth.batch_spec(seed, 512, 64, 4096)
+    hbm = (measured_peaks().get("hbm_gbs") or 6800.0) * 1e9
+    fp32 = fp32_peak_tflops() * 1e12
+    px = int(np.sum(h.astype(np.int64) * w))
+    res = {"images": 512, "pixels": px, "mean_flop_per_px": round(float(np.sum(2.0 * k * k * h * w) / px), 1)}
+    for dtype, name, esz in ((pg.PENCIL_F32, "f32", 4), (pg.PENCIL_F16, "f16", 2)):
+        items = []
+        for i in range(512):
+            img = synth.image_f32(seed + 17 * i, 1, int(h[i]), int(w[i]))
+            t = torch.from_numpy(img).to(dev)
+            if dtype == pg.PENCIL_F16:
+                t = t.half()
+            kk = torch.from_numpy(synth.filter_f32(seed + 17 * i + 1, int(k[i]), int(k[i]))).to(dev)
+            items.append((t, torch.empty_like(t), kk, int(h[i]), int(w[i]), int(k[i])))
+        plan = pg.pencil_batch_create(dtype, 512, 1 << 22)
+        with torch.cuda.stream(stream):
+            chosen = tune.autotune(plan, dtype, items, reps=3)
+            imgs = pg.make_images(items)
+            ms_b = _time_stream(torch, stream, lambda: pg.pencil_batch_run(plan, imgs, stream.cuda_stream), 5)
+
+            def per_image():
+                for it in items:
+                    pg.pencil_conv2d_ex(1, it[3], it[4], it[0], it[5], it[5], it[2], it[1], dtype, 0,
+                                        stream.cuda_stream)
+            ms_p = _time_stream(torch, stream, per_image, 3)
+        pg.pencil_batch_destroy(plan)
+        # roofline time: per image the larger of its HBM time and FP32 time
+        roof = float(np.sum(np.maximum(2 * esz * h * w / hbm, 2.0 * k * k * h * w / fp32))) * 1e3
+        res[name] = {"batched_ms": round(ms_b, 3), "batched_gpx_s": round(px / ms_b / 1e6, 2),
+                     "per_image_launch_ms": round(ms_p, 3), "per_image_gpx_s": round(px / ms_p / 1e6, 2),
+                     "roofline_ms": round(roof, 3), "frac_of_roofline": round(roof / ms_b, 4),
+                     "variants": {str(a): v for a, (v, _) in chosen.items()}}
+        del items
+    return res
 
 
 def measure_e2e(torch, pg, img, ks, g, steps):

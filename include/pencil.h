@@ -110,6 +110,56 @@ int pencil_conv2d_sep(int h, int w, PENCIL_ARR2(const float, in, h, w), int kx, 
 int pencil_conv2d_sep_ex(int c, int h, int w, const void *in, int kx, const float *gx, int ky,
                          const float *gy, void *out, int dtype, void *stream);
 
+/* ------------------------------------------------------------------- batch
+ * Many images, each with its own size and odd filter side 1..15, convolved in
+ * ONE persistent kernel launch replayed from a CUDA graph.  The tiles of all
+ * images are handed out from one work queue, most expensive first (larger
+ * filter side, then larger image), so uneven images keep every SM busy; each
+ * batched pixel is the same bits as pencil_conv2d_ex on that image alone (the
+ * same fixed per-pixel order).  This is the tuned, launch-once form of the
+ * independent loop over images and pixels (Sec. 2.2.3); the tile shape per
+ * filter side is chosen by measurement (the auto-tuning step of Sec. 2).
+ */
+typedef struct pencil_image {
+    const void *in;   /* h*w elements of the batch dtype, device memory */
+    void *out;        /* h*w elements of the batch dtype, device memory */
+    const float *k;   /* ks*ks FP32 weights, row-major, device memory */
+    int h, w;         /* image size, both > 0 */
+    int ks;           /* odd filter side, 1..15 */
+} pencil_image;
+
+/* A reusable batch plan: device and pinned host tables sized for up to
+ * max_images images and max_tiles tiles, and the captured graph. */
+typedef struct pencil_batch pencil_batch;
+
+/* Tile shapes the batched kernel offers: 0 = 32 x 128, 1 = 16 x 128 outputs. */
+#define PENCIL_BATCH_VARIANTS 2
+
+/* Create a plan for dtype PENCIL_F32 or PENCIL_F16 (allocates; captures the
+ * graph).  All sides start with variant 0.  Errors: NULL, ARG, NOMEM, CUDA. */
+int pencil_batch_create(int dtype, int max_images, long long max_tiles, pencil_batch **out);
+
+/* Tile shape used for images whose filter side is ks (odd 1..15).
+ * Errors: NULL, ARG. */
+int pencil_batch_set_variant(pencil_batch *b, int ks, int variant);
+
+/* Number of tiles n images need with the plan's current variants (host only).
+ * Errors: NULL, ARG. */
+int pencil_batch_tiles(const pencil_batch *b, int n, const pencil_image *imgs, long long *tiles);
+
+/* Stream-ordered: convolve n images (descriptors in host memory, read before
+ * the call returns) with one graph launch on `stream`.  Outputs must not
+ * overlap each other or any input or filter of the batch (PENCIL_ERR_ALIAS).
+ * Image buffers must be device memory (not checked per image).  A plan runs
+ * on one stream at a time; use one plan per stream for concurrent batches.
+ * Errors: NULL, ARG (bad size or side), ALIAS, NOMEM (more images or tiles
+ * than the plan holds), CUDA. */
+int pencil_batch_run(pencil_batch *b, int n, const pencil_image *imgs, void *stream);
+
+/* Wait for the plan's last uploads, then free it.  Call after its last batch
+ * has finished.  NULL is accepted. */
+int pencil_batch_destroy(pencil_batch *b);
+
 /* ------------------------------------------------------------------ jacobi
  * One sweep: v[i][j] = 0.25f * ((u[i-1][j] + u[i+1][j]) + (u[i][j-1] + u[i][j+1]))
  * on the interior 1 <= i <= h-2, 1 <= j <= w-2, in FP32 in exactly that order;
@@ -179,6 +229,10 @@ int pencil_jacobi2d_noalloc(int h, int w, float *u, int iters, int check_every, 
 
 /* Human-readable text of a pencil_status (static storage). */
 const char *pencil_strerror(int status);
+
+/* The current device's name (NUL-terminated, truncated to len), SM count and
+ * CUDA driver version; any output pointer may be NULL.  Errors: CUDA. */
+int pencil_device_info(char *name, int len, int *sm_count, int *driver_version);
 
 /* Library version as major*10000 + minor*100 + patch. */
 int pencil_version(void);

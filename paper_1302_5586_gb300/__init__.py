@@ -10,18 +10,27 @@ Python binding of that ABI plus the batching and serving layers built on it.
 from ._binding import (  # noqa: F401
     HEADER,
     LIB_PATH,
+    PENCIL_BATCH_VARIANTS,
     PENCIL_CONV_GENERIC,
     PENCIL_F16,
     PENCIL_F32,
     PENCIL_MAX_SPECIALISED_K,
     PENCIL_NOALLOC_SCRATCH_BYTES,
     PencilError,
+    PencilImage,
     declared_symbols,
     lib,
+    make_images,
+    pencil_batch_create,
+    pencil_batch_destroy,
+    pencil_batch_run,
+    pencil_batch_set_variant,
+    pencil_batch_tiles,
     pencil_conv2d,
     pencil_conv2d_ex,
     pencil_conv2d_sep,
     pencil_conv2d_sep_ex,
+    pencil_device_info,
     pencil_jacobi2d,
     pencil_jacobi2d_ex,
     pencil_jacobi2d_noalloc,

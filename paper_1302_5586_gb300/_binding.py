@@ -29,6 +29,15 @@ STATUS = {
 }
 
 
+class PencilImage(ctypes.Structure):
+    """struct pencil_image."""
+    _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("k", ctypes.c_void_p),
+                ("h", ctypes.c_int), ("w", ctypes.c_int), ("ks", ctypes.c_int)]
+
+
+PENCIL_BATCH_VARIANTS = 2
+
+
 class PencilError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
@@ -62,6 +71,12 @@ def lib():
         "pencil_jacobi2d_ex": (i, [i, i, vp, i, i, d, vp, sz, i, vp]),
         "pencil_residual2d": (i, [i, i, vp, d, vp, sz, vp]),
         "pencil_jacobi2d_noalloc": (i, [i, i, vp, i, i, d, i, vp]),
+        "pencil_batch_create": (i, [i, i, ctypes.c_longlong, ctypes.POINTER(ctypes.c_void_p)]),
+        "pencil_batch_set_variant": (i, [vp, i, i]),
+        "pencil_batch_tiles": (i, [vp, i, vp, ctypes.POINTER(ctypes.c_longlong)]),
+        "pencil_batch_run": (i, [vp, i, vp, vp]),
+        "pencil_batch_destroy": (i, [vp]),
+        "pencil_device_info": (i, [ctypes.c_char_p, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
         "pencil_strerror": (ctypes.c_char_p, [i]),
         "pencil_version": (i, []),
         "pencil_last_cuda_error": (i, []),
@@ -153,6 +168,47 @@ def pencil_jacobi2d_noalloc(h, w, u, iters, check_every, res_out, temporal_t=0, 
 
 
 PENCIL_NOALLOC_SCRATCH_BYTES = 17 << 20
+
+
+def make_images(items):
+    """A ctypes array of pencil_image from (in, out, k, h, w, ks) tuples."""
+    arr = (PencilImage * len(items))()
+    for j, (i_, o, k, h, w, ks) in enumerate(items):
+        arr[j] = PencilImage(_ptr(i_), _ptr(o), _ptr(k), h, w, ks)
+    return arr
+
+
+def pencil_batch_create(dtype, max_images, max_tiles) -> int:
+    """Returns the plan handle (an integer address)."""
+    out = ctypes.c_void_p()
+    _check(lib().pencil_batch_create(dtype, max_images, max_tiles, ctypes.byref(out)), "pencil_batch_create")
+    return out.value
+
+
+def pencil_batch_set_variant(b, ks, variant):
+    _check(lib().pencil_batch_set_variant(b, ks, variant), "pencil_batch_set_variant")
+
+
+def pencil_batch_tiles(b, imgs) -> int:
+    t = ctypes.c_longlong()
+    _check(lib().pencil_batch_tiles(b, len(imgs), imgs, ctypes.byref(t)), "pencil_batch_tiles")
+    return t.value
+
+
+def pencil_batch_run(b, imgs, stream=None):
+    _check(lib().pencil_batch_run(b, len(imgs), imgs, _stream(stream)), "pencil_batch_run")
+
+
+def pencil_batch_destroy(b):
+    _check(lib().pencil_batch_destroy(b), "pencil_batch_destroy")
+
+
+def pencil_device_info():
+    """(device name, SM count, CUDA driver version) of the current device."""
+    name = ctypes.create_string_buffer(256)
+    sms, drv = ctypes.c_int(), ctypes.c_int()
+    _check(lib().pencil_device_info(name, 256, ctypes.byref(sms), ctypes.byref(drv)), "pencil_device_info")
+    return name.value.decode(), sms.value, drv.value
 
 
 def pencil_strerror(status: int) -> str:

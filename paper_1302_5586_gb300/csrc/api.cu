@@ -105,6 +105,24 @@ const char *pencil_strerror(int status) {
 
 int pencil_version(void) { return 100; }
 
+int pencil_device_info(char *name, int len, int *sm_count, int *driver_version) {
+    int dev = 0;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (name && len > 0) {
+        strncpy(name, prop.name, (size_t)len - 1);
+        name[len - 1] = 0;
+    }
+    if (sm_count) *sm_count = prop.multiProcessorCount;
+    if (driver_version) {
+        e = cudaDriverGetVersion(driver_version);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return PENCIL_OK;
+}
+
 int pencil_last_cuda_error(void) { return g_last_cuda; }
 
 void pencil_shutdown(void) {

@@ -1,0 +1,350 @@
+// batch.cu -- many images, each with its own size and filter side, in one
+// persistent kernel launch replayed from a CUDA graph.
+//
+// The host builds a tile table: images are ordered by cost (filter side,
+// then tile count, descending) so the most expensive tiles start first, and
+// every tile of image i gets the entry i.  The table, the image descriptors
+// and a header {next, total} are copied to a device buffer owned by the plan;
+// the kernel's CTAs (a resident grid: SMs x CTAs per SM) take tile indices
+// from `next` with one atomicAdd per tile (fetched one tile ahead, so its
+// latency overlaps the current tile), look the image up, and run the same
+// tile body as the standalone direct kernel -- so every batched pixel is the
+// same bits as pencil_conv2d_ex on that image alone.  The kernel reads the
+// tile count from the device header, so one captured graph serves every
+// batch the plan runs.
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "conv_tile.cuh"
+
+namespace pencil {
+namespace {
+
+using namespace tile;
+
+struct BatchHeader {
+    int next;   // next tile to hand out
+    int total;  // tiles in this batch
+    int n;      // images
+    int pad;
+};
+
+struct BatchImage {
+    const void *in;
+    void *out;
+    const float *k;
+    int h, w, ks, var;
+    int tiles_x, tile_base;
+    int vec_ok, pad;
+};
+
+constexpr int BT = 128;  // threads per CTA of the batched kernel
+
+// Tile shapes (all 128 threads): variant 0 = 32 x 128, variant 1 = 16 x 128.
+// Sides up to 7 use one 4-column group per thread; larger sides two groups.
+__host__ __device__ constexpr int var_th(int v) { return v == 0 ? 32 : 16; }
+constexpr int kTileW = 128;
+
+template <typename T, int K, int V>
+__device__ __forceinline__ void run_tile(const BatchImage &d, int y0, int x0, float *smem) {
+    const T *in = static_cast<const T *>(d.in);
+    T *out = static_cast<T *>(d.out);
+    if (K <= 7)
+        direct_tile<T, K, K, 32, 4, (V == 0 ? 8 : 4), 1>(in, d.k, out, d.h, d.w, d.vec_ok, y0, x0, smem);
+    else
+        direct_tile<T, K, K, 16, 8, (V == 0 ? 4 : 2), 2>(in, d.k, out, d.h, d.w, d.vec_ok, y0, x0, smem);
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void run_tile_v(const BatchImage &d, int y0, int x0, float *smem) {
+    if (d.var == 0)
+        run_tile<T, K, 0>(d, y0, x0, smem);
+    else
+        run_tile<T, K, 1>(d, y0, x0, smem);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BT, 4)
+    conv2d_batch_kernel(BatchHeader *__restrict__ hdr, const BatchImage *__restrict__ imgs,
+                        const int *__restrict__ tile_img) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ int s_t;
+    const int total = hdr->total;
+    if (threadIdx.x == 0) s_t = atomicAdd(&hdr->next, 1);
+    __syncthreads();
+    int t = s_t;
+    while (t < total) {
+        __syncthreads();  // every thread has read s_t
+        if (threadIdx.x == 0) s_t = atomicAdd(&hdr->next, 1);
+        const BatchImage d = imgs[__ldg(tile_img + t)];
+        const int local = t - d.tile_base;
+        const int ty = local / d.tiles_x, tx = local - ty * d.tiles_x;
+        const int y0 = ty * var_th(d.var), x0 = tx * kTileW;
+        switch (d.ks) {
+            case 1: run_tile_v<T, 1>(d, y0, x0, smem); break;
+            case 3: run_tile_v<T, 3>(d, y0, x0, smem); break;
+            case 5: run_tile_v<T, 5>(d, y0, x0, smem); break;
+            case 7: run_tile_v<T, 7>(d, y0, x0, smem); break;
+            case 9: run_tile_v<T, 9>(d, y0, x0, smem); break;
+            case 11: run_tile_v<T, 11>(d, y0, x0, smem); break;
+            case 13: run_tile_v<T, 13>(d, y0, x0, smem); break;
+            default: run_tile_v<T, 15>(d, y0, x0, smem); break;
+        }
+        __syncthreads();  // tile finished; s_t holds the next index
+        t = s_t;
+    }
+}
+
+// Largest dynamic shared memory any tile body of the batched kernel needs.
+size_t batch_smem(size_t esz) {
+    size_t m = 0;
+    m = std::max(m, DirectCfg<15, 15, 16, 8, 4, 2>::smem(esz));
+    m = std::max(m, DirectCfg<7, 7, 32, 4, 8, 1>::smem(esz));
+    m = std::max(m, DirectCfg<15, 15, 16, 8, 2, 2>::smem(esz));
+    return m;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace pencil
+
+using namespace pencil;
+
+struct pencil_batch {
+    int dtype = PENCIL_F32;
+    int max_images = 0;
+    long long max_tiles = 0;
+    unsigned char var_of_k[16] = {};
+    size_t bytes = 0;          // table bytes (device and each host copy)
+    void *dbuf = nullptr;      // device: header | images | tile table
+    void *hbuf[2] = {nullptr, nullptr};  // pinned host staging (ping-pong)
+    cudaEvent_t uploaded[2] = {nullptr, nullptr};
+    int flip = 0;
+    int grid = 0;
+    size_t smem = 0;
+    cudaGraphExec_t exec = nullptr;
+    std::mutex mu;
+};
+
+namespace {
+
+size_t table_bytes(int max_images, long long max_tiles) {
+    return align256(sizeof(BatchHeader)) + align256(sizeof(BatchImage) * (size_t)max_images) +
+           sizeof(int) * (size_t)max_tiles;
+}
+
+size_t elem_size(int dtype) { return dtype == PENCIL_F16 ? 2 : 4; }
+
+long long tiles_of(const pencil_image &im, int var) {
+    const long long ty = (im.h + var_th(var) - 1) / var_th(var);
+    const long long tx = (im.w + kTileW - 1) / kTileW;
+    return ty * tx;
+}
+
+bool image_ok(const pencil_image &im) {
+    return im.in && im.out && im.k && im.h > 0 && im.w > 0 && im.ks >= 1 && im.ks <= 15 &&
+           (im.ks & 1) && (long long)im.h * im.w <= (1ll << 40);
+}
+
+// Every output range must be disjoint from every other output and every input
+// and filter range (the restrict rule, per image and across the batch).
+bool batch_disjoint(int n, const pencil_image *imgs, size_t esz) {
+    struct R { uintptr_t lo, hi; };
+    std::vector<R> outs(n), ins;
+    ins.reserve(2 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const size_t nb = esz * (size_t)imgs[i].h * imgs[i].w;
+        outs[i] = {(uintptr_t)imgs[i].out, (uintptr_t)imgs[i].out + nb};
+        ins.push_back({(uintptr_t)imgs[i].in, (uintptr_t)imgs[i].in + nb});
+        ins.push_back({(uintptr_t)imgs[i].k, (uintptr_t)imgs[i].k + sizeof(float) * imgs[i].ks * imgs[i].ks});
+    }
+    std::sort(outs.begin(), outs.end(), [](const R &a, const R &b) { return a.lo < b.lo; });
+    for (size_t i = 1; i < outs.size(); ++i)
+        if (outs[i].lo < outs[i - 1].hi) return false;
+    for (const R &r : ins) {
+        // first output starting at or after r.hi cannot overlap; check the one before it
+        auto it = std::lower_bound(outs.begin(), outs.end(), r.hi,
+                                   [](const R &a, uintptr_t v) { return a.lo < v; });
+        if (it != outs.begin() && std::prev(it)->hi > r.lo) return false;
+    }
+    return true;
+}
+
+cudaError_t capture_graph(pencil_batch *b) {
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    BatchHeader *hdr = static_cast<BatchHeader *>(b->dbuf);
+    BatchImage *imgs = reinterpret_cast<BatchImage *>(static_cast<char *>(b->dbuf) + align256(sizeof(BatchHeader)));
+    int *tile_img = reinterpret_cast<int *>(reinterpret_cast<char *>(imgs) +
+                                            align256(sizeof(BatchImage) * (size_t)b->max_images));
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        if (b->dtype == PENCIL_F32)
+            conv2d_batch_kernel<float><<<b->grid, BT, b->smem, cs>>>(hdr, imgs, tile_img);
+        else
+            conv2d_batch_kernel<__half><<<b->grid, BT, b->smem, cs>>>(hdr, imgs, tile_img);
+        cudaError_t le = cudaGetLastError();
+        e = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    return e;
+}
+
+void release(pencil_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (int i = 0; i < 2; ++i) {
+        if (b->uploaded[i]) cudaEventDestroy(b->uploaded[i]);
+        if (b->hbuf[i]) cudaFreeHost(b->hbuf[i]);
+    }
+    if (b->dbuf) cudaFree(b->dbuf);
+}
+
+}  // namespace
+
+extern "C" {
+
+int pencil_batch_create(int dtype, int max_images, long long max_tiles, pencil_batch **out) {
+    if (!out) return PENCIL_ERR_NULL;
+    *out = nullptr;
+    if ((dtype != PENCIL_F32 && dtype != PENCIL_F16) || max_images <= 0 || max_tiles <= 0 ||
+        max_tiles > (1ll << 31) - 1)
+        return PENCIL_ERR_ARG;
+    pencil_batch *b = new (std::nothrow) pencil_batch;
+    if (!b) return PENCIL_ERR_NOMEM;
+    b->dtype = dtype;
+    b->max_images = max_images;
+    b->max_tiles = max_tiles;
+    b->bytes = table_bytes(max_images, max_tiles);
+    b->smem = batch_smem(elem_size(dtype));
+    cudaError_t e = cudaMalloc(&b->dbuf, b->bytes);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaMallocHost(&b->hbuf[i], b->bytes);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) {
+        auto kern = dtype == PENCIL_F32 ? conv2d_batch_kernel<float> : conv2d_batch_kernel<__half>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+        int per_sm = 0, dev = 0, sms = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT, b->smem);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        b->grid = std::max(1, per_sm) * sms;
+    }
+    if (e == cudaSuccess) e = capture_graph(b);
+    if (e != cudaSuccess) {
+        release(b);
+        delete b;
+        return e == cudaErrorMemoryAllocation ? PENCIL_ERR_NOMEM : cuda_fail(e);
+    }
+    *out = b;
+    return PENCIL_OK;
+}
+
+int pencil_batch_set_variant(pencil_batch *b, int ks, int variant) {
+    if (!b) return PENCIL_ERR_NULL;
+    if (ks < 1 || ks > 15 || !(ks & 1) || variant < 0 || variant >= PENCIL_BATCH_VARIANTS)
+        return PENCIL_ERR_ARG;
+    std::lock_guard<std::mutex> lk(b->mu);
+    b->var_of_k[ks] = (unsigned char)variant;
+    return PENCIL_OK;
+}
+
+int pencil_batch_tiles(const pencil_batch *b, int n, const pencil_image *imgs, long long *tiles) {
+    if (!b || !tiles || (n > 0 && !imgs)) return PENCIL_ERR_NULL;
+    if (n < 0) return PENCIL_ERR_ARG;
+    long long t = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!image_ok(imgs[i])) return PENCIL_ERR_ARG;
+        t += tiles_of(imgs[i], b->var_of_k[imgs[i].ks]);
+    }
+    *tiles = t;
+    return PENCIL_OK;
+}
+
+int pencil_batch_run(pencil_batch *b, int n, const pencil_image *imgs, void *stream) {
+    if (!b || (n > 0 && !imgs)) return PENCIL_ERR_NULL;
+    if (n < 0) return PENCIL_ERR_ARG;
+    if (n == 0) return PENCIL_OK;
+    if (n > b->max_images) return PENCIL_ERR_NOMEM;
+    const size_t esz = elem_size(b->dtype);
+    for (int i = 0; i < n; ++i)
+        if (!image_ok(imgs[i])) return PENCIL_ERR_ARG;
+    if (!batch_disjoint(n, imgs, esz)) return PENCIL_ERR_ALIAS;
+    std::lock_guard<std::mutex> lk(b->mu);
+    // cost order: larger filter side first, then more tiles
+    std::vector<int> order(n);
+    std::vector<long long> nt(n);
+    for (int i = 0; i < n; ++i) {
+        order[i] = i;
+        nt[i] = tiles_of(imgs[i], b->var_of_k[imgs[i].ks]);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if (imgs[x].ks != imgs[y].ks) return imgs[x].ks > imgs[y].ks;
+        return nt[x] > nt[y];
+    });
+    long long total = 0;
+    for (int i = 0; i < n; ++i) total += nt[i];
+    if (total > b->max_tiles) return PENCIL_ERR_NOMEM;
+
+    const int slot = b->flip;
+    b->flip ^= 1;
+    cudaError_t e = cudaEventSynchronize(b->uploaded[slot]);  // the copy that last read this staging buffer
+    if (e != cudaSuccess) return cuda_fail(e);
+    char *h = static_cast<char *>(b->hbuf[slot]);
+    BatchHeader *hh = reinterpret_cast<BatchHeader *>(h);
+    BatchImage *hi = reinterpret_cast<BatchImage *>(h + align256(sizeof(BatchHeader)));
+    int *ht = reinterpret_cast<int *>(reinterpret_cast<char *>(hi) + align256(sizeof(BatchImage) * (size_t)b->max_images));
+    const int vec = b->dtype == PENCIL_F16 ? 8 : 4;
+    long long base = 0;
+    for (int j = 0; j < n; ++j) {
+        const pencil_image &im = imgs[order[j]];
+        BatchImage &d = hi[j];
+        d.in = im.in;
+        d.out = im.out;
+        d.k = im.k;
+        d.h = im.h;
+        d.w = im.w;
+        d.ks = im.ks;
+        d.var = b->var_of_k[im.ks];
+        d.tiles_x = (im.w + kTileW - 1) / kTileW;
+        d.tile_base = (int)base;
+        d.vec_ok = (im.w % vec == 0) && ((uintptr_t)im.in % 16 == 0) && ((uintptr_t)im.out % 16 == 0);
+        d.pad = 0;
+        for (long long t = 0; t < nt[order[j]]; ++t) ht[base + t] = j;
+        base += nt[order[j]];
+    }
+    hh->next = 0;
+    hh->total = (int)total;
+    hh->n = n;
+    hh->pad = 0;
+    // copy header + descriptors + the used part of the tile table
+    const size_t head = align256(sizeof(BatchHeader)) + align256(sizeof(BatchImage) * (size_t)b->max_images);
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemcpyAsync(b->dbuf, h, head + sizeof(int) * (size_t)total, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b->uploaded[slot], s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
+    return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
+}
+
+int pencil_batch_destroy(pencil_batch *b) {
+    if (!b) return PENCIL_OK;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2; ++i)
+        if (b->uploaded[i]) {
+            cudaError_t ei = cudaEventSynchronize(b->uploaded[i]);
+            if (e == cudaSuccess) e = ei;
+        }
+    release(b);
+    delete b;
+    return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
+}
+
+}  // extern "C"

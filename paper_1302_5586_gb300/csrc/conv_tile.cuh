@@ -1,0 +1,257 @@
+// conv_tile.cuh -- the shared tile body of the direct conv2d kernels
+// (standalone and batched).  Every caller computes an output pixel with the
+// same FP32 operation order: per filter row a, s = k[a][0]*x0 then
+// s = fma(k[a][b], xb, s) for b = 1..kw-1, and acc = acc + s from acc = +0.
+#pragma once
+
+#include "internal.cuh"
+
+namespace pencil {
+namespace tile {
+
+template <typename T>
+struct Io;
+
+template <>
+struct Io<float> {
+    static constexpr int VEC = 4;  // elements per 16-byte chunk
+    __device__ __forceinline__ static float ld(const float *p) { return __ldg(p); }
+    __device__ __forceinline__ static void ld16(const float *p, float *d) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+    }
+    __device__ __forceinline__ static void st(float *p, float v) { *p = v; }
+    __device__ __forceinline__ static void st4(float *p, const float *v) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    __device__ __forceinline__ static void ld16s(const float *p, float *d) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+    }
+};
+
+template <>
+struct Io<__half> {
+    static constexpr int VEC = 8;
+    __device__ __forceinline__ static float ld(const __half *p) { return __half2float(__ldg(p)); }
+    __device__ __forceinline__ static void ld16(const __half *p, float *d) {
+        unpack(__ldg(reinterpret_cast<const uint4 *>(p)), d);
+    }
+    __device__ __forceinline__ static void ld16s(const __half *p, float *d) {
+        unpack(*reinterpret_cast<const uint4 *>(p), d);
+    }
+    __device__ __forceinline__ static void unpack(const uint4 v, float *d) {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            __half2 hh;
+            memcpy(&hh, &w[q], 4);
+            const float2 f = __half22float2(hh);
+            d[2 * q] = f.x;
+            d[2 * q + 1] = f.y;
+        }
+    }
+    __device__ __forceinline__ static void st(__half *p, float v) { *p = __float2half_rn(v); }
+    __device__ __forceinline__ static void st4(__half *p, const float *v) {
+        const __half2 a = __floats2half2_rn(v[0], v[1]);
+        const __half2 b = __floats2half2_rn(v[2], v[3]);
+        uint2 u;
+        memcpy(&u.x, &a, 4);
+        memcpy(&u.y, &b, 4);
+        *reinterpret_cast<uint2 *>(p) = u;
+    }
+};
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+
+// Stage s[r][c] = in[clamp(y0 + r)][clamp(x0 + c)] for r < SH, c < SW (as FP32).
+// x0 is a multiple of VEC, SW a multiple of VEC.  vec_ok: rows are 16-byte
+// aligned (w % VEC == 0 and the plane base is 16-byte aligned).  Chunks that
+// lie inside the row go through cp.async (all of a CTA's copies in flight at
+// once); chunks that cross an edge are gathered with clamped scalar loads.
+// FP32 chunks land in s directly; binary16 chunks land in the staging area
+// `s16` and are widened into s afterwards.  Ends with a barrier.
+template <typename T, int SH, int SW, int NT>
+__device__ __forceinline__ void stage_tile(const T *__restrict__ src, int h, int w, int y0, int x0,
+                                           bool vec_ok, float *__restrict__ s, T *__restrict__ s16) {
+    constexpr int V = Io<T>::VEC;
+    constexpr int CPR = SW / V;
+    constexpr bool F16 = sizeof(T) == 2;
+    for (int idx = threadIdx.x; idx < SH * CPR; idx += NT) {
+        const int r = idx / CPR;
+        const int q = idx - r * CPR;
+        const int gr = clampi(y0 + r, 0, h - 1);
+        const int gc = x0 + q * V;
+        const T *row = src + (size_t)gr * (size_t)w;
+        if (vec_ok && gc >= 0 && gc + V <= w) {
+            if (F16)
+                cp_async16(s16 + r * SW + q * V, row + gc);
+            else
+                cp_async16(s + r * SW + q * V, row + gc);
+        } else if (F16) {
+            T *d16 = s16 + r * SW + q * V;  // raw binary16 values, widened below
+#pragma unroll
+            for (int e = 0; e < V; ++e) d16[e] = row[clampi(gc + e, 0, w - 1)];
+        } else {
+            float v[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) v[e] = Io<T>::ld(row + clampi(gc + e, 0, w - 1));
+            float *d = s + r * SW + q * V;
+#pragma unroll
+            for (int e = 0; e < V; e += 4)
+                *reinterpret_cast<float4 *>(d + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+        }
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    if (F16) {
+        __syncthreads();
+        // widen the staged binary16 tile (exact) into the FP32 tile
+        for (int idx = threadIdx.x; idx < SH * CPR; idx += NT) {
+            float v[V];
+            Io<T>::ld16s(s16 + idx * V, v);
+            float *d = s + idx * V;
+#pragma unroll
+            for (int e = 0; e < V; e += 4)
+                *reinterpret_cast<float4 *>(d + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+        }
+    }
+    __syncthreads();
+}
+
+// Write a thread's R x 4 block (rows y, cols x..x+3), bounds-checked.
+template <typename T, int R>
+__device__ __forceinline__ void store_block(T *__restrict__ dst, int h, int w, int y, int x,
+                                            bool vec_ok, const float (&acc)[R][4]) {
+#pragma unroll
+    for (int o = 0; o < R; ++o) {
+        const int i = y + o;
+        if (i >= h) break;
+        T *row = dst + (size_t)i * (size_t)w;
+        if (vec_ok && x + 4 <= w) {
+            Io<T>::st4(row + x, acc[o]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (x + c < w) Io<T>::st(row + x + c, acc[o][c]);
+        }
+    }
+}
+
+// ------------------------------------------------------------ direct kernel
+// Tile: TH = TY*R output rows by TW = G*TX*4 columns.  A thread owns R rows and
+// G groups of 4 adjacent columns; group g starts TX*4*g columns after group 0,
+// so the loads of a warp stay contiguous (conflict-free LDS.128) in every group.
+template <int KH, int KW, int TX, int TY, int R, int G>
+struct DirectCfg {
+    static constexpr int C = 4;
+    static constexpr int AH = KH / 2, AW = KW / 2;
+    static constexpr int NT = TX * TY;
+    static constexpr int GS = TX * C;               // column stride between groups
+    static constexpr int TW = G * GS, TH = TY * R;
+    static constexpr int P = round_up(AW, 8);       // left halo, 16-byte aligned for f32 and f16
+    static constexpr int SW = TW + 2 * P;
+    static constexpr int SH = TH + KH - 1;
+    static constexpr int KWP = round_up(KW, 4);     // filter row padded to LDS.128
+    static constexpr int NX = round_up(P - AW + C + KW - 1, 4);
+    static constexpr size_t smem_f32 = sizeof(float) * (size_t)(SH * SW + KH * KWP);
+    // binary16 staging area appended for FP16 images
+    static constexpr size_t smem(size_t esz) { return smem_f32 + (esz == 2 ? 2 * (size_t)SH * SW : 0); }
+};
+
+// One staged input row r applied to every output row o that uses it (filter
+// row a = r - o).  CHECK tests a against [0, KH); for a compile-time r the test
+// folds away.
+template <bool CHECK, int R, int G, int GS, int KH, int KW, int KWP, int NX, int B0>
+__device__ __forceinline__ void direct_row(int r, const float *__restrict__ xrow,
+                                           const float *__restrict__ s_k, float (&acc)[R][G * 4]) {
+    float x[G][NX];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int m = 0; m < NX; m += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(xrow + g * GS + m);
+            x[g][m] = v.x; x[g][m + 1] = v.y; x[g][m + 2] = v.z; x[g][m + 3] = v.w;
+        }
+#pragma unroll
+    for (int o = 0; o < R; ++o) {
+        const int a = r - o;
+        if (!CHECK || (a >= 0 && a < KH)) {
+            float kr[KWP];
+#pragma unroll
+            for (int m = 0; m < KWP; m += 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(s_k + a * KWP + m);
+                kr[m] = v.x; kr[m + 1] = v.y; kr[m + 2] = v.z; kr[m + 3] = v.w;
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float sum = __fmul_rn(kr[0], x[g][B0 + c]);
+#pragma unroll
+                    for (int b = 1; b < KW; ++b) sum = __fmaf_rn(kr[b], x[g][B0 + c + b], sum);
+                    acc[o][g * 4 + c] = __fadd_rn(acc[o][g * 4 + c], sum);
+                }
+        }
+    }
+}
+
+// One TH x TW output tile with origin (y0, x0) of one plane: stage, compute,
+// store.  Called by every thread of an NT-thread block (it contains barriers);
+// `smem` must hold DirectCfg::smem(sizeof(T)) bytes.
+template <typename T, int KH, int KW, int TX, int TY, int R, int G>
+__device__ __forceinline__ void direct_tile(const T *__restrict__ src, const float *__restrict__ k,
+                                            T *__restrict__ dst, int h, int w, bool vec_ok, int y0,
+                                            int x0, float *__restrict__ smem) {
+    using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
+    constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, SH = Cfg::SH, KWP = Cfg::KWP,
+                  NX = Cfg::NX, AW = Cfg::AW, AH = Cfg::AH, GS = Cfg::GS;
+    constexpr int B0 = P - AW;  // x index of tap 0 for column 0
+    float *s_in = smem;
+    float *s_k = smem + SH * SW;
+    T *s16 = reinterpret_cast<T *>(smem + SH * SW + KH * KWP);
+
+    for (int t = threadIdx.x; t < KH * KWP; t += Cfg::NT) {
+        const int a = t / KWP, b = t - a * KWP;
+        s_k[t] = b < KW ? __ldg(k + a * KW + b) : 0.0f;
+    }
+    stage_tile<T, SH, SW, Cfg::NT>(src, h, w, y0 - AH, x0 - P, vec_ok, s_in, s16);
+
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const float *srow = s_in + (ty * R) * SW + tx * C;
+
+    float acc[R][G * 4];
+#pragma unroll
+    for (int o = 0; o < R; ++o)
+#pragma unroll
+        for (int c = 0; c < G * 4; ++c) acc[o][c] = 0.0f;
+
+    // Rows r < R-1 and r >= KH feed only some output rows: fully unrolled, so
+    // the validity tests are resolved at compile time.  Rows R-1 <= r <= KH-1
+    // feed every output row: that loop has no branches.
+    constexpr int NR = R + KH - 1;
+    constexpr int PRO = (R - 1 < NR) ? R - 1 : NR;
+    constexpr int EPI = (KH > PRO) ? KH : PRO;
+#pragma unroll
+    for (int r = 0; r < PRO; ++r)
+        direct_row<true, R, G, GS, KH, KW, KWP, NX, B0>(r, srow + r * SW, s_k, acc);
+#pragma unroll 1
+    for (int r = PRO; r < EPI; ++r)
+        direct_row<false, R, G, GS, KH, KW, KWP, NX, B0>(r, srow + r * SW, s_k, acc);
+#pragma unroll
+    for (int r = EPI; r < NR; ++r)
+        direct_row<true, R, G, GS, KH, KW, KWP, NX, B0>(r, srow + r * SW, s_k, acc);
+
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        float blk[R][4];
+#pragma unroll
+        for (int o = 0; o < R; ++o)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) blk[o][c] = acc[o][g * 4 + c];
+        store_block<T, R>(dst, h, w, y0 + ty * R, x0 + g * GS + tx * C, vec_ok, blk);
+    }
+}
+
+}  // namespace tile
+}  // namespace pencil

@@ -75,3 +75,15 @@ def test_binding_refuses_missing_library(monkeypatch, tmp_path):
     monkeypatch.setattr(b, "LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError, match="missing"):
         b.lib()
+
+
+def test_batch_argument_errors_before_cuda(lib):
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.pencil_batch_create(7, 10, 100, ctypes.byref(h)) == -1      # bad dtype
+    assert lib.pencil_batch_create(0, 0, 100, ctypes.byref(h)) == -1      # no images
+    assert lib.pencil_batch_create(0, 10, 0, ctypes.byref(h)) == -1       # no tiles
+    assert lib.pencil_batch_create(0, 10, 10, None) == -2
+    assert lib.pencil_batch_set_variant(None, 3, 0) == -2
+    assert lib.pencil_batch_run(None, 1, None, None) == -2
+    assert lib.pencil_batch_destroy(None) == 0
