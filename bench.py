@@ -41,6 +41,7 @@ PX_PER_STEP = PX_PER_PASS * PASSES
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
+SERVE_SECONDS = 10.0
 WORKLOAD = ("conv2d clamp-to-edge, 3 planar channels of 8192x8192 FP32, filters 3x3/7x7/15x15 "
             "direct (normalised U[0,1) weights) + 15x15 Gaussian sigma=3 separable")
 
@@ -214,7 +215,7 @@ def run_ours(args, rank, world, local_rank):
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        extras = measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g)
+        extras = measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g, args.serve_seconds)
     e2e = measure_e2e(torch, pg, img, ks, g, max(2, min(args.steps // 50, 5))) if not args.no_e2e else None
 
     del d_out, d_img
@@ -249,7 +250,7 @@ def _time_stream(torch, stream, fn, reps):
     return a.elapsed_time(b) / reps
 
 
-def measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g):
+def measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g, serve_seconds=SERVE_SECONDS):
     """Per-pass kernel times of the workload, the FP16-storage variant, and
     the 8192^2 x 100-sweep Jacobi run (residual every 10 sweeps)."""
     sraw = stream.cuda_stream
@@ -306,7 +307,36 @@ def measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g):
     out["jacobi_8192x8192_100sweeps"] = jac
     del u0, u, ws
     out["batched_512"] = measure_batched(torch, pg, dev, stream)
+    out["serving"] = measure_serving(torch, pg, dev, serve_seconds)
     return out
+
+
+
+def measure_serving(torch, pg, dev, seconds):
+    """Open-loop Poisson replay, FP16 storage, sides log-uniform [128, 4096],
+    odd filter sides 3..15, 8 GiB arena budget: continuous batching against
+    one launch per request, at 2000 req/s (latency) and at a saturating rate
+    (throughput)."""
+    from paper_1302_5586_gb300 import serve, tune
+
+    res = {}
+    seed = synth.SEEDS["serve"]
+    for label, rate, dur in (("2000_req_s", 2000.0, seconds), ("saturation_40000_req_s", 40000.0, 0.5)):
+        tr = serve.make_trace(seed, rate, dur)
+        pool = serve.host_pool(tr, pg.PENCIL_F16, seed + 1)
+        bank = torch.from_numpy(tr.filters).to(dev)
+        srv = serve.Server(dtype=pg.PENCIL_F16, budget_bytes=8 << 30, streams=4, max_wave=64, max_inflight=256)
+        try:
+            srv.set_variants(tune.cached_variants(pg.PENCIL_F16))
+            served, _ = srv.run(tr, pool, bank, mode="served")
+            plain, _ = srv.run(tr, pool, bank, mode="plain")
+        finally:
+            srv.close()
+        res[label] = {"offered_req_s": rate, "seconds": dur,
+                      "offered_gpx_s": round(sum(r.h * r.w for r in tr.requests) / dur / 1e9, 3),
+                      "served": served.summary(), "plain": plain.summary()}
+        del pool, bank
+    return res
 
 
 def measure_batched(torch, pg, dev, stream):
@@ -490,6 +520,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=SERVE_SECONDS)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -160,6 +160,32 @@ int pencil_batch_run(pencil_batch *b, int n, const pencil_image *imgs, void *str
  * has finished.  NULL is accepted. */
 int pencil_batch_destroy(pencil_batch *b);
 
+/* ------------------------------------------------------------------- arena
+ * Byte-offset bookkeeping for one device memory budget, used by the serving
+ * loop to admit requests only while their buffers fit (the paper has no
+ * serving layer; this is runtime support for the batched path).  First-fit
+ * over free blocks kept in address order; freeing merges neighbours.  Host
+ * only: it never calls CUDA.  Thread-safe.
+ */
+typedef struct pencil_arena pencil_arena;
+
+/* capacity: budget in bytes (rounded down to align); align: a power of two.
+ * Errors: NULL, ARG, NOMEM. */
+int pencil_arena_create(size_t capacity, size_t align, pencil_arena **out);
+
+/* First block of round_up(bytes, align) bytes; its offset in *offset.
+ * Errors: NULL, ARG (bytes == 0), NOMEM (no free block is large enough). */
+int pencil_arena_alloc(pencil_arena *a, size_t bytes, size_t *offset);
+
+/* Release the block that starts at offset.  Errors: NULL, ARG (no such block). */
+int pencil_arena_free(pencil_arena *a, size_t offset);
+
+/* Free bytes in total, and the largest free block (0 for NULL). */
+size_t pencil_arena_free_bytes(pencil_arena *a);
+size_t pencil_arena_largest_free(pencil_arena *a);
+
+void pencil_arena_destroy(pencil_arena *a);
+
 /* ------------------------------------------------------------------ jacobi
  * One sweep: v[i][j] = 0.25f * ((u[i-1][j] + u[i+1][j]) + (u[i][j-1] + u[i][j+1]))
  * on the interior 1 <= i <= h-2, 1 <= j <= w-2, in FP32 in exactly that order;

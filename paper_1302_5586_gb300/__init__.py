@@ -21,6 +21,12 @@ from ._binding import (  # noqa: F401
     declared_symbols,
     lib,
     make_images,
+    pencil_arena_alloc,
+    pencil_arena_create,
+    pencil_arena_destroy,
+    pencil_arena_free,
+    pencil_arena_free_bytes,
+    pencil_arena_largest_free,
     pencil_batch_create,
     pencil_batch_destroy,
     pencil_batch_run,

@@ -77,6 +77,12 @@ def lib():
         "pencil_batch_run": (i, [vp, i, vp, vp]),
         "pencil_batch_destroy": (i, [vp]),
         "pencil_device_info": (i, [ctypes.c_char_p, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "pencil_arena_create": (i, [sz, sz, ctypes.POINTER(ctypes.c_void_p)]),
+        "pencil_arena_alloc": (i, [vp, sz, ctypes.POINTER(ctypes.c_size_t)]),
+        "pencil_arena_free": (i, [vp, sz]),
+        "pencil_arena_free_bytes": (sz, [vp]),
+        "pencil_arena_largest_free": (sz, [vp]),
+        "pencil_arena_destroy": (None, [vp]),
         "pencil_strerror": (ctypes.c_char_p, [i]),
         "pencil_version": (i, []),
         "pencil_last_cuda_error": (i, []),
@@ -209,6 +215,38 @@ def pencil_device_info():
     sms, drv = ctypes.c_int(), ctypes.c_int()
     _check(lib().pencil_device_info(name, 256, ctypes.byref(sms), ctypes.byref(drv)), "pencil_device_info")
     return name.value.decode(), sms.value, drv.value
+
+
+def pencil_arena_create(capacity, align=256) -> int:
+    out = ctypes.c_void_p()
+    _check(lib().pencil_arena_create(capacity, align, ctypes.byref(out)), "pencil_arena_create")
+    return out.value
+
+
+def pencil_arena_alloc(a, nbytes):
+    """Offset of a new block, or None when no free block is large enough."""
+    off = ctypes.c_size_t()
+    st = lib().pencil_arena_alloc(a, nbytes, ctypes.byref(off))
+    if st == -5:
+        return None
+    _check(st, "pencil_arena_alloc")
+    return off.value
+
+
+def pencil_arena_free(a, offset):
+    _check(lib().pencil_arena_free(a, offset), "pencil_arena_free")
+
+
+def pencil_arena_free_bytes(a) -> int:
+    return int(lib().pencil_arena_free_bytes(a))
+
+
+def pencil_arena_largest_free(a) -> int:
+    return int(lib().pencil_arena_largest_free(a))
+
+
+def pencil_arena_destroy(a):
+    lib().pencil_arena_destroy(a)
 
 
 def pencil_strerror(status: int) -> str:

@@ -31,7 +31,7 @@ def _nvcc() -> str:
 
 
 def sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
 def _headers():
@@ -55,7 +55,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     nvcc = _nvcc()
     srcs = sources()
     hdrs = _headers()
-    objs = [os.path.join(OUT, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(OUT, os.path.splitext(os.path.basename(s))[0] + ".o") for s in srcs]
     extra = ["-Xptxas", "-v"] if ptxas_v else []
 
     def compile_one(pair):

@@ -1,0 +1,278 @@
+"""Continuous-batching conv2d serving on one GPU.
+
+Requests (image size, filter side, input window, filter) arrive open-loop on
+a Poisson trace.  The scheduler loop:
+
+* admits arrived requests in arrival order while a slot is free
+  (`max_inflight`) and the arena (one device buffer of `budget_bytes`, offsets
+  kept by the native pencil_arena) has room for the request's input and
+  output; a request that does not fit waits until completions free memory;
+* packs every request admitted in one pass into a wave and issues it on the
+  next of `streams` CUDA streams: host-to-device copies of the inputs (from
+  pinned host memory into the arena), ONE batched persistent conv2d launch
+  (pencil_batch_run, graph replay; one plan per stream), device-to-host copies
+  of the outputs, and an event;
+* polls the events of the waves in flight; a finished wave's requests are
+  timestamped (latency = completion - arrival) and their arena blocks freed.
+
+Waves on different streams overlap on the device (copies of one wave with the
+kernel of another), and requests that arrive while others run join the next
+wave -- continuous batching.  `mode="plain"` replays the same trace with one
+standalone pencil_conv2d_ex launch per request (same copies, same admission)
+for comparison.  Every result is the same bits in either mode and alone.
+
+The paper has no serving layer; this is the serving pattern built on the
+batched kernel (the tuned launch of the independent image loop, Sec. 2.2.3).
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+import synth
+
+from . import _binding as b
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float   # seconds after the start of the replay
+    h: int
+    w: int
+    ks: int
+    src: int         # element offset of the input window in the host pool
+    filt: int        # element offset of the filter in the filter bank
+
+
+@dataclasses.dataclass
+class Trace:
+    requests: list
+    pool_elems: int
+    filters: np.ndarray  # all filters, concatenated FP32
+
+
+def make_trace(seed: int, rate: float, duration: float, lo: int = 128, hi: int = 4096,
+               klo: int = 3, khi: int = 15, pool_elems: int = 1 << 25) -> Trace:
+    """Poisson arrivals at `rate` per second for `duration` seconds; sides
+    log-uniform in [lo, hi]; odd filter sides uniform in [klo, khi]; inputs
+    are windows of a seeded noise pool at seed-derived offsets."""
+    t = synth.poisson_arrivals(seed, rate, duration)
+    n = len(t)
+    h = synth.loguniform_sides(seed ^ 0xA1, n, lo, hi)
+    w = synth.loguniform_sides(seed ^ 0xA2, n, lo, hi)
+    ks = synth.odd_ksizes(seed ^ 0xA3, n, klo, khi)
+    pool_elems = max(pool_elems, int(np.max(h * w)) if n else 1)
+    z = synth.splitmix64(seed ^ 0xA4, n) if n else np.zeros(0, np.uint64)
+    span = (pool_elems - h * w + 1).astype(np.uint64)
+    src = (z % np.maximum(span, 1)).astype(np.int64)
+    filts, reqs, off = [], [], 0
+    for i in range(n):
+        k = synth.filter_f32(seed * 7919 + i, int(ks[i]), int(ks[i])).ravel()
+        filts.append(k)
+        reqs.append(Request(i, float(t[i]), int(h[i]), int(w[i]), int(ks[i]), int(src[i]), off))
+        off += k.size
+    bank = np.concatenate(filts) if filts else np.zeros(1, np.float32)
+    return Trace(reqs, pool_elems, bank)
+
+
+@dataclasses.dataclass
+class Stats:
+    mode: str
+    requests: int
+    rejected: int
+    pixels: int
+    wall_s: float
+    latency_ms: np.ndarray
+    waves: int
+    peak_inflight: int
+    peak_arena_bytes: int
+
+    def summary(self) -> dict:
+        lat = self.latency_ms
+        ok = lat[np.isfinite(lat)]
+        return {
+            "mode": self.mode, "requests": self.requests, "rejected": self.rejected,
+            "p50_ms": round(float(np.percentile(ok, 50)), 3) if ok.size else None,
+            "p99_ms": round(float(np.percentile(ok, 99)), 3) if ok.size else None,
+            "mean_ms": round(float(ok.mean()), 3) if ok.size else None,
+            "max_ms": round(float(ok.max()), 3) if ok.size else None,
+            "gpx_s": round(self.pixels / self.wall_s / 1e9, 3) if self.wall_s > 0 else None,
+            "req_s": round(ok.size / self.wall_s, 1) if self.wall_s > 0 else None,
+            "waves": self.waves, "mean_wave": round(ok.size / max(self.waves, 1), 2),
+            "peak_inflight": self.peak_inflight, "peak_arena_mib": round(self.peak_arena_bytes / 2**20, 1),
+        }
+
+
+class Server:
+    """One GPU, `streams` CUDA streams, one batch plan per stream, one arena."""
+
+    def __init__(self, dtype: int = b.PENCIL_F16, budget_bytes: int = 8 << 30, streams: int = 4,
+                 max_wave: int = 64, max_inflight: int = 256, max_tiles: int = 1 << 20, device=None):
+        import torch
+
+        self.torch = torch
+        self.dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.dtype = dtype
+        self.tdtype = torch.float16 if dtype == b.PENCIL_F16 else torch.float32
+        self.esz = 2 if dtype == b.PENCIL_F16 else 4
+        self.budget = budget_bytes
+        self.pool = torch.empty(budget_bytes, dtype=torch.uint8, device=self.dev)
+        self.arena = b.pencil_arena_create(budget_bytes, 256)
+        self.streams = [torch.cuda.Stream(self.dev) for _ in range(streams)]
+        self.plans = [b.pencil_batch_create(dtype, max_wave, max_tiles) for _ in range(streams)]
+        self.max_wave = max_wave
+        self.max_inflight = max_inflight
+
+    def close(self):
+        self.torch.cuda.synchronize(self.dev)
+        for p in self.plans:
+            b.pencil_batch_destroy(p)
+        self.plans = []
+        if self.arena:
+            b.pencil_arena_destroy(self.arena)
+            self.arena = None
+
+    def set_variants(self, variants: dict):
+        for p in self.plans:
+            for ks, v in variants.items():
+                b.pencil_batch_set_variant(p, int(ks), int(v))
+
+    def _view(self, off: int, n: int):
+        return self.pool[off:off + n * self.esz].view(self.tdtype)
+
+    def run(self, trace: Trace, host_pool, filters_dev, mode: str = "served", keep_outputs: bool = False,
+            sink_bytes: int = 1 << 29) -> tuple:
+        """Replay `trace` open-loop.  host_pool: pinned host tensor of the
+        storage dtype (trace.pool_elems elements); filters_dev: device FP32
+        tensor holding trace.filters.  Returns (Stats, outputs or None)."""
+        torch = self.torch
+        reqs = trace.requests
+        n = len(reqs)
+        lat = np.full(n, np.nan)
+        outputs = [None] * n if keep_outputs else None
+        sink = None if keep_outputs else torch.empty(sink_bytes // self.esz, dtype=self.tdtype, pin_memory=True)
+        sink_pos = 0
+        pending = collections.deque()
+        inflight = [collections.deque() for _ in self.streams]
+        n_inflight = 0
+        peak_inflight = 0
+        peak_arena = 0
+        rejected = 0
+        waves = 0
+        done = 0
+        pix = 0
+        nxt = 0
+        rr = 0
+        kbase = filters_dev.data_ptr()
+        t0 = time.perf_counter()
+        last_done = t0
+        while done + rejected < n:
+            now = time.perf_counter() - t0
+            while nxt < n and reqs[nxt].arrival <= now:
+                r = reqs[nxt]
+                if 2 * r.h * r.w * self.esz > self.budget:  # can never fit
+                    rejected += 1
+                else:
+                    pending.append(r)
+                nxt += 1
+            progressed = False
+            # completions
+            for q in inflight:
+                while q and q[0][0].query():
+                    ev, items = q.popleft()
+                    tdone = time.perf_counter()
+                    for r, oi, oo in items:
+                        lat[r.rid] = (tdone - t0 - r.arrival) * 1e3
+                        b.pencil_arena_free(self.arena, oi)
+                        b.pencil_arena_free(self.arena, oo)
+                        pix += r.h * r.w
+                    n_inflight -= len(items)
+                    done += len(items)
+                    last_done = tdone
+                    progressed = True
+            # admission: arrival order, while a slot and arena memory are free
+            wave = []
+            limit = self.max_wave if mode == "served" else 1
+            while pending and len(wave) < limit and n_inflight + len(wave) < self.max_inflight:
+                r = pending[0]
+                nb = r.h * r.w * self.esz
+                oi = b.pencil_arena_alloc(self.arena, nb)
+                if oi is None:
+                    break
+                oo = b.pencil_arena_alloc(self.arena, nb)
+                if oo is None:
+                    b.pencil_arena_free(self.arena, oi)
+                    break
+                pending.popleft()
+                wave.append((r, oi, oo))
+            if wave:
+                s = self.streams[rr % len(self.streams)]
+                plan = self.plans[rr % len(self.plans)]
+                q = inflight[rr % len(self.streams)]
+                rr += 1
+                with torch.cuda.stream(s):
+                    for r, oi, _ in wave:
+                        hw = r.h * r.w
+                        self._view(oi, hw).copy_(host_pool[r.src:r.src + hw], non_blocking=True)
+                    if mode == "served":
+                        imgs = b.make_images([(self.pool.data_ptr() + oi, self.pool.data_ptr() + oo,
+                                               kbase + 4 * r.filt, r.h, r.w, r.ks) for r, oi, oo in wave])
+                        b.pencil_batch_run(plan, imgs, s.cuda_stream)
+                    else:
+                        for r, oi, oo in wave:
+                            b.pencil_conv2d_ex(1, r.h, r.w, self.pool.data_ptr() + oi, r.ks, r.ks,
+                                               kbase + 4 * r.filt, self.pool.data_ptr() + oo, self.dtype, 0,
+                                               s.cuda_stream)
+                    for r, _, oo in wave:
+                        hw = r.h * r.w
+                        src = self._view(oo, hw)
+                        if keep_outputs:
+                            outputs[r.rid] = torch.empty(hw, dtype=self.tdtype, pin_memory=True)
+                            outputs[r.rid].copy_(src, non_blocking=True)
+                        else:
+                            if sink_pos + hw > sink.numel():
+                                sink_pos = 0
+                            sink[sink_pos:sink_pos + hw].copy_(src, non_blocking=True)
+                            sink_pos += hw
+                    ev = torch.cuda.Event()
+                    ev.record(s)
+                q.append((ev, wave))
+                waves += 1
+                n_inflight += len(wave)
+                peak_inflight = max(peak_inflight, n_inflight)
+                peak_arena = max(peak_arena, self.budget - b.pencil_arena_free_bytes(self.arena))
+                progressed = True
+            if not progressed:
+                # nothing to do until the next arrival or completion
+                wait = (reqs[nxt].arrival - (time.perf_counter() - t0)) if nxt < n else 0.0
+                if wait > 2e-4 and not any(inflight):
+                    time.sleep(min(wait, 0.01) - 1e-4)
+        torch.cuda.synchronize(self.dev)
+        first = reqs[0].arrival if n else 0.0
+        wall = (last_done - t0) - first
+        st = Stats(mode, n, rejected, pix, wall, lat, waves, peak_inflight, peak_arena)
+        if keep_outputs:
+            outputs = [o.view(r.h, r.w) if o is not None else None for o, r in zip(outputs, reqs)]
+        return st, outputs
+
+
+def host_pool(trace: Trace, dtype: int, seed: int):
+    """The pinned host noise pool the trace's input windows come from."""
+    import torch
+
+    vals = synth.u01_f32(seed, trace.pool_elems)
+    t = torch.from_numpy(vals)
+    if dtype == b.PENCIL_F16:
+        t = t.half()
+    return t.pin_memory()
+
+
+def percentile_summary(stats_list):
+    return {s.mode: s.summary() for s in stats_list}
+
+
+__all__ = ["Request", "Trace", "Stats", "Server", "make_trace", "host_pool", "percentile_summary"]

@@ -80,3 +80,14 @@ def autotune(plan, dtype: int, items, reps: int = 5, use_cache: bool = True, pat
             json.dump(cache, f, indent=1, sort_keys=True)
         os.replace(tmp, path)
     return chosen
+
+
+def cached_variants(dtype: int, path: str | None = None) -> dict:
+    """{ks: variant} recorded for this GPU and dtype (sides never tuned are absent)."""
+    cache = _load(path or cache_path())
+    out = {}
+    for ks in range(1, 16, 2):
+        rec = cache.get(_key(dtype, ks))
+        if rec is not None:
+            out[ks] = int(rec["variant"])
+    return out
