@@ -69,9 +69,21 @@ def measured_peaks():
         return {}
 
 
-def traffic_record(kernel_key, source):
+KERNEL_SOURCES = ["paper_1302_5586_gb300/csrc/conv2d.cu", "paper_1302_5586_gb300/csrc/conv_tile.cuh",
+                  "paper_1302_5586_gb300/csrc/internal.cuh"]
+
+
+def sources_sha(paths=KERNEL_SOURCES):
+    hsh = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            hsh.update(f.read())
+    return hsh.hexdigest()[:16]
+
+
+def traffic_record(kernel_key):
     """DRAM bytes per launch from the committed ncu summary, if the kernel
-    source has not changed since it was taken."""
+    sources have not changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -80,9 +92,7 @@ def traffic_record(kernel_key, source):
         return None
     if not rec:
         return None
-    with open(os.path.join(ROOT, source), "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    return rec.get("bytes_per_launch") if rec.get("source_sha") == sha else None
+    return rec.get("bytes_per_launch") if rec.get("source_sha") == sources_sha() else None
 
 
 class Clocks:
@@ -206,7 +216,7 @@ def run_ours(args, rank, world, local_rank):
     flops_15 = 2 * 15 * 15 * PX_PER_PASS
     achieved = flops_15 / (k15_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
-    traffic = traffic_record("conv2d_direct_f32_15x15_8192x8192x3", "paper_1302_5586_gb300/csrc/conv2d.cu")
+    traffic = traffic_record("conv2d_direct_f32_15x15_8192x8192x3")
     roofline = {"bound": "alu", "kernel": "conv2d_direct_kernel<float,15,15,16,8,4,2,3>", "achieved": round(achieved, 3),
                 "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
@@ -493,6 +503,20 @@ def run_case(name, reps):
         out = torch.empty_like(img)
         for _ in range(reps):
             pg.pencil_conv2d_sep_ex(c, h, w, img, 15, g, 15, g, out, pg.PENCIL_F32)
+    elif name == "batch":
+        seed = synth.SEEDS["batch512"]
+        h, w, k = synth.batch_spec(seed, 128, 64, 2048)
+        items = []
+        for i in range(128):
+            t = torch.from_numpy(synth.image_f32(seed + i, 1, int(h[i]), int(w[i]))).to(dev)
+            kk = torch.from_numpy(synth.filter_f32(seed + 500 + i, int(k[i]), int(k[i]))).to(dev)
+            items.append((t, torch.empty_like(t), kk, int(h[i]), int(w[i]), int(k[i])))
+        plan = pg.pencil_batch_create(pg.PENCIL_F32, 128, 1 << 20)
+        imgs = pg.make_images(items)
+        for _ in range(reps):
+            pg.pencil_batch_run(plan, imgs)
+        torch.cuda.synchronize()
+        pg.pencil_batch_destroy(plan)
     elif name.startswith("jacobi"):
         t = int(name.split("t")[-1]) if "t" in name[6:] else 1
         n = 8192
@@ -510,7 +534,7 @@ def run_case(name, reps):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default=None,
-                    help="profile one kernel on a reduced workload: conv3, conv7, conv15, sep15, jacobi, jacobi-t5")
+                    help="profile one kernel on a reduced workload: conv3, conv7, conv15, sep15, batch, jacobi, jacobi-t5")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=600)
