@@ -436,7 +436,8 @@ def _oracle_band(oracle, img, ks, g, rows, r0):
 def cpu_baseline(img, ks, g, budget_s=15.0):
     import oracle
 
-    probe = 16
+    probe = 32
+    _oracle_band(oracle, img, ks, g, 8, 0)  # start the thread pool
     t_probe = _oracle_band(oracle, img, ks, g, probe, 4096)
     rows = int(max(probe, min(H, probe * budget_s / max(t_probe, 1e-6))))
     dt = _oracle_band(oracle, img, ks, g, rows, 4096 - rows // 2 if rows < H else 0)
@@ -456,6 +457,7 @@ def run_reference(args, rank, world):
     img = synth.image_f32(synth.SEEDS["conv8192x3"], C, H, W)
     ks = [synth.filter_f32(synth.SEEDS["conv8192x3"] + K, K, K) for K in DIRECT_K]
     g = synth.gaussian_taps_f32(GAUSS_R, GAUSS_SIGMA)
+    _oracle_band(oracle, img, ks, g, 8, 0)  # start the thread pool
     t_probe = _oracle_band(oracle, img, ks, g, 8, 4096)
     per_step_budget = max(0.5, 150.0 / max(args.steps + args.warmup, 1))
     rows = int(max(1, min(H, 8 * per_step_budget / max(t_probe, 1e-6))))

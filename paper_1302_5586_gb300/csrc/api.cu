@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of libpencilgpu: argument checks, the restrict rule,
 // memory-kind checks, the scratch pool of the plain calls, and dispatch.
+#include <algorithm>
 #include <mutex>
 #include <string.h>
 
@@ -41,11 +42,16 @@ bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
 
 size_t elem_size(int dtype) { return dtype == PENCIL_F16 ? 2 : 4; }
 
-// Plain calls' scratch: a few grow-only device buffers, one mutex.
+// Plain calls' scratch: grow-only device buffers, the library's copy
+// streams, one mutex (plain calls are serialised).
+constexpr int kSlots = 16;
+constexpr int kBandStreams = 3;
+
 struct Pool {
     std::mutex mu;
-    void *buf[4] = {nullptr, nullptr, nullptr, nullptr};
-    size_t cap[4] = {0, 0, 0, 0};
+    void *buf[kSlots] = {};
+    size_t cap[kSlots] = {};
+    cudaStream_t streams[kBandStreams] = {};
 
     // Returns a device buffer of >= bytes in slot i, or nullptr.
     void *get(int i, size_t bytes) {
@@ -61,11 +67,22 @@ struct Pool {
         cap[i] = bytes;
         return buf[i];
     }
+    cudaStream_t stream(int i) {
+        if (!streams[i] && cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            streams[i] = nullptr;
+        }
+        return streams[i];
+    }
     void release() {
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < kSlots; ++i) {
             if (buf[i]) cudaFree(buf[i]);
             buf[i] = nullptr;
             cap[i] = 0;
+        }
+        for (int i = 0; i < kBandStreams; ++i) {
+            if (streams[i]) cudaStreamDestroy(streams[i]);
+            streams[i] = nullptr;
         }
     }
 };
@@ -78,6 +95,49 @@ Pool &pool() {
 int check_dims(int h, int w) {
     if (h <= 0 || w <= 0) return PENCIL_ERR_ARG;
     if ((int64_t)h * (int64_t)w > ((int64_t)1 << 40)) return PENCIL_ERR_ARG;
+    return PENCIL_OK;
+}
+
+// A plain-call convolution whose image is in host memory (or mixed): the
+// output rows are processed in bands of `band` rows.  A band's input rows,
+// widened by the filter's halo (ht rows above, hb below, cut at the image
+// edges), are copied into a staging buffer and convolved as a sub-image; the
+// band's own rows are copied back.  Inside the sub-image every window of a
+// band row reads the same rows as in the whole image (the halo rows are real
+// rows; at the true edges the sub-image edge is the image edge), so the
+// result is the same bits as one launch over the whole image.  Bands rotate
+// over the library's streams, so one band's copies overlap another's kernel.
+// The caller holds the pool mutex.  `launch(in, out, h_sub, stream)`.
+template <typename Launch>
+int banded(int h, int w, int ht, int hb, const float *in, float *out, Launch launch) {
+    // a device-memory argument may still be written by earlier work on any
+    // stream: a plain call starts from a finished device
+    PENCIL_CUDA_TRY(cudaDeviceSynchronize());
+    const size_t row = sizeof(float) * (size_t)w;
+    int band = (int)std::max<size_t>(32, ((size_t)16 << 20) / row);
+    band = std::min(band, h);
+    const size_t stage = row * (size_t)(band + ht + hb);
+    cudaStream_t st[kBandStreams];
+    float *din[kBandStreams], *dout[kBandStreams];
+    for (int i = 0; i < kBandStreams; ++i) {
+        st[i] = pool().stream(i);
+        din[i] = static_cast<float *>(pool().get(4 + 2 * i, stage));
+        dout[i] = static_cast<float *>(pool().get(5 + 2 * i, stage));
+        if (!st[i]) return cuda_fail(cudaErrorUnknown);
+        if (!din[i] || !dout[i]) return PENCIL_ERR_NOMEM;
+    }
+    int b = 0;
+    for (int r0 = 0; r0 < h; r0 += band, ++b) {
+        const int r1 = std::min(h, r0 + band);
+        const int i0 = std::max(0, r0 - ht), i1 = std::min(h, r1 + hb);
+        const int k = b % kBandStreams;
+        PENCIL_CUDA_TRY(cudaMemcpyAsync(din[k], in + (size_t)i0 * w, row * (size_t)(i1 - i0),
+                                        cudaMemcpyDefault, st[k]));
+        PENCIL_CUDA_TRY(launch(din[k], dout[k], i1 - i0, st[k]));
+        PENCIL_CUDA_TRY(cudaMemcpyAsync(out + (size_t)r0 * w, dout[k] + (size_t)(r0 - i0) * w,
+                                        row * (size_t)(r1 - r0), cudaMemcpyDefault, st[k]));
+    }
+    for (int i = 0; i < kBandStreams; ++i) PENCIL_CUDA_TRY(cudaStreamSynchronize(st[i]));
     return PENCIL_OK;
 }
 
@@ -184,29 +244,22 @@ int pencil_conv2d(int h, int w, const float *in, int kh, int kw, const float *k,
         return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
     }
     std::lock_guard<std::mutex> lk(pool().mu);
-    const float *din = in, *dk = k;
-    float *dout = out;
-    if (mi == Mem::Host) {
-        void *b = pool().get(0, nb);
-        if (!b) return PENCIL_ERR_NOMEM;
-        PENCIL_CUDA_TRY(cudaMemcpyAsync(b, in, nb, cudaMemcpyHostToDevice, s));
-        din = static_cast<const float *>(b);
-    }
+    const float *dk = k;
     if (mk == Mem::Host) {
         void *b = pool().get(1, kb);
         if (!b) return PENCIL_ERR_NOMEM;
-        PENCIL_CUDA_TRY(cudaMemcpyAsync(b, k, kb, cudaMemcpyHostToDevice, s));
+        PENCIL_CUDA_TRY(cudaMemcpy(b, k, kb, cudaMemcpyHostToDevice));
         dk = static_cast<const float *>(b);
     }
-    if (mo == Mem::Host) {
-        void *b = pool().get(2, nb);
-        if (!b) return PENCIL_ERR_NOMEM;
-        dout = static_cast<float *>(b);
+    if (mi == Mem::Device && mo == Mem::Device) {
+        PENCIL_CUDA_TRY(launch_conv2d(PENCIL_F32, 1, h, w, in, kh, kw, dk, out, s));
+        PENCIL_CUDA_TRY(cudaStreamSynchronize(s));
+        return PENCIL_OK;
     }
-    PENCIL_CUDA_TRY(launch_conv2d(PENCIL_F32, 1, h, w, din, kh, kw, dk, dout, s));
-    if (mo == Mem::Host) PENCIL_CUDA_TRY(cudaMemcpyAsync(out, dout, nb, cudaMemcpyDeviceToHost, s));
-    PENCIL_CUDA_TRY(cudaStreamSynchronize(s));
-    return PENCIL_OK;
+    return banded(h, w, kh / 2, kh - 1 - kh / 2, in, out,
+                  [&](const float *bi, float *bo, int hs, cudaStream_t bs) {
+                      return launch_conv2d(PENCIL_F32, 1, hs, w, bi, kh, kw, dk, bo, bs);
+                  });
 }
 
 int pencil_conv2d_sep(int h, int w, const float *in, int kx, const float *gx, int ky,
@@ -225,36 +278,29 @@ int pencil_conv2d_sep(int h, int w, const float *in, int kx, const float *gx, in
         return PENCIL_ERR_PTR;
     cudaStream_t s = 0;
     std::lock_guard<std::mutex> lk(pool().mu);
-    const float *din = in, *dgx = gx, *dgy = gy;
-    float *dout = out;
-    if (mi == Mem::Host) {
-        void *b = pool().get(0, nb);
-        if (!b) return PENCIL_ERR_NOMEM;
-        PENCIL_CUDA_TRY(cudaMemcpyAsync(b, in, nb, cudaMemcpyHostToDevice, s));
-        din = static_cast<const float *>(b);
-    }
+    const float *dgx = gx, *dgy = gy;
     if (mx == Mem::Host || my == Mem::Host) {
         float *b = static_cast<float *>(pool().get(1, sizeof(float) * 2 * PENCIL_MAX_SPECIALISED_K));
         if (!b) return PENCIL_ERR_NOMEM;
         if (mx == Mem::Host) {
-            PENCIL_CUDA_TRY(cudaMemcpyAsync(b, gx, sizeof(float) * kx, cudaMemcpyHostToDevice, s));
+            PENCIL_CUDA_TRY(cudaMemcpy(b, gx, sizeof(float) * kx, cudaMemcpyHostToDevice));
             dgx = b;
         }
         if (my == Mem::Host) {
             float *by = b + PENCIL_MAX_SPECIALISED_K;
-            PENCIL_CUDA_TRY(cudaMemcpyAsync(by, gy, sizeof(float) * ky, cudaMemcpyHostToDevice, s));
+            PENCIL_CUDA_TRY(cudaMemcpy(by, gy, sizeof(float) * ky, cudaMemcpyHostToDevice));
             dgy = by;
         }
     }
-    if (mo == Mem::Host) {
-        void *b = pool().get(2, nb);
-        if (!b) return PENCIL_ERR_NOMEM;
-        dout = static_cast<float *>(b);
+    if (mi == Mem::Device && mo == Mem::Device) {
+        PENCIL_CUDA_TRY(launch_conv2d_sep(PENCIL_F32, 1, h, w, in, kx, dgx, ky, dgy, out, s));
+        PENCIL_CUDA_TRY(cudaStreamSynchronize(s));
+        return PENCIL_OK;
     }
-    PENCIL_CUDA_TRY(launch_conv2d_sep(PENCIL_F32, 1, h, w, din, kx, dgx, ky, dgy, dout, s));
-    if (mo == Mem::Host) PENCIL_CUDA_TRY(cudaMemcpyAsync(out, dout, nb, cudaMemcpyDeviceToHost, s));
-    PENCIL_CUDA_TRY(cudaStreamSynchronize(s));
-    return PENCIL_OK;
+    return banded(h, w, ky / 2, ky - 1 - ky / 2, in, out,
+                  [&](const float *bi, float *bo, int hs, cudaStream_t bs) {
+                      return launch_conv2d_sep(PENCIL_F32, 1, hs, w, bi, kx, dgx, ky, dgy, bo, bs);
+                  });
 }
 
 size_t pencil_jacobi2d_workspace_size(int h, int w) {
