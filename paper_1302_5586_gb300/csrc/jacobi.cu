@@ -193,9 +193,9 @@ __global__ void __launch_bounds__(256) residual_finish_kernel(const double *__re
 // Per point the update is the same FP32 expression as the one-sweep kernel,
 // so the iterate is the same bits for every T.  Residuals of iterates that
 // fall inside the pass are accumulated from the staged values of the core.
-template <int T>
+template <int T, int NTHREADS = 512>
 struct TileCfg {
-    static constexpr int NT = 256;
+    static constexpr int NT = NTHREADS;
     static constexpr int WARPS = NT / 32;
     static constexpr int SWP = 136;                 // 4 + 32 chunks * 4 + 4
     static constexpr int P = round_up(T + 3, 4);    // core starts at column P
@@ -206,12 +206,12 @@ struct TileCfg {
     static constexpr size_t smem = 2 * (size_t)SH * SWP * sizeof(float);
 };
 
-template <int T>
-__global__ void __launch_bounds__(256)
+template <int T, int NT = 512>
+__global__ void __launch_bounds__(NT)
     jacobi_tiled_kernel(const float *__restrict__ u, float *__restrict__ v, int h, int w,
                         int nsweeps, int iter0, int check_every, double *__restrict__ partials,
                         int nblk) {
-    using Cfg = TileCfg<T>;
+    using Cfg = TileCfg<T, NT>;
     constexpr int SWP = Cfg::SWP, SH = Cfg::SH, P = Cfg::P, BW = Cfg::BW, BH = Cfg::BH,
                   RS = Cfg::RS;
     extern __shared__ __align__(16) float smem[];
@@ -261,10 +261,13 @@ __global__ void __launch_bounds__(256)
         for (int rr = 0; rr < RS; ++rr) {
             const int r = rbeg + rr;
             const float4 dn = *reinterpret_cast<const float4 *>(A + (r + 1) * SWP + c0);
+            // neighbours from adjacent lanes; the warp's two edge values are
+            // broadcast loads that every lane issues (no divergent branch)
+            const float lfe = A[r * SWP + 3], rte = A[r * SWP + 132];
             float lf = __shfl_up_sync(FULL, cur.w, 1);
             float rt = __shfl_down_sync(FULL, cur.x, 1);
-            if (lane == 0) lf = A[r * SWP + 3];
-            if (lane == 31) rt = A[r * SWP + 132];
+            lf = lane == 0 ? lfe : lf;
+            rt = lane == 31 ? rte : rt;
             const int gr = gy0 + r;
             const bool rint = gr >= 1 && gr <= h - 2;
             const float sx = nsum(up.x, dn.x, lf, cur.y);
@@ -341,7 +344,7 @@ cudaError_t finish(const double *partials, int n, double *res, cudaStream_t s) {
 
 template <int T>
 int tiled_nblk(int h, int w) {
-    using Cfg = TileCfg<T>;
+    using Cfg = TileCfg<T, 512>;
     return ((w + Cfg::BW - 1) / Cfg::BW) * ((h + Cfg::BH - 1) / Cfg::BH);
 }
 
@@ -362,8 +365,8 @@ size_t tiled_partials(int h, int w) {
 template <int T>
 cudaError_t run_tiled(int h, int w, float *u, float *v, int iters, int per_pass, int ce,
                       double *res, double *partials, cudaStream_t s, float **final) {
-    using Cfg = TileCfg<T>;
-    auto kern = jacobi_tiled_kernel<T>;
+    using Cfg = TileCfg<T, 512>;
+    auto kern = jacobi_tiled_kernel<T, 512>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Cfg::smem);
     if (e != cudaSuccess) return e;
