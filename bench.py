@@ -149,6 +149,19 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's elapsed time (every rank gets it)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gpx(px_per_step, world, steps, ms):
+    """Output Gpixel/s of all ranks: every rank processes its own images."""
+    return px_per_step * world * steps / (ms * 1e-3) / 1e9
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -206,11 +219,9 @@ def run_ours(args, rank, world, local_rank):
     ms = t0.elapsed_time(t1)
     k15_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
     ms_per_step = ms / args.steps
-    value = PX_PER_STEP * world * args.steps / (ms * 1e-3) / 1e9
+    value = whole_job_gpx(PX_PER_STEP, world, args.steps, ms)
 
     # dominant kernel roofline: 15x15 direct conv is FP32-pipe bound
     flops_15 = 2 * 15 * 15 * PX_PER_PASS
