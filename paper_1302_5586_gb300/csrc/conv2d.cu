@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256)
 // --------------------------------------------------------- separable kernel
 // Row pass (kx taps) of the staged halo tile into shared memory, then the
 // column pass (ky taps) from it; nothing intermediate goes to HBM.
-template <int KX, int KY, int TX, int TY, int R>
+template <int KX, int KY, int TX, int TY, int R, bool INPLACE = false>
 struct SepCfg {
     static constexpr int C = 4;
     static constexpr int AX = KX / 2, AY = KY / 2;
@@ -76,64 +76,90 @@ struct SepCfg {
     static constexpr int SW = TW + 2 * P;
     static constexpr int SH = TH + KY - 1;
     static constexpr int NX = round_up(P - AX + C + KX - 1, 4);
-    static constexpr size_t smem_f32 = sizeof(float) * (size_t)(SH * SW + SH * TW);
+    // in place: the row-pass results overwrite the staged tile (row stride SW)
+    static constexpr size_t smem_f32 = sizeof(float) * (size_t)(SH * SW + (INPLACE ? 0 : SH * TW));
     static constexpr size_t smem(size_t esz) { return smem_f32 + (esz == 2 ? 2 * (size_t)SH * SW : 0); }
 };
 
-template <typename T, int KX, int KY, int TX, int TY, int R, int MINB = 1>
+template <typename T, int KX, int KY, int TX, int TY, int R, int MINB = 1, bool INPLACE = false>
 __global__ void __launch_bounds__(TX *TY, MINB)
     conv2d_sep_kernel(const T *__restrict__ in, const float *__restrict__ gx,
                       const float *__restrict__ gy, T *__restrict__ out, int h, int w, bool vec_ok) {
-    using Cfg = SepCfg<KX, KY, TX, TY, R>;
+    using Cfg = SepCfg<KX, KY, TX, TY, R, INPLACE>;
     constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, SH = Cfg::SH, TW = Cfg::TW,
-                  NX = Cfg::NX, AX = Cfg::AX, AY = Cfg::AY;
+                  NX = Cfg::NX, AX = Cfg::AX, AY = Cfg::AY, NT = Cfg::NT;
+    constexpr int TS = INPLACE ? SW : TW;  // row stride of the row-pass results
     extern __shared__ __align__(16) float smem[];
     float *s_in = smem;
-    float *s_t = smem + SH * SW;
-    T *s16 = reinterpret_cast<T *>(smem + SH * SW + SH * TW);
-
-    float fx[KX], fy[KY];
-#pragma unroll
-    for (int b = 0; b < KX; ++b) fx[b] = __ldg(gx + b);
-#pragma unroll
-    for (int a = 0; a < KY; ++a) fy[a] = __ldg(gy + a);
+    float *s_t = INPLACE ? smem : smem + SH * SW;
+    T *s16 = reinterpret_cast<T *>(smem + Cfg::smem_f32 / sizeof(float));
 
     const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
     const T *src = in + plane;
     T *dst = out + plane;
     const int x0 = blockIdx.x * TW;
     const int y0 = blockIdx.y * Cfg::TH;
-    stage_tile<T, SH, SW, Cfg::NT>(src, h, w, y0 - AY, x0 - P, vec_ok, s_in, s16);
+    stage_tile<T, SH, SW, NT>(src, h, w, y0 - AY, x0 - P, vec_ok, s_in, s16);
 
     // row pass: t[r][q*C + c] = sum_b gx[b] * in[r][q*C + c + b - AX]
-    constexpr int QPR = TW / C;
-    for (int idx = threadIdx.x; idx < SH * QPR; idx += Cfg::NT) {
-        const int r = idx / QPR, q = idx - r * QPR;
-        const float *sp = s_in + r * SW + q * C;
-        float x[NX];
+    {
+        float fx[KX];
 #pragma unroll
-        for (int m = 0; m < NX; m += 4) {
-            const float4 v = *reinterpret_cast<const float4 *>(sp + m);
-            x[m] = v.x; x[m + 1] = v.y; x[m + 2] = v.z; x[m + 3] = v.w;
+        for (int b = 0; b < KX; ++b) fx[b] = __ldg(gx + b);
+        constexpr int QPR = TW / C;
+        constexpr int ITEMS = SH * QPR;
+        constexpr int PER = (ITEMS + NT - 1) / NT;  // items per thread
+        float4 res[INPLACE ? PER : 1];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int idx = threadIdx.x + k * NT;
+            if (idx < ITEMS) {
+                const int r = idx / QPR, q = idx - r * QPR;
+                const float *sp = s_in + r * SW + q * C;
+                float x[NX];
+#pragma unroll
+                for (int m = 0; m < NX; m += 4) {
+                    const float4 v = *reinterpret_cast<const float4 *>(sp + m);
+                    x[m] = v.x; x[m + 1] = v.y; x[m + 2] = v.z; x[m + 3] = v.w;
+                }
+                float tv[C];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    float sum = __fmul_rn(fx[0], x[P - AX + c]);
+#pragma unroll
+                    for (int b = 1; b < KX; ++b) sum = __fmaf_rn(fx[b], x[P - AX + c + b], sum);
+                    tv[c] = sum;
+                }
+                const float4 t4 = make_float4(tv[0], tv[1], tv[2], tv[3]);
+                if (INPLACE)
+                    res[k] = t4;
+                else
+                    *reinterpret_cast<float4 *>(s_t + r * TS + q * C) = t4;
+            }
         }
-        float t[C];
+        if (INPLACE) {
+            __syncthreads();  // every read of the staged tile is done
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            float s = __fmul_rn(fx[0], x[P - AX + c]);
-#pragma unroll
-            for (int b = 1; b < KX; ++b) s = __fmaf_rn(fx[b], x[P - AX + c + b], s);
-            t[c] = s;
+            for (int k = 0; k < PER; ++k) {
+                const int idx = threadIdx.x + k * NT;
+                if (idx < ITEMS) {
+                    const int r = idx / QPR, q = idx - r * QPR;
+                    *reinterpret_cast<float4 *>(s_t + r * TS + q * C) = res[k];
+                }
+            }
         }
-        *reinterpret_cast<float4 *>(s_t + r * TW + q * C) = make_float4(t[0], t[1], t[2], t[3]);
     }
     __syncthreads();
 
     // column pass: out[o][c] = sum_a gy[a] * t[o + a][c]
+    float fy[KY];
+#pragma unroll
+    for (int a = 0; a < KY; ++a) fy[a] = __ldg(gy + a);
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     float acc[R][C];
 #pragma unroll
     for (int r = 0; r < R + KY - 1; ++r) {
-        const float4 v = *reinterpret_cast<const float4 *>(s_t + (ty * R + r) * TW + tx * C);
+        const float4 v = *reinterpret_cast<const float4 *>(s_t + (ty * R + r) * TS + tx * C);
         const float tv[C] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int o = 0; o < R; ++o) {
@@ -231,11 +257,11 @@ cudaError_t run_generic(int c, int h, int w, const T *in, int kh, int kw, const 
     return cudaGetLastError();
 }
 
-template <typename T, int K, int TX, int TY, int R>
+template <typename T, int K, int TX, int TY, int R, int MINB = 1, bool INPLACE = false>
 cudaError_t run_sep(int c, int h, int w, const T *in, const float *gx, const float *gy, T *out,
                     bool vec_ok, cudaStream_t s) {
-    using Cfg = SepCfg<K, K, TX, TY, R>;
-    auto kern = conv2d_sep_kernel<T, K, K, TX, TY, R>;
+    using Cfg = SepCfg<K, K, TX, TY, R, INPLACE>;
+    auto kern = conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE>;
     const size_t smem = Cfg::smem(sizeof(T));
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
@@ -252,10 +278,10 @@ cudaError_t run_sep_any(int c, int h, int w, const T *in, int kx, const float *g
             case 3: return run_sep<T, 3, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
             case 5: return run_sep<T, 5, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
             case 7: return run_sep<T, 7, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
-            case 9: return run_sep<T, 9, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
-            case 11: return run_sep<T, 11, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
-            case 13: return run_sep<T, 13, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
-            case 15: return run_sep<T, 15, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
+            case 9: return run_sep<T, 9, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, s);
+            case 11: return run_sep<T, 11, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, s);
+            case 13: return run_sep<T, 13, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, s);
+            case 15: return run_sep<T, 15, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, s);
             default: break;
         }
     }

@@ -72,8 +72,8 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v,
 // FP32 chunks land in s directly; binary16 chunks land in the staging area
 // `s16` and are widened into s afterwards.  Ends with a barrier.
 template <typename T, int SH, int SW, int NT>
-__device__ __forceinline__ void stage_tile(const T *__restrict__ src, int h, int w, int y0, int x0,
-                                           bool vec_ok, float *__restrict__ s, T *__restrict__ s16) {
+__device__ __forceinline__ void stage_issue(const T *__restrict__ src, int h, int w, int y0, int x0,
+                                            bool vec_ok, float *__restrict__ s, T *__restrict__ s16) {
     constexpr int V = Io<T>::VEC;
     constexpr int CPR = SW / V;
     constexpr bool F16 = sizeof(T) == 2;
@@ -103,10 +103,17 @@ __device__ __forceinline__ void stage_tile(const T *__restrict__ src, int h, int
         }
     }
     cp_async_commit();
+}
+
+// Second half of staging: wait for this thread's copies, then (binary16)
+// widen the staged tile into s.  Ends with a barrier.
+template <typename T, int SH, int SW, int NT>
+__device__ __forceinline__ void stage_finish(float *__restrict__ s, const T *__restrict__ s16) {
+    constexpr int V = Io<T>::VEC;
+    constexpr int CPR = SW / V;
     cp_async_wait_all();
-    if (F16) {
+    if (sizeof(T) == 2) {
         __syncthreads();
-        // widen the staged binary16 tile (exact) into the FP32 tile
         for (int idx = threadIdx.x; idx < SH * CPR; idx += NT) {
             float v[V];
             Io<T>::ld16s(s16 + idx * V, v);
@@ -117,6 +124,20 @@ __device__ __forceinline__ void stage_tile(const T *__restrict__ src, int h, int
         }
     }
     __syncthreads();
+}
+
+// Stage s[r][c] = in[clamp(y0 + r)][clamp(x0 + c)] for r < SH, c < SW (as FP32).
+// x0 is a multiple of VEC, SW a multiple of VEC.  vec_ok: rows are 16-byte
+// aligned (w % VEC == 0 and the plane base is 16-byte aligned).  Chunks that
+// lie inside the row go through cp.async (all of a CTA's copies in flight at
+// once); chunks that cross an edge are gathered with clamped scalar loads.
+// FP32 chunks land in s directly; binary16 chunks land in the staging area
+// `s16` and are widened into s afterwards.  Ends with a barrier.
+template <typename T, int SH, int SW, int NT>
+__device__ __forceinline__ void stage_tile(const T *__restrict__ src, int h, int w, int y0, int x0,
+                                           bool vec_ok, float *__restrict__ s, T *__restrict__ s16) {
+    stage_issue<T, SH, SW, NT>(src, h, w, y0, x0, vec_ok, s, s16);
+    stage_finish<T, SH, SW, NT>(s, s16);
 }
 
 // Write a thread's R x 4 block (rows y, cols x..x+3), bounds-checked.
@@ -196,27 +217,16 @@ __device__ __forceinline__ void direct_row(int r, const float *__restrict__ xrow
     }
 }
 
-// One TH x TW output tile with origin (y0, x0) of one plane: stage, compute,
-// store.  Called by every thread of an NT-thread block (it contains barriers);
-// `smem` must hold DirectCfg::smem(sizeof(T)) bytes.
+// Compute and store one TH x TW output tile with origin (y0, x0) from a
+// staged tile s_in (see stage_tile) and staged filter rows s_k.
 template <typename T, int KH, int KW, int TX, int TY, int R, int G>
-__device__ __forceinline__ void direct_tile(const T *__restrict__ src, const float *__restrict__ k,
-                                            T *__restrict__ dst, int h, int w, bool vec_ok, int y0,
-                                            int x0, float *__restrict__ smem) {
+__device__ __forceinline__ void direct_compute(const float *__restrict__ s_in,
+                                               const float *__restrict__ s_k, T *__restrict__ dst,
+                                               int h, int w, bool vec_ok, int y0, int x0) {
     using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
-    constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, SH = Cfg::SH, KWP = Cfg::KWP,
-                  NX = Cfg::NX, AW = Cfg::AW, AH = Cfg::AH, GS = Cfg::GS;
+    constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, KWP = Cfg::KWP, NX = Cfg::NX,
+                  AW = Cfg::AW, GS = Cfg::GS;
     constexpr int B0 = P - AW;  // x index of tap 0 for column 0
-    float *s_in = smem;
-    float *s_k = smem + SH * SW;
-    T *s16 = reinterpret_cast<T *>(smem + SH * SW + KH * KWP);
-
-    for (int t = threadIdx.x; t < KH * KWP; t += Cfg::NT) {
-        const int a = t / KWP, b = t - a * KWP;
-        s_k[t] = b < KW ? __ldg(k + a * KW + b) : 0.0f;
-    }
-    stage_tile<T, SH, SW, Cfg::NT>(src, h, w, y0 - AH, x0 - P, vec_ok, s_in, s16);
-
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const float *srow = s_in + (ty * R) * SW + tx * C;
 
@@ -251,6 +261,32 @@ __device__ __forceinline__ void direct_tile(const T *__restrict__ src, const flo
             for (int c = 0; c < 4; ++c) blk[o][c] = acc[o][g * 4 + c];
         store_block<T, R>(dst, h, w, y0 + ty * R, x0 + g * GS + tx * C, vec_ok, blk);
     }
+}
+
+// Filter rows into shared memory, each padded with zeros to KWP.
+template <int KH, int KW, int KWP, int NT>
+__device__ __forceinline__ void stage_filter(const float *__restrict__ k, float *__restrict__ s_k) {
+    for (int t = threadIdx.x; t < KH * KWP; t += NT) {
+        const int a = t / KWP, b = t - a * KWP;
+        s_k[t] = b < KW ? __ldg(k + a * KW + b) : 0.0f;
+    }
+}
+
+// One TH x TW output tile with origin (y0, x0) of one plane: stage, compute,
+// store.  Called by every thread of an NT-thread block (it contains barriers);
+// `smem` must hold DirectCfg::smem(sizeof(T)) bytes.
+template <typename T, int KH, int KW, int TX, int TY, int R, int G>
+__device__ __forceinline__ void direct_tile(const T *__restrict__ src, const float *__restrict__ k,
+                                            T *__restrict__ dst, int h, int w, bool vec_ok, int y0,
+                                            int x0, float *__restrict__ smem) {
+    using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
+    constexpr int SW = Cfg::SW, SH = Cfg::SH, KWP = Cfg::KWP, AH = Cfg::AH, P = Cfg::P;
+    float *s_in = smem;
+    float *s_k = smem + SH * SW;
+    T *s16 = reinterpret_cast<T *>(smem + SH * SW + KH * KWP);
+    stage_filter<KH, KW, KWP, Cfg::NT>(k, s_k);
+    stage_tile<T, SH, SW, Cfg::NT>(src, h, w, y0 - AH, x0 - P, vec_ok, s_in, s16);
+    direct_compute<T, KH, KW, TX, TY, R, G>(s_in, s_k, dst, h, w, vec_ok, y0, x0);
 }
 
 }  // namespace tile
