@@ -6,9 +6,9 @@
 // every tile of image i gets the entry i.  The table, the image descriptors
 // and a header {next, total} are copied to a device buffer owned by the plan;
 // the kernel's CTAs (a resident grid: SMs x CTAs per SM) take tile indices
-// from `next` with one atomicAdd per tile (fetched one tile ahead, so its
-// latency overlaps the current tile), look the image up, and run the same
-// tile body as the standalone direct kernel -- so every batched pixel is the
+// from `next` with one atomicAdd per tile, look the image up, and run the same
+// tile body as the standalone direct kernel; each CTA has two staging slots,
+// so the copies of its next tile run while the current one is computed -- so every batched pixel is the
 // same bits as pencil_conv2d_ex on that image alone.  The kernel reads the
 // tile count from the device header, so one captured graph serves every
 // batch the plan runs.
@@ -46,65 +46,125 @@ constexpr int BT = 128;  // threads per CTA of the batched kernel
 // Sides up to 7 use one 4-column group per thread; larger sides two groups.
 __host__ __device__ constexpr int var_th(int v) { return v == 0 ? 32 : 16; }
 constexpr int kTileW = 128;
+__host__ __device__ constexpr int btx(int k) { return k <= 7 ? 32 : 16; }
+__host__ __device__ constexpr int bty(int k) { return k <= 7 ? 4 : 8; }
+__host__ __device__ constexpr int bg(int k) { return k <= 7 ? 1 : 2; }
+__host__ __device__ constexpr int brows(int k, int v) { return k <= 7 ? (v == 0 ? 8 : 4) : (v == 0 ? 4 : 2); }
+template <int K, int V>
+using BCfg = DirectCfg<K, K, btx(K), bty(K), brows(K, V), bg(K)>;
 
+// A staging slot: filter rows (up to 15 x 16) | FP32 tile | binary16 tile.
+constexpr int kSlotK = 15 * 16;
+constexpr int kSlotIn = BCfg<15, 0>::SH * BCfg<15, 0>::SW;  // the largest staged tile
+static_assert(BCfg<7, 0>::SH * BCfg<7, 0>::SW <= kSlotIn, "slot too small");
+__host__ __device__ constexpr int slot_floats(int esz) { return kSlotK + kSlotIn + (esz == 2 ? kSlotIn / 2 : 0); }
+
+// Issue the copies of one tile (filter and halo tile) into a slot; one commit group.
 template <typename T, int K, int V>
-__device__ __forceinline__ void run_tile(const BatchImage &d, int y0, int x0, float *smem) {
-    const T *in = static_cast<const T *>(d.in);
-    T *out = static_cast<T *>(d.out);
-    if (K <= 7)
-        direct_tile<T, K, K, 32, 4, (V == 0 ? 8 : 4), 1>(in, d.k, out, d.h, d.w, d.vec_ok, y0, x0, smem);
-    else
-        direct_tile<T, K, K, 16, 8, (V == 0 ? 4 : 2), 2>(in, d.k, out, d.h, d.w, d.vec_ok, y0, x0, smem);
+__device__ __forceinline__ void issue_tile(const BatchImage &d, int y0, int x0, float *slot) {
+    using Cfg = BCfg<K, V>;
+    stage_filter_async<K, K, Cfg::KWP, BT>(d.k, slot);
+    stage_issue<T, Cfg::SH, Cfg::SW, BT>(static_cast<const T *>(d.in), d.h, d.w, y0 - Cfg::AH, x0 - Cfg::P,
+                                         d.vec_ok, slot + kSlotK,
+                                         reinterpret_cast<T *>(slot + kSlotK + kSlotIn));
 }
 
-template <typename T, int K>
-__device__ __forceinline__ void run_tile_v(const BatchImage &d, int y0, int x0, float *smem) {
-    if (d.var == 0)
-        run_tile<T, K, 0>(d, y0, x0, smem);
-    else
-        run_tile<T, K, 1>(d, y0, x0, smem);
+// Widen (binary16) and compute one staged tile.
+template <typename T, int K, int V>
+__device__ __forceinline__ void compute_tile(const BatchImage &d, int y0, int x0, float *slot) {
+    using Cfg = BCfg<K, V>;
+    stage_widen<T, Cfg::SH, Cfg::SW, BT>(slot + kSlotK, reinterpret_cast<const T *>(slot + kSlotK + kSlotIn));
+    direct_compute<T, K, K, btx(K), bty(K), brows(K, V), bg(K)>(slot + kSlotK, slot, static_cast<T *>(d.out),
+                                                               d.h, d.w, d.vec_ok, y0, x0);
 }
 
-template <typename T>
+template <typename T, bool ISSUE>
+__device__ __forceinline__ void tile_op(const BatchImage &d, int y0, int x0, float *slot) {
+#define PENCIL_BATCH_CASE(K)                                                     \
+    case K:                                                                      \
+        if (d.var == 0) {                                                        \
+            if (ISSUE) issue_tile<T, K, 0>(d, y0, x0, slot);                     \
+            else compute_tile<T, K, 0>(d, y0, x0, slot);                         \
+        } else {                                                                 \
+            if (ISSUE) issue_tile<T, K, 1>(d, y0, x0, slot);                     \
+            else compute_tile<T, K, 1>(d, y0, x0, slot);                         \
+        }                                                                        \
+        break;
+    switch (d.ks) {
+        PENCIL_BATCH_CASE(1)
+        PENCIL_BATCH_CASE(3)
+        PENCIL_BATCH_CASE(5)
+        PENCIL_BATCH_CASE(7)
+        PENCIL_BATCH_CASE(9)
+        PENCIL_BATCH_CASE(11)
+        PENCIL_BATCH_CASE(13)
+        default: PENCIL_BATCH_CASE(15)
+    }
+#undef PENCIL_BATCH_CASE
+}
+
+__device__ __forceinline__ void tile_origin(const BatchImage &d, int t, int &y0, int &x0) {
+    const int local = t - d.tile_base;
+    const int ty = local / d.tiles_x, tx = local - ty * d.tiles_x;
+    y0 = ty * var_th(d.var);
+    x0 = tx * kTileW;
+}
+
+// NSLOT = 2: while tile i is computed from one staging slot, the copies of
+// tile i+1 are already in flight into the other.  NSLOT = 1 (binary16, whose
+// slots are larger): the next tile's copies are issued after the compute.
+template <typename T, int NSLOT>
 __global__ void __launch_bounds__(BT, 4)
     conv2d_batch_kernel(BatchHeader *__restrict__ hdr, const BatchImage *__restrict__ imgs,
                         const int *__restrict__ tile_img) {
     extern __shared__ __align__(16) float smem[];
-    __shared__ int s_t;
+    __shared__ int s_next;
+    constexpr int SLOT = slot_floats(sizeof(T));
     const int total = hdr->total;
-    if (threadIdx.x == 0) s_t = atomicAdd(&hdr->next, 1);
+    if (threadIdx.x == 0) s_next = atomicAdd(&hdr->next, 1);
     __syncthreads();
-    int t = s_t;
-    while (t < total) {
-        __syncthreads();  // every thread has read s_t
-        if (threadIdx.x == 0) s_t = atomicAdd(&hdr->next, 1);
-        const BatchImage d = imgs[__ldg(tile_img + t)];
-        const int local = t - d.tile_base;
-        const int ty = local / d.tiles_x, tx = local - ty * d.tiles_x;
-        const int y0 = ty * var_th(d.var), x0 = tx * kTileW;
-        switch (d.ks) {
-            case 1: run_tile_v<T, 1>(d, y0, x0, smem); break;
-            case 3: run_tile_v<T, 3>(d, y0, x0, smem); break;
-            case 5: run_tile_v<T, 5>(d, y0, x0, smem); break;
-            case 7: run_tile_v<T, 7>(d, y0, x0, smem); break;
-            case 9: run_tile_v<T, 9>(d, y0, x0, smem); break;
-            case 11: run_tile_v<T, 11>(d, y0, x0, smem); break;
-            case 13: run_tile_v<T, 13>(d, y0, x0, smem); break;
-            default: run_tile_v<T, 15>(d, y0, x0, smem); break;
+    int t = s_next;
+    if (t >= total) return;
+    __syncthreads();
+    if (threadIdx.x == 0) s_next = atomicAdd(&hdr->next, 1);
+    BatchImage d = imgs[__ldg(tile_img + t)];
+    int y0, x0;
+    tile_origin(d, t, y0, x0);
+    tile_op<T, true>(d, y0, x0, smem);
+    __syncthreads();
+    int tn = s_next;
+    for (int i = 0; t < total; ++i) {
+        float *cur = smem + (NSLOT == 2 ? (i & 1) * SLOT : 0);
+        float *nxt = smem + (NSLOT == 2 ? ((i + 1) & 1) * SLOT : 0);
+        BatchImage dn;
+        int yn = 0, xn = 0;
+        if (tn < total) {
+            dn = imgs[__ldg(tile_img + tn)];
+            tile_origin(dn, tn, yn, xn);
         }
-        __syncthreads();  // tile finished; s_t holds the next index
-        t = s_t;
+        if (NSLOT == 2 && tn < total) {
+            tile_op<T, true>(dn, yn, xn, nxt);
+            cp_async_wait_prev();  // the current tile's group has landed
+        } else {
+            cp_async_wait_all();
+        }
+        __syncthreads();  // every thread has read s_next (end of the previous iteration)
+        if (threadIdx.x == 0) s_next = atomicAdd(&hdr->next, 1);
+        tile_op<T, false>(d, y0, x0, cur);
+        __syncthreads();  // `cur` is free; s_next is visible
+        if (NSLOT == 1 && tn < total) tile_op<T, true>(dn, yn, xn, nxt);
+        t = tn;
+        d = dn;
+        y0 = yn;
+        x0 = xn;
+        tn = s_next;
     }
 }
 
-// Largest dynamic shared memory any tile body of the batched kernel needs.
-size_t batch_smem(size_t esz) {
-    size_t m = 0;
-    m = std::max(m, DirectCfg<15, 15, 16, 8, 4, 2>::smem(esz));
-    m = std::max(m, DirectCfg<7, 7, 32, 4, 8, 1>::smem(esz));
-    m = std::max(m, DirectCfg<15, 15, 16, 8, 2, 2>::smem(esz));
-    return m;
-}
+constexpr int nslot(size_t esz) { return esz == 2 ? 1 : 2; }
+
+// Dynamic shared memory of the batched kernel.
+size_t batch_smem(size_t esz) { return nslot(esz) * sizeof(float) * (size_t)slot_floats((int)esz); }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -185,9 +245,9 @@ cudaError_t capture_graph(pencil_batch *b) {
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         if (b->dtype == PENCIL_F32)
-            conv2d_batch_kernel<float><<<b->grid, BT, b->smem, cs>>>(hdr, imgs, tile_img);
+            conv2d_batch_kernel<float, 2><<<b->grid, BT, b->smem, cs>>>(hdr, imgs, tile_img);
         else
-            conv2d_batch_kernel<__half><<<b->grid, BT, b->smem, cs>>>(hdr, imgs, tile_img);
+            conv2d_batch_kernel<__half, 1><<<b->grid, BT, b->smem, cs>>>(hdr, imgs, tile_img);
         cudaError_t le = cudaGetLastError();
         e = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = le;
@@ -230,7 +290,7 @@ int pencil_batch_create(int dtype, int max_images, long long max_tiles, pencil_b
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded[i], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) {
-        auto kern = dtype == PENCIL_F32 ? conv2d_batch_kernel<float> : conv2d_batch_kernel<__half>;
+        auto kern = dtype == PENCIL_F32 ? conv2d_batch_kernel<float, 2> : conv2d_batch_kernel<__half, 1>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
         int per_sm = 0, dev = 0, sms = 0;
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT, b->smem);

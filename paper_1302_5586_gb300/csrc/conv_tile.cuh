@@ -66,9 +66,11 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v,
 
 // Stage s[r][c] = in[clamp(y0 + r)][clamp(x0 + c)] for r < SH, c < SW (as FP32).
 // x0 is a multiple of VEC, SW a multiple of VEC.  vec_ok: rows are 16-byte
-// aligned (w % VEC == 0 and the plane base is 16-byte aligned).  Chunks that
-// lie inside the row go through cp.async (all of a CTA's copies in flight at
-// once); chunks that cross an edge are gathered with clamped scalar loads.
+// aligned (w % VEC == 0 and the plane base is 16-byte aligned).  Everything
+// goes through cp.async (all of a CTA's copies in flight at once): 16-byte
+// chunks inside aligned rows; otherwise 4-byte copies per element from the
+// clamped column (FP32) or per pair (binary16 rows that are 4-byte aligned);
+// only binary16 chunks that are neither use clamped scalar loads.
 // FP32 chunks land in s directly; binary16 chunks land in the staging area
 // `s16` and are widened into s afterwards.  Ends with a barrier.
 template <typename T, int SH, int SW, int NT>
@@ -83,26 +85,49 @@ __device__ __forceinline__ void stage_issue(const T *__restrict__ src, int h, in
         const int gr = clampi(y0 + r, 0, h - 1);
         const int gc = x0 + q * V;
         const T *row = src + (size_t)gr * (size_t)w;
-        if (vec_ok && gc >= 0 && gc + V <= w) {
+        const bool inside = gc >= 0 && gc + V <= w;
+        if (vec_ok && inside) {
             if (F16)
                 cp_async16(s16 + r * SW + q * V, row + gc);
             else
                 cp_async16(s + r * SW + q * V, row + gc);
-        } else if (F16) {
+        } else if (!F16) {
+            // unaligned row or a chunk across the edge: one 4-byte copy per
+            // element, from the clamped column
+            float *d = s + r * SW + q * V;
+#pragma unroll
+            for (int e = 0; e < V; ++e) cp_async4(d + e, row + clampi(gc + e, 0, w - 1));
+        } else if (inside && ((uintptr_t)(row + gc) & 3) == 0) {
+            // binary16 row that is only 4-byte aligned: pairs of elements
+            T *d16 = s16 + r * SW + q * V;
+#pragma unroll
+            for (int e = 0; e < V; e += 2) cp_async4(d16 + e, row + gc + e);
+        } else {
             T *d16 = s16 + r * SW + q * V;  // raw binary16 values, widened below
 #pragma unroll
             for (int e = 0; e < V; ++e) d16[e] = row[clampi(gc + e, 0, w - 1)];
-        } else {
+        }
+    }
+    cp_async_commit();
+}
+
+// After the copies of a staged tile have landed and a barrier: widen a
+// binary16 tile into s (no-op for FP32).  Ends with a barrier for binary16.
+template <typename T, int SH, int SW, int NT>
+__device__ __forceinline__ void stage_widen(float *__restrict__ s, const T *__restrict__ s16) {
+    constexpr int V = Io<T>::VEC;
+    constexpr int CPR = SW / V;
+    if (sizeof(T) == 2) {
+        for (int idx = threadIdx.x; idx < SH * CPR; idx += NT) {
             float v[V];
-#pragma unroll
-            for (int e = 0; e < V; ++e) v[e] = Io<T>::ld(row + clampi(gc + e, 0, w - 1));
-            float *d = s + r * SW + q * V;
+            Io<T>::ld16s(s16 + idx * V, v);
+            float *d = s + idx * V;
 #pragma unroll
             for (int e = 0; e < V; e += 4)
                 *reinterpret_cast<float4 *>(d + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
         }
+        __syncthreads();
     }
-    cp_async_commit();
 }
 
 // Second half of staging: wait for this thread's copies, then (binary16)
@@ -128,9 +153,11 @@ __device__ __forceinline__ void stage_finish(float *__restrict__ s, const T *__r
 
 // Stage s[r][c] = in[clamp(y0 + r)][clamp(x0 + c)] for r < SH, c < SW (as FP32).
 // x0 is a multiple of VEC, SW a multiple of VEC.  vec_ok: rows are 16-byte
-// aligned (w % VEC == 0 and the plane base is 16-byte aligned).  Chunks that
-// lie inside the row go through cp.async (all of a CTA's copies in flight at
-// once); chunks that cross an edge are gathered with clamped scalar loads.
+// aligned (w % VEC == 0 and the plane base is 16-byte aligned).  Everything
+// goes through cp.async (all of a CTA's copies in flight at once): 16-byte
+// chunks inside aligned rows; otherwise 4-byte copies per element from the
+// clamped column (FP32) or per pair (binary16 rows that are 4-byte aligned);
+// only binary16 chunks that are neither use clamped scalar loads.
 // FP32 chunks land in s directly; binary16 chunks land in the staging area
 // `s16` and are widened into s afterwards.  Ends with a barrier.
 template <typename T, int SH, int SW, int NT>
@@ -260,6 +287,19 @@ __device__ __forceinline__ void direct_compute(const float *__restrict__ s_in,
 #pragma unroll
             for (int c = 0; c < 4; ++c) blk[o][c] = acc[o][g * 4 + c];
         store_block<T, R>(dst, h, w, y0 + ty * R, x0 + g * GS + tx * C, vec_ok, blk);
+    }
+}
+
+// Filter rows into shared memory with 4-byte cp.async (part of the caller's
+// next commit group), each padded with zeros to KWP.
+template <int KH, int KW, int KWP, int NT>
+__device__ __forceinline__ void stage_filter_async(const float *__restrict__ k, float *__restrict__ s_k) {
+    for (int t = threadIdx.x; t < KH * KWP; t += NT) {
+        const int a = t / KWP, b = t - a * KWP;
+        if (b < KW)
+            cp_async4(s_k + t, k + a * KW + b);
+        else
+            s_k[t] = 0.0f;
     }
 }
 
