@@ -193,7 +193,7 @@ def run_ours(args, rank, world, local_rank):
             pg.pencil_conv2d_ex(C, H, W, d_img, K, K, dk, d_out[n], pg.PENCIL_F32, 0, sraw)
             if K == 15 and ev15 is not None:
                 ev15[1].record(stream)
-        pg.pencil_conv2d_sep_ex(C, H, W, d_img, 15, d_g, 15, d_g, d_out[-1], pg.PENCIL_F32, sraw)
+        pg.pencil_conv2d_sep_ex(C, H, W, d_img, 15, d_g, 15, d_g, d_out[-1], pg.PENCIL_F32, 0, sraw)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -287,7 +287,7 @@ def measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g, serve_seconds=SE
                            "hbm_frac": round(8 * PX_PER_PASS / (ms * 1e-3) / 1e9 / hbm, 4),
                            "fp32_frac": round(2 * K * K * PX_PER_PASS / (ms * 1e-3) / 1e12 / fp32_peak_tflops(), 4)}
     ms = _time_stream(torch, stream, lambda: pg.pencil_conv2d_sep_ex(C, H, W, d_img, 15, d_g, 15, d_g, d_out[0],
-                                                                     pg.PENCIL_F32, sraw), 10)
+                                                                     pg.PENCIL_F32, 0, sraw), 10)
     per["gauss15-sep"] = {"ms": round(ms, 4), "gpx_s": round(PX_PER_PASS / ms / 1e6, 2),
                           "hbm_frac": round(8 * PX_PER_PASS / (ms * 1e-3) / 1e9 / hbm, 4)}
     out["passes_f32"] = per
@@ -301,7 +301,7 @@ def measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g, serve_seconds=SE
         per16[f"{K}x{K}"] = {"ms": round(ms, 4), "gpx_s": round(PX_PER_PASS / ms / 1e6, 2),
                              "hbm_frac": round(4 * PX_PER_PASS / (ms * 1e-3) / 1e9 / hbm, 4)}
     ms = _time_stream(torch, stream, lambda: pg.pencil_conv2d_sep_ex(C, H, W, d16, 15, d_g, 15, d_g, o16,
-                                                                     pg.PENCIL_F16, sraw), 10)
+                                                                     pg.PENCIL_F16, 0, sraw), 10)
     per16["gauss15-sep"] = {"ms": round(ms, 4), "gpx_s": round(PX_PER_PASS / ms / 1e6, 2),
                             "hbm_frac": round(4 * PX_PER_PASS / (ms * 1e-3) / 1e9 / hbm, 4)}
     out["passes_f16"] = per16

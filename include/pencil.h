@@ -63,6 +63,22 @@ enum { PENCIL_F32 = 0, PENCIL_F16 = 1 };
  * that the fixed per-pixel order can be checked across kernels. */
 #define PENCIL_CONV_GENERIC 1
 
+/* Border modes for the _ex conv2d calls, passed in flags as PENCIL_BORDER(m);
+ * index i of an axis of length n reads (the plain calls always clamp):
+ *   CLAMP    clamp(i) to [0, n-1]           a a | a b c d | d d
+ *   ZERO     a zero outside [0, n-1]        0 0 | a b c d | 0 0
+ *   REFLECT  edge repeated, period 2n       b a | a b c d | d c
+ *   MIRROR   edge not repeated, period 2n-2 c b | a b c d | c b
+ *   WRAP     periodic, period n             c d | a b c d | a b
+ * The modes other than CLAMP are the "other border modes" of image DSLs
+ * (Sec. 1); they change only which input values a window reads. */
+#define PENCIL_BORDER_CLAMP 0
+#define PENCIL_BORDER_ZERO 1
+#define PENCIL_BORDER_REFLECT 2
+#define PENCIL_BORDER_MIRROR 3
+#define PENCIL_BORDER_WRAP 4
+#define PENCIL_BORDER(m) ((m) << 8)
+
 /* Largest filter side the specialised kernels handle; larger (or non-square)
  * filters take the generic kernel, which has no size limit. */
 #define PENCIL_MAX_SPECIALISED_K 15
@@ -89,8 +105,8 @@ int pencil_conv2d(int h, int w, PENCIL_ARR2(const float, in, h, w), int kh, int 
 /* Stream-ordered, c planar channels, storage dtype PENCIL_F32 or PENCIL_F16
  * (binary16 images; FP32 accumulation; binary16 results rounded to nearest
  * even).  in, out: c*h*w elements of dtype, device memory; k: kh*kw FP32,
- * device memory.  flags: 0 or PENCIL_CONV_GENERIC.  Errors: ARG, NULL, ALIAS,
- * PTR, CUDA. */
+ * device memory.  flags: PENCIL_CONV_GENERIC and/or one PENCIL_BORDER(m).
+ * Errors: ARG, NULL, ALIAS, PTR, CUDA. */
 int pencil_conv2d_ex(int c, int h, int w, const void *in, int kh, int kw, const float *k,
                      void *out, int dtype, int flags, void *stream);
 
@@ -105,10 +121,10 @@ int pencil_conv2d_sep(int h, int w, PENCIL_ARR2(const float, in, h, w), int kx, 
                       int ky, const float *gy, PENCIL_ARR2(float, out, h, w));
 
 /* Stream-ordered separable filter over c planar channels of dtype
- * PENCIL_F32 or PENCIL_F16; every array is device memory.
- * Errors: ARG, NULL, ALIAS, PTR, UNSUPPORTED, CUDA. */
+ * PENCIL_F32 or PENCIL_F16; every array is device memory.  flags: 0 or one
+ * PENCIL_BORDER(m).  Errors: ARG, NULL, ALIAS, PTR, UNSUPPORTED, CUDA. */
 int pencil_conv2d_sep_ex(int c, int h, int w, const void *in, int kx, const float *gx, int ky,
-                         const float *gy, void *out, int dtype, void *stream);
+                         const float *gy, void *out, int dtype, int flags, void *stream);
 
 /* ------------------------------------------------------------------- batch
  * Many images, each with its own size and odd filter side 1..15, convolved in

@@ -64,6 +64,8 @@ def lib():
     L.oracle_f64_to_f16_array.argtypes = [i64, vp, vp]
     L.oracle_conv2d.argtypes = [i64, i64, i64, vp, i32, i32, i32, vp, dp, dp]
     L.oracle_conv2d.restype = i32
+    L.oracle_conv2d_mode.argtypes = [i64, i64, i64, vp, i32, i32, i32, vp, dp, dp, i32]
+    L.oracle_conv2d_mode.restype = i32
     L.oracle_conv2d_sep.argtypes = [i64, i64, i64, vp, i32, i32, vp, i32, vp, dp, dp]
     L.oracle_conv2d_sep.restype = i32
     L.oracle_conv2d_points.argtypes = [i64, i64, i64, vp, i32, i32, i32, vp, i64, vp, dp, dp]
@@ -125,17 +127,21 @@ def f64_to_f16(x: np.ndarray) -> np.ndarray:
     return out.reshape(np.shape(x))
 
 
-def conv2d(img: np.ndarray, k: np.ndarray, want_bound: bool = True):
-    """Clamp-to-edge correlation of every planar channel with k (FP64).
+BORDER = {"clamp": 0, "zero": 1, "reflect": 2, "mirror": 3, "wrap": 4}
 
-    Returns (out, bound) shaped like img ([h][w] inputs give [1][h][w])."""
+
+def conv2d(img: np.ndarray, k: np.ndarray, want_bound: bool = True, border: str = "clamp"):
+    """Correlation of every planar channel with k (FP64) under a border mode
+    (clamp-to-edge by default).  Returns (out, bound) shaped like img
+    ([h][w] inputs give [1][h][w])."""
     x, dt = _image(img)
     kk = np.ascontiguousarray(k, dtype=np.float32)
     c, h, w = x.shape
     kh, kw = kk.shape
     out = np.empty((c, h, w), dtype=np.float64)
     bound = np.empty((c, h, w), dtype=np.float64) if want_bound else None
-    rc = lib().oracle_conv2d(c, h, w, _ptr(x), dt, kh, kw, _ptr(kk), _ptr(out), _ptr(bound))
+    rc = lib().oracle_conv2d_mode(c, h, w, _ptr(x), dt, kh, kw, _ptr(kk), _ptr(out), _ptr(bound),
+                                  BORDER[border])
     if rc != 0:
         raise ValueError("oracle_conv2d rejected its arguments")
     return out, bound

@@ -16,7 +16,8 @@
  * regular motif, Sec. 2).  The readings taken here:
  *   conv2d   out[i][j] = sum_a sum_b k[a][b] * in[clamp(i+a-kh/2)][clamp(j+b-kw/2)]
  *            -- correlation (no flip), anchor (kh/2, kw/2) in integer division,
- *            clamp-to-edge per axis, the same filter on every planar channel;
+ *            clamp-to-edge per axis (other border modes: see border_index),
+ *            the same filter on every planar channel;
  *            bound[i][j] = sum_a sum_b |k[a][b]| * |in[...]|.
  *   jacobi   the 5-point average (up + down + left + right) / 4 on the interior,
  *            boundary ring fixed, two buffers (a Jacobi step, not Gauss-Seidel);
@@ -122,24 +123,51 @@ static int64_t clamp64(int64_t v, int64_t lo, int64_t hi)
     return v < lo ? lo : (v > hi ? hi : v);
 }
 
+/* Border modes: where index i of an axis of length n lands, or -1 for a
+ * zero value.
+ *   0 clamp   a a a | a b c d | d d d     (replicate the edge)
+ *   1 zero    0 0 0 | a b c d | 0 0 0
+ *   2 reflect c b a | a b c d | d c b     (edge repeated; period 2n)
+ *   3 mirror  d c b | a b c d | c b a     (edge not repeated; period 2n-2)
+ *   4 wrap    b c d | a b c d | a b c     (periodic; period n)  */
+static int64_t border_index(int64_t i, int64_t n, int mode)
+{
+    if (i >= 0 && i < n) return i;
+    switch (mode) {
+    case 1: return -1;
+    case 2: {
+        int64_t p = 2 * n, j = ((i % p) + p) % p;
+        return j < n ? j : p - 1 - j;
+    }
+    case 3: {
+        if (n == 1) return 0;
+        int64_t p = 2 * n - 2, j = ((i % p) + p) % p;
+        return j < n ? j : p - j;
+    }
+    case 4: return ((i % n) + n) % n;
+    default: return clamp64(i, 0, n - 1);
+    }
+}
+
 static double load_px(const void *in, int dtype, int64_t idx)
 {
     if (dtype == ORACLE_DT_F16) return oracle_f16_to_f64(((const uint16_t *)in)[idx]);
     return (double)((const float *)in)[idx];
 }
 
-/* One output pixel of one channel plane (base = first element of the plane). */
+/* One output pixel of one channel plane (base = first element of the plane);
+ * window positions that the border mode maps to zero contribute nothing. */
 static void conv_pixel(int64_t h, int64_t w, const void *in, int dtype, int64_t base,
                        int kh, int kw, const double *k, int64_t i, int64_t j,
-                       double *out, double *bound)
+                       double *out, double *bound, int mode)
 {
     const int ah = kh / 2, aw = kw / 2;
     double s = 0.0, b = 0.0;
     for (int a = 0; a < kh; ++a) {
-        const int64_t r = clamp64(i + a - ah, 0, h - 1);
+        const int64_t r = border_index(i + a - ah, h, mode);
         for (int bb = 0; bb < kw; ++bb) {
-            const int64_t c = clamp64(j + bb - aw, 0, w - 1);
-            const double x = load_px(in, dtype, base + r * w + c);
+            const int64_t c = border_index(j + bb - aw, w, mode);
+            const double x = (r < 0 || c < 0) ? 0.0 : load_px(in, dtype, base + r * w + c);
             const double wt = k[a * kw + bb];
             s += wt * x;
             b += fabs(wt) * fabs(x);
@@ -150,7 +178,7 @@ static void conv_pixel(int64_t h, int64_t w, const void *in, int dtype, int64_t 
 }
 
 static void conv_planes(int64_t nc, int64_t h, int64_t w, const void *in, int dtype,
-                        int kh, int kw, const double *k, double *out, double *bound)
+                        int kh, int kw, const double *k, double *out, double *bound, int mode)
 {
     const int64_t rows = nc * h;
 #pragma omp parallel for schedule(dynamic, 4)
@@ -159,7 +187,7 @@ static void conv_planes(int64_t nc, int64_t h, int64_t w, const void *in, int dt
         const int64_t base = ch * h * w;
         for (int64_t j = 0; j < w; ++j)
             conv_pixel(h, w, in, dtype, base, kh, kw, k, i, j, out + base + i * w + j,
-                       bound ? bound + base + i * w + j : NULL);
+                       bound ? bound + base + i * w + j : NULL, mode);
     }
 }
 
@@ -171,19 +199,27 @@ static double *widen_filter(int kh, int kw, const float *k)
     return kd;
 }
 
-/* Direct correlation with clamp-to-edge over nc planar channels.
+/* Direct correlation over nc planar channels with border mode `mode`
+ * (0 clamp-to-edge, 1 zero, 2 reflect, 3 mirror, 4 wrap).
  * in: nc*h*w values (FP32 or binary16 bits), k: kh*kw FP32 weights row-major,
  * out/bound: nc*h*w doubles (bound may be NULL).  Returns 0, or -1 on bad
  * arguments or allocation failure. */
+int oracle_conv2d_mode(int64_t nc, int64_t h, int64_t w, const void *in, int dtype,
+                       int kh, int kw, const float *k, double *out, double *bound, int mode)
+{
+    if (nc < 0 || h <= 0 || w <= 0 || kh <= 0 || kw <= 0 || mode < 0 || mode > 4) return -1;
+    double *kd = widen_filter(kh, kw, k);
+    if (!kd) return -1;
+    conv_planes(nc, h, w, in, dtype, kh, kw, kd, out, bound, mode);
+    free(kd);
+    return 0;
+}
+
+/* Clamp-to-edge correlation (mode 0). */
 int oracle_conv2d(int64_t nc, int64_t h, int64_t w, const void *in, int dtype,
                   int kh, int kw, const float *k, double *out, double *bound)
 {
-    if (nc < 0 || h <= 0 || w <= 0 || kh <= 0 || kw <= 0) return -1;
-    double *kd = widen_filter(kh, kw, k);
-    if (!kd) return -1;
-    conv_planes(nc, h, w, in, dtype, kh, kw, kd, out, bound);
-    free(kd);
-    return 0;
+    return oracle_conv2d_mode(nc, h, w, in, dtype, kh, kw, k, out, bound, 0);
 }
 
 /* Separable filter: the 2-D weight array is the outer product gy[a] * gx[b]
@@ -198,7 +234,7 @@ int oracle_conv2d_sep(int64_t nc, int64_t h, int64_t w, const void *in, int dtyp
     if (!kd) return -1;
     for (int a = 0; a < ky; ++a)
         for (int b = 0; b < kx; ++b) kd[a * kx + b] = (double)gy[a] * (double)gx[b];
-    conv_planes(nc, h, w, in, dtype, ky, kx, kd, out, bound);
+    conv_planes(nc, h, w, in, dtype, ky, kx, kd, out, bound, 0);
     free(kd);
     return 0;
 }
@@ -217,7 +253,7 @@ int oracle_conv2d_points(int64_t nc, int64_t h, int64_t w, const void *in, int d
     for (int64_t p = 0; p < npts; ++p) {
         const int64_t ch = pts[3 * p], i = pts[3 * p + 1], j = pts[3 * p + 2];
         if (ch < 0 || ch >= nc || i < 0 || i >= h || j < 0 || j >= w) { bad = 1; continue; }
-        conv_pixel(h, w, in, dtype, ch * h * w, kh, kw, kd, i, j, out + p, bound ? bound + p : NULL);
+        conv_pixel(h, w, in, dtype, ch * h * w, kh, kw, kd, i, j, out + p, bound ? bound + p : NULL, 0);
     }
     free(kd);
     return bad ? -1 : 0;
@@ -238,7 +274,7 @@ int oracle_conv2d_sep_points(int64_t nc, int64_t h, int64_t w, const void *in, i
     for (int64_t p = 0; p < npts; ++p) {
         const int64_t ch = pts[3 * p], i = pts[3 * p + 1], j = pts[3 * p + 2];
         if (ch < 0 || ch >= nc || i < 0 || i >= h || j < 0 || j >= w) { bad = 1; continue; }
-        conv_pixel(h, w, in, dtype, ch * h * w, ky, kx, kd, i, j, out + p, bound ? bound + p : NULL);
+        conv_pixel(h, w, in, dtype, ch * h * w, ky, kx, kd, i, j, out + p, bound ? bound + p : NULL, 0);
     }
     free(kd);
     return bad ? -1 : 0;

@@ -10,7 +10,9 @@ Python binding of that ABI plus the batching and serving layers built on it.
 from ._binding import (  # noqa: F401
     HEADER,
     LIB_PATH,
+    BORDER_MODES,
     PENCIL_BATCH_VARIANTS,
+    PENCIL_BORDER,
     PENCIL_CONV_GENERIC,
     PENCIL_F16,
     PENCIL_F32,

@@ -20,6 +20,12 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "pencil.h")
 PENCIL_F32 = 0
 PENCIL_F16 = 1
 PENCIL_CONV_GENERIC = 1
+PENCIL_BORDER_CLAMP, PENCIL_BORDER_ZERO, PENCIL_BORDER_REFLECT, PENCIL_BORDER_MIRROR, PENCIL_BORDER_WRAP = range(5)
+BORDER_MODES = {"clamp": 0, "zero": 1, "reflect": 2, "mirror": 3, "wrap": 4}
+
+
+def PENCIL_BORDER(m):
+    return m << 8
 PENCIL_MAX_SPECIALISED_K = 15
 
 STATUS = {
@@ -65,7 +71,7 @@ def lib():
         "pencil_conv2d": (i, [i, i, vp, i, i, vp, vp]),
         "pencil_conv2d_ex": (i, [i, i, i, vp, i, i, vp, vp, i, i, vp]),
         "pencil_conv2d_sep": (i, [i, i, vp, i, vp, i, vp, vp]),
-        "pencil_conv2d_sep_ex": (i, [i, i, i, vp, i, vp, i, vp, vp, i, vp]),
+        "pencil_conv2d_sep_ex": (i, [i, i, i, vp, i, vp, i, vp, vp, i, i, vp]),
         "pencil_jacobi2d": (i, [i, i, vp, i]),
         "pencil_jacobi2d_workspace_size": (sz, [i, i]),
         "pencil_jacobi2d_ex": (i, [i, i, vp, i, i, d, vp, sz, i, vp]),
@@ -144,9 +150,9 @@ def pencil_conv2d_sep(h, w, in_, kx, gx, ky, gy, out):
            "pencil_conv2d_sep")
 
 
-def pencil_conv2d_sep_ex(c, h, w, in_, kx, gx, ky, gy, out, dtype, stream=None):
+def pencil_conv2d_sep_ex(c, h, w, in_, kx, gx, ky, gy, out, dtype, flags=0, stream=None):
     _check(lib().pencil_conv2d_sep_ex(c, h, w, _ptr(in_), kx, _ptr(gx), ky, _ptr(gy), _ptr(out), dtype,
-                                      _stream(stream)), "pencil_conv2d_sep_ex")
+                                      flags, _stream(stream)), "pencil_conv2d_sep_ex")
 
 
 def pencil_jacobi2d(h, w, u, iters):

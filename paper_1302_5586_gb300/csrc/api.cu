@@ -192,7 +192,10 @@ void pencil_shutdown(void) {
 
 int pencil_conv2d_ex(int c, int h, int w, const void *in, int kh, int kw, const float *k, void *out,
                      int dtype, int flags, void *stream) {
-    if (c <= 0 || kh <= 0 || kw <= 0 || (flags & ~PENCIL_CONV_GENERIC) != 0) return PENCIL_ERR_ARG;
+    const int border = (flags >> 8) & 0xF;
+    if (c <= 0 || kh <= 0 || kw <= 0 || (flags & ~(PENCIL_CONV_GENERIC | 0xF00)) != 0 ||
+        border > PENCIL_BORDER_WRAP)
+        return PENCIL_ERR_ARG;
     if (dtype != PENCIL_F32 && dtype != PENCIL_F16) return PENCIL_ERR_ARG;
     int st = check_dims(h, w);
     if (st) return st;
@@ -203,14 +206,16 @@ int pencil_conv2d_ex(int c, int h, int w, const void *in, int kh, int kw, const 
     if (kind_of(in) != Mem::Device || kind_of(out) != Mem::Device || kind_of(k) != Mem::Device)
         return PENCIL_ERR_PTR;
     cudaError_t e = (flags & PENCIL_CONV_GENERIC)
-                        ? launch_conv2d_generic(dtype, c, h, w, in, kh, kw, k, out, (cudaStream_t)stream)
-                        : launch_conv2d(dtype, c, h, w, in, kh, kw, k, out, (cudaStream_t)stream);
+                        ? launch_conv2d_generic(dtype, c, h, w, in, kh, kw, k, out, (cudaStream_t)stream, border)
+                        : launch_conv2d(dtype, c, h, w, in, kh, kw, k, out, (cudaStream_t)stream, border);
     return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
 }
 
 int pencil_conv2d_sep_ex(int c, int h, int w, const void *in, int kx, const float *gx, int ky,
-                         const float *gy, void *out, int dtype, void *stream) {
-    if (c <= 0 || kx <= 0 || ky <= 0) return PENCIL_ERR_ARG;
+                         const float *gy, void *out, int dtype, int flags, void *stream) {
+    const int border = (flags >> 8) & 0xF;
+    if (c <= 0 || kx <= 0 || ky <= 0 || (flags & ~0xF00) != 0 || border > PENCIL_BORDER_WRAP)
+        return PENCIL_ERR_ARG;
     if (dtype != PENCIL_F32 && dtype != PENCIL_F16) return PENCIL_ERR_ARG;
     int st = check_dims(h, w);
     if (st) return st;
@@ -223,7 +228,7 @@ int pencil_conv2d_sep_ex(int c, int h, int w, const void *in, int kx, const floa
     if (kind_of(in) != Mem::Device || kind_of(out) != Mem::Device || kind_of(gx) != Mem::Device ||
         kind_of(gy) != Mem::Device)
         return PENCIL_ERR_PTR;
-    cudaError_t e = launch_conv2d_sep(dtype, c, h, w, in, kx, gx, ky, gy, out, (cudaStream_t)stream);
+    cudaError_t e = launch_conv2d_sep(dtype, c, h, w, in, kx, gx, ky, gy, out, (cudaStream_t)stream, border);
     return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
 }
 

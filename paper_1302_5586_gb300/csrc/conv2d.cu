@@ -27,15 +27,15 @@ namespace {
 
 using namespace tile;
 
-template <typename T, int KH, int KW, int TX, int TY, int R, int G, int MINB>
+template <typename T, int KH, int KW, int TX, int TY, int R, int G, int MINB, bool ANYB>
 __global__ void __launch_bounds__(TX *TY, MINB)
     conv2d_direct_kernel(const T *__restrict__ in, const float *__restrict__ k, T *__restrict__ out,
-                         int h, int w, bool vec_ok) {
+                         int h, int w, bool vec_ok, int border) {
     using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
     extern __shared__ __align__(16) float smem[];
     const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
-    direct_tile<T, KH, KW, TX, TY, R, G>(in + plane, k, out + plane, h, w, vec_ok, blockIdx.y * Cfg::TH,
-                                         blockIdx.x * Cfg::TW, smem);
+    direct_tile<T, KH, KW, TX, TY, R, G, ANYB>(in + plane, k, out + plane, h, w, vec_ok,
+                                               blockIdx.y * Cfg::TH, blockIdx.x * Cfg::TW, smem, border);
 }
 
 // ------------------------------------------------------------ generic kernel
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
 template <typename T>
 __global__ void __launch_bounds__(256)
     conv2d_generic_kernel(const T *__restrict__ in, const float *__restrict__ k, T *__restrict__ out,
-                          int h, int w, int kh, int kw) {
+                          int h, int w, int kh, int kw, int border) {
     const int j = blockIdx.x * 32 + (threadIdx.x & 31);
     const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (i >= h || j >= w) return;
@@ -53,11 +53,15 @@ __global__ void __launch_bounds__(256)
     const int ah = kh / 2, aw = kw / 2;
     float acc = 0.0f;
     for (int a = 0; a < kh; ++a) {
-        const T *row = src + (size_t)clampi(i + a - ah, 0, h - 1) * (size_t)w;
+        const int r = border_index(i + a - ah, h, border);
+        const T *row = src + (size_t)max(r, 0) * (size_t)w;
         const float *kr = k + (size_t)a * kw;
-        float s = __fmul_rn(__ldg(kr), Io<T>::ld(row + clampi(j - aw, 0, w - 1)));
-        for (int b = 1; b < kw; ++b)
-            s = __fmaf_rn(__ldg(kr + b), Io<T>::ld(row + clampi(j + b - aw, 0, w - 1)), s);
+        auto px = [&](int b) {
+            const int c = border_index(j + b - aw, w, border);
+            return (r < 0 || c < 0) ? 0.0f : Io<T>::ld(row + c);
+        };
+        float s = __fmul_rn(__ldg(kr), px(0));
+        for (int b = 1; b < kw; ++b) s = __fmaf_rn(__ldg(kr + b), px(b), s);
         acc = __fadd_rn(acc, s);
     }
     Io<T>::st(out + plane + (size_t)i * w + j, acc);
@@ -81,10 +85,12 @@ struct SepCfg {
     static constexpr size_t smem(size_t esz) { return smem_f32 + (esz == 2 ? 2 * (size_t)SH * SW : 0); }
 };
 
-template <typename T, int KX, int KY, int TX, int TY, int R, int MINB = 1, bool INPLACE = false>
+template <typename T, int KX, int KY, int TX, int TY, int R, int MINB = 1, bool INPLACE = false,
+          bool ANYB = false>
 __global__ void __launch_bounds__(TX *TY, MINB)
     conv2d_sep_kernel(const T *__restrict__ in, const float *__restrict__ gx,
-                      const float *__restrict__ gy, T *__restrict__ out, int h, int w, bool vec_ok) {
+                      const float *__restrict__ gy, T *__restrict__ out, int h, int w, bool vec_ok,
+                      int border) {
     using Cfg = SepCfg<KX, KY, TX, TY, R, INPLACE>;
     constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, SH = Cfg::SH, TW = Cfg::TW,
                   NX = Cfg::NX, AX = Cfg::AX, AY = Cfg::AY, NT = Cfg::NT;
@@ -99,7 +105,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
     T *dst = out + plane;
     const int x0 = blockIdx.x * TW;
     const int y0 = blockIdx.y * Cfg::TH;
-    stage_tile<T, SH, SW, NT>(src, h, w, y0 - AY, x0 - P, vec_ok, s_in, s16);
+    stage_tile<T, SH, SW, NT, ANYB>(src, h, w, y0 - AY, x0 - P, vec_ok, s_in, s16, border);
 
     // row pass: t[r][q*C + c] = sum_b gx[b] * in[r][q*C + c + b - AX]
     {
@@ -182,7 +188,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
     conv2d_sep_generic_kernel(const T *__restrict__ in, const float *__restrict__ gx,
                               const float *__restrict__ gy, T *__restrict__ out, int h, int w,
-                              int kx, int ky) {
+                              int kx, int ky, int border) {
     // tile 32 x 32 outputs, 256 threads
     extern __shared__ __align__(16) float smem[];
     const int SH = 32 + ky - 1;
@@ -193,10 +199,15 @@ __global__ void __launch_bounds__(256)
     const int ax = kx / 2, ay = ky / 2;
     for (int idx = threadIdx.x; idx < SH * 32; idx += 256) {
         const int r = idx / 32, c = idx % 32;
-        const T *row = src + (size_t)clampi(y0 + r - ay, 0, h - 1) * (size_t)w;
+        const int gr = border_index(y0 + r - ay, h, border);
+        const T *row = src + (size_t)max(gr, 0) * (size_t)w;
         const int j = x0 + c;
-        float s = __fmul_rn(__ldg(gx), Io<T>::ld(row + clampi(j - ax, 0, w - 1)));
-        for (int b = 1; b < kx; ++b) s = __fmaf_rn(__ldg(gx + b), Io<T>::ld(row + clampi(j + b - ax, 0, w - 1)), s);
+        auto px = [&](int b) {
+            const int gc = border_index(j + b - ax, w, border);
+            return (gr < 0 || gc < 0) ? 0.0f : Io<T>::ld(row + gc);
+        };
+        float s = __fmul_rn(__ldg(gx), px(0));
+        for (int b = 1; b < kx; ++b) s = __fmaf_rn(__ldg(gx + b), px(b), s);
         s_t[idx] = s;
     }
     __syncthreads();
@@ -219,75 +230,77 @@ cudaError_t set_smem(Kern kern, size_t bytes) {
 
 template <typename T, int K, int TX, int TY, int R, int G = 1, int MINB = 1>
 cudaError_t run_direct(int c, int h, int w, const T *in, const float *k, T *out, bool vec_ok,
-                       cudaStream_t s) {
+                       int border, cudaStream_t s) {
     using Cfg = DirectCfg<K, K, TX, TY, R, G>;
-    auto kern = conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB>;
+    auto kern = border == 0 ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false>
+                            : conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, true>;
     const size_t smem = Cfg::smem(sizeof(T));
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((w + Cfg::TW - 1) / Cfg::TW, (h + Cfg::TH - 1) / Cfg::TH, c);
-    kern<<<grid, Cfg::NT, smem, s>>>(in, k, out, h, w, vec_ok);
+    kern<<<grid, Cfg::NT, smem, s>>>(in, k, out, h, w, vec_ok, border);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t run_direct_k(int K, int c, int h, int w, const T *in, const float *k, T *out,
-                         bool vec_ok, cudaStream_t s) {
+                         bool vec_ok, int border, cudaStream_t s) {
     // Tile shapes and register caps per side, from timing sweeps on GB300 at
     // 8192 x 8192 x 3 (small sides: occupancy for HBM streaming; large sides:
     // two column groups so each filter-row load feeds eight FMA chains).
     switch (K) {
-        case 1: return run_direct<T, 1, 32, 8, 4, 1, 8>(c, h, w, in, k, out, vec_ok, s);
-        case 3: return run_direct<T, 3, 32, 8, 4, 1, 8>(c, h, w, in, k, out, vec_ok, s);
-        case 5: return run_direct<T, 5, 32, 4, 4, 2, 6>(c, h, w, in, k, out, vec_ok, s);
-        case 7: return run_direct<T, 7, 32, 4, 8, 1, 8>(c, h, w, in, k, out, vec_ok, s);
-        case 9: return run_direct<T, 9, 32, 4, 4, 2, 3>(c, h, w, in, k, out, vec_ok, s);
-        case 11: return run_direct<T, 11, 32, 4, 4, 2, 3>(c, h, w, in, k, out, vec_ok, s);
-        case 13: return run_direct<T, 13, 32, 4, 4, 2, 3>(c, h, w, in, k, out, vec_ok, s);
-        case 15: return run_direct<T, 15, 16, 8, 4, 2, 3>(c, h, w, in, k, out, vec_ok, s);
+        case 1: return run_direct<T, 1, 32, 8, 4, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
+        case 3: return run_direct<T, 3, 32, 8, 4, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
+        case 5: return run_direct<T, 5, 32, 4, 4, 2, 6>(c, h, w, in, k, out, vec_ok, border, s);
+        case 7: return run_direct<T, 7, 32, 4, 8, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
+        case 9: return run_direct<T, 9, 32, 4, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
+        case 11: return run_direct<T, 11, 32, 4, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
+        case 13: return run_direct<T, 13, 32, 4, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
+        case 15: return run_direct<T, 15, 16, 8, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <typename T>
 cudaError_t run_generic(int c, int h, int w, const T *in, int kh, int kw, const float *k, T *out,
-                        cudaStream_t s) {
+                        int border, cudaStream_t s) {
     dim3 grid((w + 31) / 32, (h + 7) / 8, c);
-    conv2d_generic_kernel<T><<<grid, 256, 0, s>>>(in, k, out, h, w, kh, kw);
+    conv2d_generic_kernel<T><<<grid, 256, 0, s>>>(in, k, out, h, w, kh, kw, border);
     return cudaGetLastError();
 }
 
 template <typename T, int K, int TX, int TY, int R, int MINB = 1, bool INPLACE = false>
 cudaError_t run_sep(int c, int h, int w, const T *in, const float *gx, const float *gy, T *out,
-                    bool vec_ok, cudaStream_t s) {
+                    bool vec_ok, int border, cudaStream_t s) {
     using Cfg = SepCfg<K, K, TX, TY, R, INPLACE>;
-    auto kern = conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE>;
+    auto kern = border == 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false>
+                            : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true>;
     const size_t smem = Cfg::smem(sizeof(T));
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((w + Cfg::TW - 1) / Cfg::TW, (h + Cfg::TH - 1) / Cfg::TH, c);
-    kern<<<grid, Cfg::NT, smem, s>>>(in, gx, gy, out, h, w, vec_ok);
+    kern<<<grid, Cfg::NT, smem, s>>>(in, gx, gy, out, h, w, vec_ok, border);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t run_sep_any(int c, int h, int w, const T *in, int kx, const float *gx, int ky,
-                        const float *gy, T *out, bool vec_ok, cudaStream_t s) {
+                        const float *gy, T *out, bool vec_ok, int border, cudaStream_t s) {
     if (kx == ky) {
         switch (kx) {
-            case 3: return run_sep<T, 3, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
-            case 5: return run_sep<T, 5, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
-            case 7: return run_sep<T, 7, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, s);
-            case 9: return run_sep<T, 9, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, s);
-            case 11: return run_sep<T, 11, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, s);
-            case 13: return run_sep<T, 13, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, s);
-            case 15: return run_sep<T, 15, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, s);
+            case 3: return run_sep<T, 3, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 5: return run_sep<T, 5, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 7: return run_sep<T, 7, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 9: return run_sep<T, 9, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 11: return run_sep<T, 11, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 13: return run_sep<T, 13, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 15: return run_sep<T, 15, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
             default: break;
         }
     }
     const size_t smem = sizeof(float) * (size_t)(32 + ky - 1) * 32;
     dim3 grid((w + 31) / 32, (h + 31) / 32, c);
-    conv2d_sep_generic_kernel<T><<<grid, 256, smem, s>>>(in, gx, gy, out, h, w, kx, ky);
+    conv2d_sep_generic_kernel<T><<<grid, 256, smem, s>>>(in, gx, gy, out, h, w, kx, ky, border);
     return cudaGetLastError();
 }
 
@@ -298,42 +311,42 @@ bool rows_aligned(const void *p, int w, int vec) {
 }  // namespace
 
 cudaError_t launch_conv2d(int dtype, int c, int h, int w, const void *in, int kh, int kw,
-                          const float *k, void *out, cudaStream_t s) {
+                          const float *k, void *out, cudaStream_t s, int border) {
     const bool special = (kh == kw) && (kh % 2 == 1) && kh <= PENCIL_MAX_SPECIALISED_K;
     if (dtype == PENCIL_F32) {
         const float *i = static_cast<const float *>(in);
         float *o = static_cast<float *>(out);
         const bool v = rows_aligned(in, w, 4) && rows_aligned(out, w, 4);
-        if (special) return run_direct_k<float>(kh, c, h, w, i, k, o, v, s);
-        return run_generic<float>(c, h, w, i, kh, kw, k, o, s);
+        if (special) return run_direct_k<float>(kh, c, h, w, i, k, o, v, border, s);
+        return run_generic<float>(c, h, w, i, kh, kw, k, o, border, s);
     }
     const __half *i = static_cast<const __half *>(in);
     __half *o = static_cast<__half *>(out);
     const bool v = rows_aligned(in, w, 8) && rows_aligned(out, w, 8);
-    if (special) return run_direct_k<__half>(kh, c, h, w, i, k, o, v, s);
-    return run_generic<__half>(c, h, w, i, kh, kw, k, o, s);
+    if (special) return run_direct_k<__half>(kh, c, h, w, i, k, o, v, border, s);
+    return run_generic<__half>(c, h, w, i, kh, kw, k, o, border, s);
 }
 
 cudaError_t launch_conv2d_generic(int dtype, int c, int h, int w, const void *in, int kh, int kw,
-                                  const float *k, void *out, cudaStream_t s) {
+                                  const float *k, void *out, cudaStream_t s, int border) {
     if (dtype == PENCIL_F32)
         return run_generic<float>(c, h, w, static_cast<const float *>(in), kh, kw, k,
-                                  static_cast<float *>(out), s);
+                                  static_cast<float *>(out), border, s);
     return run_generic<__half>(c, h, w, static_cast<const __half *>(in), kh, kw, k,
-                               static_cast<__half *>(out), s);
+                               static_cast<__half *>(out), border, s);
 }
 
 cudaError_t launch_conv2d_sep(int dtype, int c, int h, int w, const void *in, int kx,
                               const float *gx, int ky, const float *gy, void *out,
-                              cudaStream_t s) {
+                              cudaStream_t s, int border) {
     if (dtype == PENCIL_F32) {
         const bool v = rows_aligned(in, w, 4) && rows_aligned(out, w, 4);
         return run_sep_any<float>(c, h, w, static_cast<const float *>(in), kx, gx, ky, gy,
-                                  static_cast<float *>(out), v, s);
+                                  static_cast<float *>(out), v, border, s);
     }
     const bool v = rows_aligned(in, w, 8) && rows_aligned(out, w, 8);
     return run_sep_any<__half>(c, h, w, static_cast<const __half *>(in), kx, gx, ky, gy,
-                               static_cast<__half *>(out), v, s);
+                               static_cast<__half *>(out), v, border, s);
 }
 
 }  // namespace pencil

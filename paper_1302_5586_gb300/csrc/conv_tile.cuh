@@ -64,7 +64,32 @@ struct Io<__half> {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
-// Stage s[r][c] = in[clamp(y0 + r)][clamp(x0 + c)] for r < SH, c < SW (as FP32).
+// Where index i of an axis of length n lands under a border mode, or -1 for a
+// zero value: 0 clamp (replicate the edge), 1 zero, 2 reflect (edge repeated,
+// period 2n), 3 mirror (edge not repeated, period 2n-2), 4 wrap (period n).
+// The periodic modes sit out of line: they are rare and need divisions.
+static __device__ __noinline__ int border_index_periodic(int i, int n, int mode) {
+    if (mode == 2) {
+        const int p = 2 * n, j = ((i % p) + p) % p;
+        return j < n ? j : p - 1 - j;
+    }
+    if (mode == 3) {
+        if (n == 1) return 0;
+        const int p = 2 * n - 2, j = ((i % p) + p) % p;
+        return j < n ? j : p - j;
+    }
+    return ((i % n) + n) % n;
+}
+
+__device__ __forceinline__ int border_index(int i, int n, int mode) {
+    if (i >= 0 && i < n) return i;
+    if (mode == 0) return clampi(i, 0, n - 1);
+    if (mode == 1) return -1;
+    return border_index_periodic(i, n, mode);
+}
+
+// Stage s[r][c] = in[map(y0 + r)][map(x0 + c)] for r < SH, c < SW (as FP32),
+// map = the border mode (clamp-to-edge by default; zero mode stages zeros).
 // x0 is a multiple of VEC, SW a multiple of VEC.  vec_ok: rows are 16-byte
 // aligned (w % VEC == 0 and the plane base is 16-byte aligned).  Everything
 // goes through cp.async (all of a CTA's copies in flight at once): 16-byte
@@ -73,17 +98,33 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v,
 // only binary16 chunks that are neither use clamped scalar loads.
 // FP32 chunks land in s directly; binary16 chunks land in the staging area
 // `s16` and are widened into s afterwards.  Ends with a barrier.
-template <typename T, int SH, int SW, int NT>
+// ANYB = false compiles the clamp-to-edge staging only (border ignored).
+template <typename T, int SH, int SW, int NT, bool ANYB = false>
 __device__ __forceinline__ void stage_issue(const T *__restrict__ src, int h, int w, int y0, int x0,
-                                            bool vec_ok, float *__restrict__ s, T *__restrict__ s16) {
+                                            bool vec_ok, float *__restrict__ s, T *__restrict__ s16,
+                                            int border = 0) {
     constexpr int V = Io<T>::VEC;
     constexpr int CPR = SW / V;
     constexpr bool F16 = sizeof(T) == 2;
     for (int idx = threadIdx.x; idx < SH * CPR; idx += NT) {
         const int r = idx / CPR;
         const int q = idx - r * CPR;
-        const int gr = clampi(y0 + r, 0, h - 1);
         const int gc = x0 + q * V;
+        int gr;
+        if constexpr (ANYB) {
+            gr = border_index(y0 + r, h, border);
+            if (gr < 0) {  // a row of zeros (zero border)
+                if (F16) {
+#pragma unroll
+                    for (int e = 0; e < V; ++e) s16[r * SW + q * V + e] = static_cast<T>(0.0f);
+                } else {
+                    *reinterpret_cast<float4 *>(s + r * SW + q * V) = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                continue;
+            }
+        } else {
+            gr = clampi(y0 + r, 0, h - 1);
+        }
         const T *row = src + (size_t)gr * (size_t)w;
         const bool inside = gc >= 0 && gc + V <= w;
         if (vec_ok && inside) {
@@ -93,10 +134,20 @@ __device__ __forceinline__ void stage_issue(const T *__restrict__ src, int h, in
                 cp_async16(s + r * SW + q * V, row + gc);
         } else if (!F16) {
             // unaligned row or a chunk across the edge: one 4-byte copy per
-            // element, from the clamped column
+            // element, from the column the border mode selects
             float *d = s + r * SW + q * V;
 #pragma unroll
-            for (int e = 0; e < V; ++e) cp_async4(d + e, row + clampi(gc + e, 0, w - 1));
+            for (int e = 0; e < V; ++e) {
+                if constexpr (ANYB) {
+                    const int c = border_index(gc + e, w, border);
+                    if (c < 0)
+                        d[e] = 0.0f;
+                    else
+                        cp_async4(d + e, row + c);
+                } else {
+                    cp_async4(d + e, row + clampi(gc + e, 0, w - 1));
+                }
+            }
         } else if (inside && ((uintptr_t)(row + gc) & 3) == 0) {
             // binary16 row that is only 4-byte aligned: pairs of elements
             T *d16 = s16 + r * SW + q * V;
@@ -105,7 +156,14 @@ __device__ __forceinline__ void stage_issue(const T *__restrict__ src, int h, in
         } else {
             T *d16 = s16 + r * SW + q * V;  // raw binary16 values, widened below
 #pragma unroll
-            for (int e = 0; e < V; ++e) d16[e] = row[clampi(gc + e, 0, w - 1)];
+            for (int e = 0; e < V; ++e) {
+                if constexpr (ANYB) {
+                    const int c = border_index(gc + e, w, border);
+                    d16[e] = c < 0 ? static_cast<T>(0.0f) : row[c];
+                } else {
+                    d16[e] = row[clampi(gc + e, 0, w - 1)];
+                }
+            }
         }
     }
     cp_async_commit();
@@ -151,7 +209,8 @@ __device__ __forceinline__ void stage_finish(float *__restrict__ s, const T *__r
     __syncthreads();
 }
 
-// Stage s[r][c] = in[clamp(y0 + r)][clamp(x0 + c)] for r < SH, c < SW (as FP32).
+// Stage s[r][c] = in[map(y0 + r)][map(x0 + c)] for r < SH, c < SW (as FP32),
+// map = the border mode (clamp-to-edge by default; zero mode stages zeros).
 // x0 is a multiple of VEC, SW a multiple of VEC.  vec_ok: rows are 16-byte
 // aligned (w % VEC == 0 and the plane base is 16-byte aligned).  Everything
 // goes through cp.async (all of a CTA's copies in flight at once): 16-byte
@@ -160,10 +219,11 @@ __device__ __forceinline__ void stage_finish(float *__restrict__ s, const T *__r
 // only binary16 chunks that are neither use clamped scalar loads.
 // FP32 chunks land in s directly; binary16 chunks land in the staging area
 // `s16` and are widened into s afterwards.  Ends with a barrier.
-template <typename T, int SH, int SW, int NT>
+template <typename T, int SH, int SW, int NT, bool ANYB = false>
 __device__ __forceinline__ void stage_tile(const T *__restrict__ src, int h, int w, int y0, int x0,
-                                           bool vec_ok, float *__restrict__ s, T *__restrict__ s16) {
-    stage_issue<T, SH, SW, NT>(src, h, w, y0, x0, vec_ok, s, s16);
+                                           bool vec_ok, float *__restrict__ s, T *__restrict__ s16,
+                                           int border = 0) {
+    stage_issue<T, SH, SW, NT, ANYB>(src, h, w, y0, x0, vec_ok, s, s16, border);
     stage_finish<T, SH, SW, NT>(s, s16);
 }
 
@@ -315,17 +375,17 @@ __device__ __forceinline__ void stage_filter(const float *__restrict__ k, float 
 // One TH x TW output tile with origin (y0, x0) of one plane: stage, compute,
 // store.  Called by every thread of an NT-thread block (it contains barriers);
 // `smem` must hold DirectCfg::smem(sizeof(T)) bytes.
-template <typename T, int KH, int KW, int TX, int TY, int R, int G>
+template <typename T, int KH, int KW, int TX, int TY, int R, int G, bool ANYB = false>
 __device__ __forceinline__ void direct_tile(const T *__restrict__ src, const float *__restrict__ k,
                                             T *__restrict__ dst, int h, int w, bool vec_ok, int y0,
-                                            int x0, float *__restrict__ smem) {
+                                            int x0, float *__restrict__ smem, int border = 0) {
     using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
     constexpr int SW = Cfg::SW, SH = Cfg::SH, KWP = Cfg::KWP, AH = Cfg::AH, P = Cfg::P;
     float *s_in = smem;
     float *s_k = smem + SH * SW;
     T *s16 = reinterpret_cast<T *>(smem + SH * SW + KH * KWP);
     stage_filter<KH, KW, KWP, Cfg::NT>(k, s_k);
-    stage_tile<T, SH, SW, Cfg::NT>(src, h, w, y0 - AH, x0 - P, vec_ok, s_in, s16);
+    stage_tile<T, SH, SW, Cfg::NT, ANYB>(src, h, w, y0 - AH, x0 - P, vec_ok, s_in, s16, border);
     direct_compute<T, KH, KW, TX, TY, R, G>(s_in, s_k, dst, h, w, vec_ok, y0, x0);
 }
 

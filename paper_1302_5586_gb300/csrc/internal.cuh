@@ -42,14 +42,15 @@ __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wa
 // ----------------------------------------------------------------- conv2d
 // All launchers queue work on `s` and return the launch status.
 // Arrays are device memory; the host layer has validated sizes and pointers.
+// border: 0 clamp-to-edge, 1 zero, 2 reflect, 3 mirror, 4 wrap.
 cudaError_t launch_conv2d(int dtype, int c, int h, int w, const void *in, int kh, int kw,
-                          const float *k, void *out, cudaStream_t s);
+                          const float *k, void *out, cudaStream_t s, int border = 0);
 // Force the generic (any-size) kernel; used by tests of the fixed-order rule.
 cudaError_t launch_conv2d_generic(int dtype, int c, int h, int w, const void *in, int kh, int kw,
-                                  const float *k, void *out, cudaStream_t s);
+                                  const float *k, void *out, cudaStream_t s, int border = 0);
 cudaError_t launch_conv2d_sep(int dtype, int c, int h, int w, const void *in, int kx,
                               const float *gx, int ky, const float *gy, void *out,
-                              cudaStream_t s);
+                              cudaStream_t s, int border = 0);
 
 // ----------------------------------------------------------------- jacobi
 size_t jacobi_workspace_bytes(int h, int w);

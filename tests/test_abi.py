@@ -58,7 +58,9 @@ def test_conv2d_argument_errors_before_cuda(lib, args, status):
 def test_ex_argument_errors_before_cuda(lib):
     assert lib.pencil_conv2d_ex(1, 4, 4, 1, 3, 3, 2, 3, 7, 0, None) == -1   # bad dtype
     assert lib.pencil_conv2d_ex(1, 4, 4, 1, 3, 3, 2, 3, 0, 4, None) == -1   # unknown flag
-    assert lib.pencil_conv2d_sep_ex(1, 4, 4, 1, 17, 2, 3, 3, 5, 0, None) == -8  # side > 15
+    assert lib.pencil_conv2d_sep_ex(1, 4, 4, 1, 17, 2, 3, 3, 5, 0, 0, None) == -8  # side > 15
+    assert lib.pencil_conv2d_ex(1, 4, 4, 1, 3, 3, 2, 3, 0, 5 << 8, None) == -1   # border mode 5
+    assert lib.pencil_conv2d_sep_ex(1, 4, 4, 1, 3, 2, 3, 3, 5, 0, 1, None) == -1  # generic flag not allowed
     assert lib.pencil_conv2d_sep(4, 4, 1, 3, 2, 16, 3, 5) == -8
     assert lib.pencil_jacobi2d_ex(4, 4, 1, -1, 0, None, 256, 1 << 20, 0, None) == -1
     assert lib.pencil_jacobi2d_ex(4, 4, 1, 10, 5, None, 256, 1 << 20, 0, None) == -2  # no res_out

@@ -240,3 +240,35 @@ def test_rejects_bad_arguments():
         oracle.conv2d(np.zeros((1, 0, 3), dtype=np.float32), np.ones((3, 3), dtype=np.float32))
     with pytest.raises(ValueError):
         oracle.conv2d(np.zeros((1, 2, 3), dtype=np.float32), np.ones((0, 3), dtype=np.float32))
+
+
+SCIPY_MODE = {"clamp": "nearest", "zero": "constant", "reflect": "reflect", "mirror": "mirror", "wrap": "wrap"}
+
+
+@pytest.mark.parametrize("border", ["clamp", "zero", "reflect", "mirror", "wrap"])
+@pytest.mark.parametrize("seed", range(12))
+def test_border_modes_match_scipy(border, seed):
+    """Each border mode against scipy.ndimage.correlate's mode of the same
+    meaning, including filters larger than the image (repeated reflection)."""
+    r = _rng(300 + seed)
+    h, w = r.integers(1, 9, size=2)
+    kh, kw = r.integers(1, 12, size=2)
+    img = r.standard_normal((h, w)).astype(np.float32)
+    k = r.standard_normal((kh, kw)).astype(np.float32)
+    out, bound = oracle.conv2d(img, k, border=border)
+    ref = ndi.correlate(img.astype(np.float64), k.astype(np.float64), mode=SCIPY_MODE[border], cval=0.0)
+    assert np.all(np.abs(out[0] - ref) <= 1e-13 * bound[0] + 1e-300)
+
+
+def test_border_modes_hand_row():
+    """One row [1, 2, 3], filter [1, 10, 100, 1000, 10000] (anchor 2): the two
+    columns past each edge read, per mode: clamp 1 1 | 3 3, zero 0 0 | 0 0,
+    reflect 2 1 | 3 2, mirror 3 2 | 2 1, wrap 2 3 | 1 2."""
+    img = np.array([[1, 2, 3]], dtype=np.float32)
+    k = np.array([[1, 10, 100, 1000, 10000]], dtype=np.float32)
+    ext = {"clamp": [1, 1, 1, 2, 3, 3, 3], "zero": [0, 0, 1, 2, 3, 0, 0], "reflect": [2, 1, 1, 2, 3, 3, 2],
+           "mirror": [3, 2, 1, 2, 3, 2, 1], "wrap": [2, 3, 1, 2, 3, 1, 2]}
+    for mode, e in ext.items():
+        want = [sum(k[0, b] * e[j + b] for b in range(5)) for j in range(3)]
+        out, _ = oracle.conv2d(img, k, border=mode)
+        np.testing.assert_array_equal(out[0, 0], want, err_msg=mode)
