@@ -326,6 +326,19 @@ def measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g, serve_seconds=SE
             "effective_hbm_frac": round(8 * n * n * 100 / (ms * 1e-3) / 1e9 / hbm, 4)}
     jac["residuals"] = [float(x) for x in res.cpu()]
     out["jacobi_8192x8192_100sweeps"] = jac
+    # red-black SOR, omega 1.9, in place: per sweep each point is read twice and
+    # its float4 written twice (16 B per point-sweep)
+    wsr = pg.pencil_rbsor2d_workspace_size(n, n)
+
+    def sor():
+        u.copy_(u0)
+        pg.pencil_rbsor2d_ex(n, n, u, 100, 1.9, 10, res, ws, wsr, sraw)
+    ms_copy = _time_stream(torch, stream, lambda: u.copy_(u0), 3)
+    ms = _time_stream(torch, stream, sor, 3) - ms_copy
+    out["rbsor_8192x8192_100sweeps"] = {
+        "ms": round(ms, 3), "gpt_sweeps_s": round((n - 2) * (n - 2) * 100 / ms / 1e6, 2),
+        "hbm_frac_16B_per_point_sweep": round(16 * n * n * 100 / (ms * 1e-3) / 1e9 / hbm, 4),
+        "residuals": [float(x) for x in res.cpu()]}
     del u0, u, ws
     out["batched_512"] = measure_batched(torch, pg, dev, stream)
     out["serving"] = measure_serving(torch, pg, dev, serve_seconds)

@@ -267,6 +267,38 @@ int pencil_residual2d(int h, int w, const float *u, double *res_out, void *works
 int pencil_jacobi2d_noalloc(int h, int w, float *u, int iters, int check_every, double *res_out,
                             int temporal_t, void *stream);
 
+/* untilconverged with its threshold (Sec. 3.2): sweeps in chunks of
+ * check_every; after each chunk the residual of the iterate is written to
+ * res_out[m-1] (device memory, max_iters/check_every doubles), read back, and
+ * the loop stops once it is <= tol or max_iters sweeps are done.  *iters_done
+ * (host memory) receives the number of sweeps performed; u holds that iterate
+ * (the same bits as pencil_jacobi2d_ex with that many sweeps).  Synchronous on
+ * `stream` (each chunk ends with a read of one double).  check_every >= 1 and
+ * max_iters a multiple of it.  Other arguments as pencil_jacobi2d_ex.
+ * Errors: ARG, NULL, ALIAS, PTR, NOMEM, CUDA. */
+int pencil_jacobi2d_until(int h, int w, float *u, int max_iters, int check_every, double tol,
+                          double *res_out, int *iters_done, void *workspace, size_t ws_bytes,
+                          int temporal_t, void *stream);
+
+/* Red-black successive over-relaxation, in place: a sweep updates the
+ * interior points with (i + j) even, then those with (i + j) odd (which see
+ * the new even values), each as
+ *   u <- fma(omega, 0.25f * ((up + down) + (left + right)) - u, u)
+ * in FP32 in exactly that order; omega in (0, 2), 1 = red-black Gauss-Seidel.
+ * The over-relaxed variant of the sequential untilconverged loop (Sec. 3.2):
+ * it needs O(n) sweeps where the Jacobi sweep needs O(n^2).  Residuals every
+ * check_every sweeps as for pencil_jacobi2d_ex.  u, res_out, workspace:
+ * device memory; workspace of pencil_rbsor2d_workspace_size(h, w) bytes.
+ * Errors: ARG, NULL, ALIAS, PTR, NOMEM, CUDA. */
+size_t pencil_rbsor2d_workspace_size(int h, int w);
+int pencil_rbsor2d_ex(int h, int w, float *u, int iters, float omega, int check_every,
+                      double *res_out, void *workspace, size_t ws_bytes, void *stream);
+
+/* The same with the convergence stop of pencil_jacobi2d_until. */
+int pencil_rbsor2d_until(int h, int w, float *u, int max_iters, float omega, int check_every,
+                         double tol, double *res_out, int *iters_done, void *workspace,
+                         size_t ws_bytes, void *stream);
+
 /* ----------------------------------------------------------------- utility */
 
 /* Human-readable text of a pencil_status (static storage). */

@@ -78,6 +78,8 @@ def lib():
     L.oracle_residual2d_f32.restype = ctypes.c_double
     L.oracle_jacobi2d.argtypes = [i64, i64, vp, i32, i32, vp]
     L.oracle_jacobi2d.restype = i32
+    L.oracle_rbsor2d.argtypes = [i64, i64, vp, i32, ctypes.c_double, i32, vp]
+    L.oracle_rbsor2d.restype = i32
     _lib = L
     return L
 
@@ -212,4 +214,16 @@ def jacobi2d(u0: np.ndarray, iters: int, check_every: int = 0):
     rc = lib().oracle_jacobi2d(h, w, _ptr(u), int(iters), int(check_every), _ptr(res))
     if rc != 0:
         raise ValueError("oracle_jacobi2d rejected its arguments")
+    return u, res[:m]
+
+
+def rbsor2d(u0: np.ndarray, iters: int, omega: float, check_every: int = 0):
+    """iters red-black SOR sweeps in FP64 from u0 (widened).  Returns (u, residuals)."""
+    u = np.array(u0, dtype=np.float64, order="C", copy=True)
+    h, w = u.shape
+    m = iters // check_every if check_every > 0 else 0
+    res = np.zeros(max(m, 1), dtype=np.float64)
+    rc = lib().oracle_rbsor2d(h, w, _ptr(u), int(iters), float(omega), int(check_every), _ptr(res))
+    if rc != 0:
+        raise ValueError("oracle_rbsor2d rejected its arguments")
     return u, res[:m]

@@ -345,3 +345,27 @@ int oracle_jacobi2d(int64_t h, int64_t w, double *u, int iters, int check_every,
     free(v);
     return 0;
 }
+
+/* Red-black successive over-relaxation: one sweep updates, in place, first
+ * the interior points with (i + j) even, then those with (i + j) odd, each as
+ * u <- u + omega * ((up + down + left + right) / 4 - u), the odd points seeing
+ * the new even values.  omega = 1 is red-black Gauss-Seidel.  Residuals as in
+ * oracle_jacobi2d.  Returns 0, or -1 on bad arguments. */
+int oracle_rbsor2d(int64_t h, int64_t w, double *u, int iters, double omega, int check_every,
+                   double *res)
+{
+    if (h <= 0 || w <= 0 || iters < 0 || check_every < 0) return -1;
+    for (int s = 1; s <= iters; ++s) {
+        for (int color = 0; color < 2; ++color)
+            for (int64_t i = 1; i + 1 < h; ++i)
+                for (int64_t j = 1; j + 1 < w; ++j) {
+                    if (((i + j) & 1) != color) continue;
+                    const int64_t p = i * w + j;
+                    const double avg = (u[p - w] + u[p + w] + u[p - 1] + u[p + 1]) / 4.0;
+                    u[p] = u[p] + omega * (avg - u[p]);
+                }
+        if (check_every > 0 && s % check_every == 0)
+            res[s / check_every - 1] = oracle_residual2d_f64(h, w, u);
+    }
+    return 0;
+}

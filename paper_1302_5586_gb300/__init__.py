@@ -42,6 +42,10 @@ from ._binding import (  # noqa: F401
     pencil_jacobi2d,
     pencil_jacobi2d_ex,
     pencil_jacobi2d_noalloc,
+    pencil_jacobi2d_until,
+    pencil_rbsor2d_ex,
+    pencil_rbsor2d_until,
+    pencil_rbsor2d_workspace_size,
     pencil_jacobi2d_workspace_size,
     pencil_last_cuda_error,
     pencil_residual2d,

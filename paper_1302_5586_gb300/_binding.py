@@ -77,6 +77,11 @@ def lib():
         "pencil_jacobi2d_ex": (i, [i, i, vp, i, i, d, vp, sz, i, vp]),
         "pencil_residual2d": (i, [i, i, vp, d, vp, sz, vp]),
         "pencil_jacobi2d_noalloc": (i, [i, i, vp, i, i, d, i, vp]),
+        "pencil_jacobi2d_until": (i, [i, i, vp, i, i, ctypes.c_double, d, ctypes.POINTER(i), vp, sz, i, vp]),
+        "pencil_rbsor2d_workspace_size": (sz, [i, i]),
+        "pencil_rbsor2d_ex": (i, [i, i, vp, i, ctypes.c_float, i, d, vp, sz, vp]),
+        "pencil_rbsor2d_until": (i, [i, i, vp, i, ctypes.c_float, i, ctypes.c_double, d, ctypes.POINTER(i), vp,
+                                     sz, vp]),
         "pencil_batch_create": (i, [i, i, ctypes.c_longlong, ctypes.POINTER(ctypes.c_void_p)]),
         "pencil_batch_set_variant": (i, [vp, i, i]),
         "pencil_batch_tiles": (i, [vp, i, vp, ctypes.POINTER(ctypes.c_longlong)]),
@@ -172,6 +177,35 @@ def pencil_jacobi2d_ex(h, w, u, iters, check_every, res_out, workspace, ws_bytes
 def pencil_residual2d(h, w, u, res_out, workspace, ws_bytes, stream=None):
     _check(lib().pencil_residual2d(h, w, _ptr(u), _ptr(res_out), _ptr(workspace), ws_bytes,
                                    _stream(stream)), "pencil_residual2d")
+
+
+def pencil_jacobi2d_until(h, w, u, max_iters, check_every, tol, res_out, workspace, ws_bytes, temporal_t=0,
+                          stream=None) -> int:
+    """Returns the number of sweeps performed."""
+    done = ctypes.c_int()
+    _check(lib().pencil_jacobi2d_until(h, w, _ptr(u), max_iters, check_every, tol, _ptr(res_out),
+                                       ctypes.byref(done), _ptr(workspace), ws_bytes, temporal_t,
+                                       _stream(stream)), "pencil_jacobi2d_until")
+    return done.value
+
+
+def pencil_rbsor2d_workspace_size(h, w) -> int:
+    return int(lib().pencil_rbsor2d_workspace_size(h, w))
+
+
+def pencil_rbsor2d_ex(h, w, u, iters, omega, check_every, res_out, workspace, ws_bytes, stream=None):
+    _check(lib().pencil_rbsor2d_ex(h, w, _ptr(u), iters, omega, check_every, _ptr(res_out), _ptr(workspace),
+                                   ws_bytes, _stream(stream)), "pencil_rbsor2d_ex")
+
+
+def pencil_rbsor2d_until(h, w, u, max_iters, omega, check_every, tol, res_out, workspace, ws_bytes,
+                         stream=None) -> int:
+    """Returns the number of sweeps performed."""
+    done = ctypes.c_int()
+    _check(lib().pencil_rbsor2d_until(h, w, _ptr(u), max_iters, omega, check_every, tol, _ptr(res_out),
+                                      ctypes.byref(done), _ptr(workspace), ws_bytes, _stream(stream)),
+           "pencil_rbsor2d_until")
+    return done.value
 
 
 def pencil_jacobi2d_noalloc(h, w, u, iters, check_every, res_out, temporal_t=0, stream=None):

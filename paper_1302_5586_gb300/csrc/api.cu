@@ -336,6 +336,75 @@ int pencil_jacobi2d_ex(int h, int w, float *u, int iters, int check_every, doubl
     return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
 }
 
+// Shared checks of the iterative entry points; returns PENCIL_OK or an error.
+static int check_iterative(int h, int w, float *u, int nres, double *res_out, void *workspace,
+                           size_t ws_bytes, size_t need) {
+    int st = check_dims(h, w);
+    if (st) return st;
+    if (!u || !workspace) return PENCIL_ERR_NULL;
+    if (nres > 0 && !res_out) return PENCIL_ERR_NULL;
+    if (ws_bytes < need) return PENCIL_ERR_NOMEM;
+    if ((uintptr_t)workspace % 256 != 0) return PENCIL_ERR_ARG;
+    const size_t ub = sizeof(float) * (size_t)h * w;
+    if (overlaps(workspace, ws_bytes, u, ub)) return PENCIL_ERR_ALIAS;
+    if (nres > 0 && (overlaps(res_out, sizeof(double) * nres, u, ub) ||
+                     overlaps(res_out, sizeof(double) * nres, workspace, ws_bytes)))
+        return PENCIL_ERR_ALIAS;
+    if (kind_of(u) != Mem::Device || kind_of(workspace) != Mem::Device) return PENCIL_ERR_PTR;
+    if (nres > 0 && kind_of(res_out) != Mem::Device) return PENCIL_ERR_PTR;
+    return PENCIL_OK;
+}
+
+int pencil_jacobi2d_until(int h, int w, float *u, int max_iters, int check_every, double tol,
+                          double *res_out, int *iters_done, void *workspace, size_t ws_bytes,
+                          int temporal_t, void *stream) {
+    if (!iters_done) return PENCIL_ERR_NULL;
+    *iters_done = 0;
+    if (max_iters < 0 || check_every < 1 || max_iters % check_every != 0 || temporal_t < 0 ||
+        !(tol >= 0.0))
+        return PENCIL_ERR_ARG;
+    if (check_dims(h, w)) return PENCIL_ERR_ARG;
+    int st = check_iterative(h, w, u, max_iters / check_every, res_out, workspace, ws_bytes,
+                             jacobi_workspace_bytes(h, w));
+    if (st) return st;
+    cudaError_t e = jacobi_until(h, w, u, max_iters, check_every, tol, res_out, iters_done, workspace,
+                                 ws_bytes, temporal_t, (cudaStream_t)stream);
+    return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
+}
+
+size_t pencil_rbsor2d_workspace_size(int h, int w) {
+    if (check_dims(h, w)) return 0;
+    return rbsor_workspace_bytes(h, w);
+}
+
+int pencil_rbsor2d_ex(int h, int w, float *u, int iters, float omega, int check_every,
+                      double *res_out, void *workspace, size_t ws_bytes, void *stream) {
+    if (iters < 0 || check_every < 0 || !(omega > 0.0f && omega < 2.0f)) return PENCIL_ERR_ARG;
+    if (check_dims(h, w)) return PENCIL_ERR_ARG;
+    const int nres = check_every > 0 ? iters / check_every : 0;
+    int st = check_iterative(h, w, u, nres, res_out, workspace, ws_bytes, rbsor_workspace_bytes(h, w));
+    if (st) return st;
+    cudaError_t e = rbsor_run(h, w, u, iters, omega, check_every, res_out, workspace, (cudaStream_t)stream);
+    return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
+}
+
+int pencil_rbsor2d_until(int h, int w, float *u, int max_iters, float omega, int check_every,
+                         double tol, double *res_out, int *iters_done, void *workspace,
+                         size_t ws_bytes, void *stream) {
+    if (!iters_done) return PENCIL_ERR_NULL;
+    *iters_done = 0;
+    if (max_iters < 0 || check_every < 1 || max_iters % check_every != 0 ||
+        !(omega > 0.0f && omega < 2.0f) || !(tol >= 0.0))
+        return PENCIL_ERR_ARG;
+    if (check_dims(h, w)) return PENCIL_ERR_ARG;
+    int st = check_iterative(h, w, u, max_iters / check_every, res_out, workspace, ws_bytes,
+                             rbsor_workspace_bytes(h, w));
+    if (st) return st;
+    cudaError_t e = rbsor_until(h, w, u, max_iters, omega, check_every, tol, res_out, iters_done,
+                                workspace, (cudaStream_t)stream);
+    return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
+}
+
 int pencil_residual2d(int h, int w, const float *u, double *res_out, void *workspace,
                       size_t ws_bytes, void *stream) {
     int st = check_dims(h, w);

@@ -57,5 +57,15 @@ size_t jacobi_workspace_bytes(int h, int w);
 cudaError_t jacobi_run(int h, int w, float *u, int iters, int check_every, double *res,
                        void *ws, size_t ws_bytes, int temporal_t, cudaStream_t s);
 cudaError_t residual_run(int h, int w, const float *u, double *res, void *ws, cudaStream_t s);
+// Sweeps in chunks of check_every until the chunk's residual <= tol or
+// max_iters; *done = sweeps performed (the stream is synchronised per chunk).
+cudaError_t jacobi_until(int h, int w, float *u, int max_iters, int check_every, double tol,
+                         double *res, int *done, void *ws, size_t ws_bytes, int temporal_t,
+                         cudaStream_t s);
+size_t rbsor_workspace_bytes(int h, int w);
+cudaError_t rbsor_run(int h, int w, float *u, int iters, float omega, int check_every, double *res,
+                      void *ws, cudaStream_t s);
+cudaError_t rbsor_until(int h, int w, float *u, int max_iters, float omega, int check_every,
+                        double tol, double *res, int *done, void *ws, cudaStream_t s);
 
 }  // namespace pencil

@@ -165,6 +165,69 @@ __global__ void __launch_bounds__(JT)
         block_sum_store((double)hi + (double)lo, partials + (size_t)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
+// ------------------------------------------------- red-black SOR sweeps
+// One colour pass, in place: interior points with (i + j) % 2 == color become
+// u + omega * (0.25f * ((up + down) + (left + right)) - u)   [fma(omega, d, u)]
+// in FP32 in exactly that order.  A point's four neighbours have the other
+// colour and are not written in this pass, so the pass has no read-after-write
+// dependence; a thread writes back its whole float4, the other colour's
+// values unchanged.
+template <int COLOR>
+__global__ void __launch_bounds__(JT) rbsor_v4_kernel(float *__restrict__ u, int h, int w, float omega) {
+    const int lane = threadIdx.x & 31;
+    const int q = blockIdx.x * JT + threadIdx.x;
+    const int j0 = q * 4;
+    const bool colok = j0 < w;
+    const int w4 = w >> 2;
+    const int i0 = blockIdx.y * JR;
+    float4 *U = reinterpret_cast<float4 *>(u);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 up = (colok && i0 > 0) ? U[(size_t)(i0 - 1) * w4 + q] : z4;
+    float4 cur = (colok && i0 < h) ? U[(size_t)i0 * w4 + q] : z4;
+#pragma unroll 4
+    for (int o = 0; o < JR; ++o) {
+        const int i = i0 + o;
+        if (i >= h) break;
+        const float4 dn = (colok && i + 1 < h) ? U[(size_t)(i + 1) * w4 + q] : z4;
+        float lf = __shfl_up_sync(FULL, cur.w, 1);
+        float rt = __shfl_down_sync(FULL, cur.x, 1);
+        if (lane == 0) lf = (colok && j0 > 0) ? u[(size_t)i * w + j0 - 1] : 0.f;
+        if (lane == 31) rt = (colok && j0 + 4 < w) ? u[(size_t)i * w + j0 + 4] : 0.f;
+        if (colok && i > 0 && i < h - 1) {
+            const int par = (i + j0) & 1;  // colour of column j0 in this row
+            float4 n = cur;
+            const float s[4] = {nsum(up.x, dn.x, lf, cur.y), nsum(up.y, dn.y, cur.x, cur.z),
+                                nsum(up.z, dn.z, cur.y, cur.w), nsum(up.w, dn.w, cur.z, rt)};
+            float c[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = j0 + e;
+                if (((par + e) & 1) == COLOR && j > 0 && j < w - 1)
+                    c[e] = __fmaf_rn(omega, __fsub_rn(__fmul_rn(0.25f, s[e]), c[e]), c[e]);
+            }
+            n = make_float4(c[0], c[1], c[2], c[3]);
+            U[(size_t)i * w4 + q] = n;
+        }
+        up = cur;
+        cur = dn;
+    }
+}
+
+template <int COLOR>
+__global__ void __launch_bounds__(JT) rbsor_s_kernel(float *__restrict__ u, int h, int w, float omega) {
+    const int j = blockIdx.x * JT + threadIdx.x;
+    const int i0 = blockIdx.y * JR;
+    if (j < 1 || j >= w - 1) return;
+    for (int o = 0; o < JR; ++o) {
+        const int i = i0 + o;
+        if (i >= h - 1) break;
+        if (i < 1 || ((i + j) & 1) != COLOR) continue;
+        const size_t p = (size_t)i * w + j;
+        const float s = nsum(u[p - w], u[p + w], u[p - 1], u[p + 1]);
+        u[p] = __fmaf_rn(omega, __fsub_rn(__fmul_rn(0.25f, s), u[p]), u[p]);
+    }
+}
+
 // res = sqrt(sum of n partials), one block, fixed order.
 __global__ void __launch_bounds__(256) residual_finish_kernel(const double *__restrict__ partials,
                                                               int n, double *__restrict__ res) {
@@ -468,6 +531,87 @@ cudaError_t residual_run(int h, int w, const float *u, double *res, void *ws, cu
     cudaError_t e = sweep<true, false>(p, u, nullptr, h, w, partials, s);
     if (e == cudaSuccess) e = finish(partials, p.nblocks, res, s);
     return e;
+}
+
+}  // namespace pencil
+
+// ------------------------------------------------ SOR and converge-to-tol
+namespace pencil {
+
+size_t rbsor_workspace_bytes(int h, int w) {
+    const size_t nb = (size_t)((w + JT - 1) / JT) * (size_t)((h + JR - 1) / JR);
+    return align256(sizeof(double) * nb);
+}
+
+cudaError_t rbsor_run(int h, int w, float *u, int iters, float omega, int check_every, double *res,
+                      void *ws, cudaStream_t s) {
+    const int nres = (check_every > 0) ? iters / check_every : 0;
+    if (h < 3 || w < 3 || iters == 0) {
+        if (nres > 0) return cudaMemsetAsync(res, 0, sizeof(double) * (size_t)nres, s);
+        return cudaSuccess;
+    }
+    double *partials = static_cast<double *>(ws);
+    const Plan p = make_plan(h, w, u, nullptr);
+    for (int k = 1; k <= iters; ++k) {
+        if (p.vec) {
+            rbsor_v4_kernel<0><<<p.grid, JT, 0, s>>>(u, h, w, omega);
+            rbsor_v4_kernel<1><<<p.grid, JT, 0, s>>>(u, h, w, omega);
+        } else {
+            rbsor_s_kernel<0><<<p.grid, JT, 0, s>>>(u, h, w, omega);
+            rbsor_s_kernel<1><<<p.grid, JT, 0, s>>>(u, h, w, omega);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (check_every > 0 && k % check_every == 0) {
+            e = sweep<true, false>(p, u, nullptr, h, w, partials, s);
+            if (e == cudaSuccess) e = finish(partials, p.nblocks, res + (k / check_every - 1), s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+}  // namespace pencil
+
+namespace {
+// Read one residual back to the host (the stream is synchronised).
+cudaError_t read_res(const double *dev, double *host, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(host, dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+}
+}  // namespace
+
+namespace pencil {
+
+cudaError_t jacobi_until(int h, int w, float *u, int max_iters, int check_every, double tol,
+                         double *res, int *done, void *ws, size_t ws_bytes, int temporal_t,
+                         cudaStream_t s) {
+    *done = 0;
+    for (int m = 1; m * check_every <= max_iters; ++m) {
+        cudaError_t e = jacobi_run(h, w, u, check_every, check_every, res + (m - 1), ws, ws_bytes,
+                                   temporal_t, s);
+        double r = 0.0;
+        if (e == cudaSuccess) e = read_res(res + (m - 1), &r, s);
+        if (e != cudaSuccess) return e;
+        *done = m * check_every;
+        if (r <= tol) break;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t rbsor_until(int h, int w, float *u, int max_iters, float omega, int check_every,
+                        double tol, double *res, int *done, void *ws, cudaStream_t s) {
+    *done = 0;
+    for (int m = 1; m * check_every <= max_iters; ++m) {
+        cudaError_t e = rbsor_run(h, w, u, check_every, omega, check_every, res + (m - 1), ws, s);
+        double r = 0.0;
+        if (e == cudaSuccess) e = read_res(res + (m - 1), &r, s);
+        if (e != cudaSuccess) return e;
+        *done = m * check_every;
+        if (r <= tol) break;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace pencil

@@ -133,3 +133,60 @@ def test_initial_state_recipe():
         np.testing.assert_array_equal(u[sl], lin[sl])
     inner = u[1:-1, 1:-1]
     assert inner.min() >= -1.0 and inner.max() < 1.0
+
+
+def test_rbsor_golden_hand_case():
+    with open(os.path.join(GOLDEN, "rbsor_hand.json")) as f:
+        cs = json.load(f)["cases"][0]
+    u, _ = oracle.rbsor2d(np.array(cs["grid"], dtype=np.float64), cs["sweeps"], cs["omega"])
+    np.testing.assert_array_equal(u, np.array(cs["expected"], dtype=np.float64))
+
+
+@pytest.mark.parametrize("omega", [0.7, 1.0, 1.5, 1.9])
+def test_rbsor_linear_field_is_a_fixed_point(omega):
+    n = 33
+    x = np.arange(n) / (n - 1)
+    u0 = 0.25 * x[None, :] + 0.5 * x[:, None] + 0.125
+    u, res = oracle.rbsor2d(u0, 12, omega, 4)
+    np.testing.assert_array_equal(u, u0)
+    assert np.all(res == 0.0)
+
+
+@pytest.mark.parametrize("omega", [1.0, 1.6])
+def test_rbsor_converges_to_the_direct_solution_faster_than_jacobi(omega):
+    h, w = 17, 13
+    u0 = synth.jacobi_init_f32(9, h, w).astype(np.float64)
+    u, res = oracle.rbsor2d(u0, 400, omega, 400)
+    uj, resj = oracle.jacobi2d(u0, 400, 400)
+    n_i, n_j = h - 2, w - 2
+    idx = lambda i, j: (i - 1) * n_j + (j - 1)
+    A = sp.lil_matrix((n_i * n_j, n_i * n_j))
+    b = np.zeros(n_i * n_j)
+    for i in range(1, h - 1):
+        for j in range(1, w - 1):
+            A[idx(i, j), idx(i, j)] = 4.0
+            for di, dj in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+                ii, jj = i + di, j + dj
+                if ii in (0, h - 1) or jj in (0, w - 1):
+                    b[idx(i, j)] += u0[ii, jj]
+                else:
+                    A[idx(i, j), idx(ii, jj)] = -1.0
+    sol = spla.spsolve(A.tocsr(), b).reshape(n_i, n_j)
+    np.testing.assert_allclose(u[1:-1, 1:-1], sol, atol=1e-11)
+    assert res[-1] < resj[-1]
+
+
+def test_rbsor_with_omega_one_matches_a_literal_gauss_seidel_ordering():
+    """omega = 1: each colour's points depend only on the other colour, so the
+    red-black sweep equals a Gauss-Seidel sweep that visits all even points
+    (any order) then all odd points; here the odd points go in reverse order."""
+    u0 = synth.jacobi_init_f32(21, 9, 11).astype(np.float64)
+    u, _ = oracle.rbsor2d(u0, 3, 1.0)
+    v = u0.copy()
+    pts = [(i, j) for i in range(1, 8) for j in range(1, 10)]
+    for _ in range(3):
+        for i, j in [p for p in pts if sum(p) % 2 == 0]:
+            v[i, j] = (v[i - 1, j] + v[i + 1, j] + v[i, j - 1] + v[i, j + 1]) / 4.0
+        for i, j in reversed([p for p in pts if sum(p) % 2 == 1]):
+            v[i, j] = (v[i - 1, j] + v[i + 1, j] + v[i, j - 1] + v[i, j + 1]) / 4.0
+    np.testing.assert_allclose(u, v, rtol=1e-15, atol=1e-15)
