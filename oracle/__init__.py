@@ -78,6 +78,8 @@ def lib():
     L.oracle_residual2d_f32.restype = ctypes.c_double
     L.oracle_jacobi2d.argtypes = [i64, i64, vp, i32, i32, vp]
     L.oracle_jacobi2d.restype = i32
+    L.oracle_op2_inc.argtypes = [i64, i64, vp, vp, vp]
+    L.oracle_op2_inc.restype = i32
     L.oracle_rbsor2d.argtypes = [i64, i64, vp, i32, ctypes.c_double, i32, vp]
     L.oracle_rbsor2d.restype = i32
     _lib = L
@@ -227,3 +229,16 @@ def rbsor2d(u0: np.ndarray, iters: int, omega: float, check_every: int = 0):
     if rc != 0:
         raise ValueError("oracle_rbsor2d rejected its arguments")
     return u, res[:m]
+
+
+def op2_inc(cells: np.ndarray, e2c: np.ndarray, edge: np.ndarray) -> np.ndarray:
+    """The sequential edge-to-cell increment (FP64); returns the new cell array."""
+    c = np.array(cells, dtype=np.float64, copy=True)
+    m = np.ascontiguousarray(e2c, dtype=np.int32).reshape(-1, 2)
+    e = np.ascontiguousarray(edge, dtype=np.float64)
+    if m.shape[0] != e.size:
+        raise ValueError("one pair of cells per edge")
+    rc = lib().oracle_op2_inc(c.size, e.size, _ptr(m), _ptr(e), _ptr(c))
+    if rc != 0:
+        raise ValueError("cell index out of range")
+    return c

@@ -369,3 +369,19 @@ int oracle_rbsor2d(int64_t h, int64_t w, double *u, int iters, double omega, int
     }
     return 0;
 }
+
+/* Indirect increment over an edge set (the OP2 loop of Sec. 3.1): for every
+ * edge i in increasing order, the cells e2c[2i+1] and then e2c[2i] (in that
+ * order) are each incremented by edge[i].  Sequential, in FP64.  Returns 0,
+ * or -1 on an index outside [0, ncells). */
+int oracle_op2_inc(int64_t ncells, int64_t nedges, const int32_t *e2c, const double *edge,
+                   double *cell)
+{
+    for (int64_t i = 0; i < nedges; ++i) {
+        const int32_t c1 = e2c[2 * i + 1], c0 = e2c[2 * i];
+        if (c0 < 0 || c1 < 0 || c0 >= ncells || c1 >= ncells) return -1;
+        cell[c1] += edge[i];
+        cell[c0] += edge[i];
+    }
+    return 0;
+}

@@ -182,3 +182,22 @@ def batch_spec(seed: int, n: int, lo: int, hi: int, klo: int = 3, khi: int = 15)
     w = loguniform_sides(seed ^ 0x2222, n, lo, hi)
     k = odd_ksizes(seed ^ 0x3333, n, klo, khi)
     return h, w, k
+
+
+def mesh_edges(seed: int, nx: int, ny: int):
+    """Edges of an nx x ny grid of cells (each edge joins two cells that share a
+    side), with cells relabelled, edges reordered and each edge's two ends
+    swapped at random, so the connectivity looks unstructured.  Returns
+    (ncells, e2c int32 [nedges][2])."""
+    ncells = nx * ny
+    idx = np.arange(ncells, dtype=np.int64).reshape(ny, nx)
+    horiz = np.stack([idx[:, :-1].ravel(), idx[:, 1:].ravel()], axis=1)
+    vert = np.stack([idx[:-1, :].ravel(), idx[1:, :].ravel()], axis=1)
+    e = np.concatenate([horiz, vert])
+    z = splitmix64(seed, ncells + 2 * len(e))
+    relabel = np.argsort(z[:ncells], kind="stable")
+    e = relabel[e]
+    e = e[np.argsort(z[ncells:ncells + len(e)], kind="stable")]
+    swap = (z[ncells + len(e):] & np.uint64(1)).astype(bool)
+    e[swap] = e[swap][:, ::-1]
+    return ncells, np.ascontiguousarray(e, dtype=np.int32)
