@@ -126,6 +126,22 @@ int pencil_conv2d_sep(int h, int w, PENCIL_ARR2(const float, in, h, w), int kx, 
 int pencil_conv2d_sep_ex(int c, int h, int w, const void *in, int kx, const float *gx, int ky,
                          const float *gy, void *out, int dtype, int flags, void *stream);
 
+/* Two filters in a row, out = conv(conv(in, k1), k2), in one kernel: the
+ * intermediate stays in on-chip memory instead of making a round trip
+ * through HBM (the fusion of dependent stencils, Sec. 2.2.3).  The result is
+ * bit-identical to two pencil_conv2d_ex calls through a temporary of the same
+ * dtype: the intermediate is rounded to the storage type and the second
+ * filter reads it clamped at the image edge.  Clamp-to-edge only.  Square odd
+ * sides 3, 5, 7 for both filters use the tiled kernel, any other sides a
+ * generic one (PENCIL_CONV_GENERIC forces it).  Every array is device memory
+ * (in, out: c*h*w elements of dtype; k1: kh1*kw1, k2: kh2*kw2 FP32).
+ * Errors: ARG, NULL, ALIAS (out overlaps in, k1 or k2), PTR, UNSUPPORTED (a
+ * border mode other than clamp, or a second filter too large for on-chip
+ * memory), CUDA. */
+int pencil_conv2d_chain(int c, int h, int w, const void *in, int kh1, int kw1, const float *k1,
+                        int kh2, int kw2, const float *k2, void *out, int dtype, int flags,
+                        void *stream);
+
 /* ------------------------------------------------------------------- batch
  * Many images, each with its own size and odd filter side 1..15, convolved in
  * ONE persistent kernel launch replayed from a CUDA graph.  The tiles of all
@@ -298,6 +314,35 @@ int pencil_rbsor2d_ex(int h, int w, float *u, int iters, float omega, int check_
 int pencil_rbsor2d_until(int h, int w, float *u, int max_iters, float omega, int check_every,
                          double tol, double *res_out, int *iters_done, void *workspace,
                          size_t ws_bytes, void *stream);
+
+/* --------------------------------------------------------------------- op2
+ * The indirect increment of the paper's unstructured-mesh example (Sec. 3.1):
+ * for every edge i (in order) the cells e2c[2i+1] and e2c[2i] are each
+ * incremented by edge[i] (FP64).  Two ways to run it:
+ *   PENCIL_OP2_ORDERED  every cell adds its edges in the sequential order
+ *                       (from a plan), so the result is the same bits as the
+ *                       sequential loop, run after run;
+ *   PENCIL_OP2_ATOMIC   one thread per edge with FP64 atomic adds: no plan use,
+ *                       but the rounding depends on the order the hardware
+ *                       picks (the precision-for-speed switch of Sec. 3.1).
+ */
+#define PENCIL_OP2_ORDERED 0
+#define PENCIL_OP2_ATOMIC 1
+typedef struct pencil_op2_plan pencil_op2_plan;
+
+/* Build the per-cell contribution lists of a mesh: e2c is host memory,
+ * 2*nedges cell indices in [0, ncells) (edge i joins e2c[2i] and e2c[2i+1]);
+ * the plan keeps device copies.  Errors: NULL, ARG (an index out of range,
+ * sizes), NOMEM, CUDA. */
+int pencil_op2_plan_create(int ncells, int nedges, const int *e2c, pencil_op2_plan **out);
+
+/* Stream-ordered: cell[c] += sum of its edges' values.  edge (nedges doubles)
+ * and cell (ncells doubles) are device memory and must not overlap.
+ * Errors: NULL, ARG (mode), ALIAS, PTR, CUDA. */
+int pencil_op2_inc(const pencil_op2_plan *p, const double *edge, double *cell, int mode, void *stream);
+
+/* Free a plan (after its last use has finished).  NULL is accepted. */
+int pencil_op2_plan_destroy(pencil_op2_plan *p);
 
 /* ----------------------------------------------------------------- utility */
 

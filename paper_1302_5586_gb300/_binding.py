@@ -77,6 +77,10 @@ def lib():
         "pencil_jacobi2d_ex": (i, [i, i, vp, i, i, d, vp, sz, i, vp]),
         "pencil_residual2d": (i, [i, i, vp, d, vp, sz, vp]),
         "pencil_jacobi2d_noalloc": (i, [i, i, vp, i, i, d, i, vp]),
+        "pencil_conv2d_chain": (i, [i, i, i, vp, i, i, vp, i, i, vp, vp, i, i, vp]),
+        "pencil_op2_plan_create": (i, [i, i, vp, ctypes.POINTER(ctypes.c_void_p)]),
+        "pencil_op2_inc": (i, [vp, vp, vp, i, vp]),
+        "pencil_op2_plan_destroy": (i, [vp]),
         "pencil_jacobi2d_until": (i, [i, i, vp, i, i, ctypes.c_double, d, ctypes.POINTER(i), vp, sz, i, vp]),
         "pencil_rbsor2d_workspace_size": (sz, [i, i]),
         "pencil_rbsor2d_ex": (i, [i, i, vp, i, ctypes.c_float, i, d, vp, sz, vp]),
@@ -177,6 +181,34 @@ def pencil_jacobi2d_ex(h, w, u, iters, check_every, res_out, workspace, ws_bytes
 def pencil_residual2d(h, w, u, res_out, workspace, ws_bytes, stream=None):
     _check(lib().pencil_residual2d(h, w, _ptr(u), _ptr(res_out), _ptr(workspace), ws_bytes,
                                    _stream(stream)), "pencil_residual2d")
+
+
+def pencil_conv2d_chain(c, h, w, inp, kh1, kw1, k1, kh2, kw2, k2, out, dtype, flags=0, stream=None):
+    _check(lib().pencil_conv2d_chain(c, h, w, _ptr(inp), kh1, kw1, _ptr(k1), kh2, kw2, _ptr(k2), _ptr(out),
+                                     dtype, flags, _stream(stream)), "pencil_conv2d_chain")
+
+
+PENCIL_OP2_ORDERED = 0
+PENCIL_OP2_ATOMIC = 1
+
+
+def pencil_op2_plan_create(ncells, nedges, e2c) -> int:
+    """e2c: host int32 array of 2*nedges cell indices; returns the plan handle."""
+    import numpy as np
+    m = np.ascontiguousarray(e2c, dtype=np.int32)
+    if m.size != 2 * nedges:
+        raise PencilError(-1, f"pencil_op2_plan_create: e2c holds {m.size} indices, expected {2 * nedges}")
+    out = ctypes.c_void_p()
+    _check(lib().pencil_op2_plan_create(ncells, nedges, m.ctypes.data, ctypes.byref(out)), "pencil_op2_plan_create")
+    return out.value
+
+
+def pencil_op2_inc(plan, edge, cell, mode=PENCIL_OP2_ORDERED, stream=None):
+    _check(lib().pencil_op2_inc(plan, _ptr(edge), _ptr(cell), mode, _stream(stream)), "pencil_op2_inc")
+
+
+def pencil_op2_plan_destroy(plan):
+    _check(lib().pencil_op2_plan_destroy(plan), "pencil_op2_plan_destroy")
 
 
 def pencil_jacobi2d_until(h, w, u, max_iters, check_every, tol, res_out, workspace, ws_bytes, temporal_t=0,

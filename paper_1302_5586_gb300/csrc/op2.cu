@@ -1,0 +1,134 @@
+// op2.cu -- the indirect edge-to-cell increment of the paper's OP2 example
+// (Sec. 3.1): every edge i adds edge[i] to its two cells, in the sequential
+// order "second end, then first end, edge by edge".
+//
+// Two kernels:
+//   ordered -- a plan lists, for every cell, the edges that increment it in
+//              exactly that sequential order (a stable counting sort of the
+//              contributions, built once on the host).  One thread per cell
+//              starts from the cell's value and adds its edges in list order in
+//              FP64, so the result is the same bits as the sequential loop and
+//              does not depend on the launch (the reproducible reading of the
+//              loop, Sec. 3.1).
+//   atomic  -- one thread per edge, two FP64 atomicAdds: no plan, but the
+//              order of the additions (and so the rounding) varies from run to
+//              run -- the precision-for-speed switch Sec. 3.1 anticipates.
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace pencil {
+namespace {
+
+__global__ void __launch_bounds__(256)
+    op2_ordered_kernel(const int *__restrict__ rowptr, const int *__restrict__ col,
+                       const double *__restrict__ edge, double *__restrict__ cell, int ncells) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    double acc = cell[c];
+    const int k1 = __ldg(rowptr + c + 1);
+    for (int k = __ldg(rowptr + c); k < k1; ++k) acc = __dadd_rn(acc, __ldg(edge + __ldg(col + k)));
+    cell[c] = acc;
+}
+
+__global__ void __launch_bounds__(256)
+    op2_atomic_kernel(const int *__restrict__ e2c, const double *__restrict__ edge,
+                      double *__restrict__ cell, int nedges) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nedges) return;
+    const double e = __ldg(edge + i);
+    const int2 cc = __ldg(reinterpret_cast<const int2 *>(e2c) + i);
+    atomicAdd(cell + cc.y, e);
+    atomicAdd(cell + cc.x, e);
+}
+
+}  // namespace
+}  // namespace pencil
+
+using namespace pencil;
+
+struct pencil_op2_plan {
+    int ncells = 0, nedges = 0;
+    int *rowptr = nullptr;  // device, ncells + 1
+    int *col = nullptr;     // device, 2 * nedges edge indices, per cell in sequential order
+    int *e2c = nullptr;     // device, 2 * nedges
+};
+
+extern "C" {
+
+int pencil_op2_plan_create(int ncells, int nedges, const int *e2c, pencil_op2_plan **out) {
+    if (!out) return PENCIL_ERR_NULL;
+    *out = nullptr;
+    if (ncells <= 0 || nedges < 0 || nedges > (1 << 29)) return PENCIL_ERR_ARG;
+    if (nedges > 0 && !e2c) return PENCIL_ERR_NULL;
+    std::vector<int> count((size_t)ncells + 1, 0);
+    for (long long t = 0; t < 2ll * nedges; ++t) {
+        const int c = e2c[t];
+        if (c < 0 || c >= ncells) return PENCIL_ERR_ARG;
+        ++count[(size_t)c + 1];
+    }
+    for (int c = 0; c < ncells; ++c) count[(size_t)c + 1] += count[c];
+    std::vector<int> col((size_t)2 * nedges > 0 ? (size_t)2 * nedges : 1);
+    std::vector<int> pos(count.begin(), count.end() - 1);
+    for (int i = 0; i < nedges; ++i) {  // sequential order: second end, then first end
+        col[(size_t)pos[e2c[2 * i + 1]]++] = i;
+        col[(size_t)pos[e2c[2 * i]]++] = i;
+    }
+    pencil_op2_plan *p = new (std::nothrow) pencil_op2_plan;
+    if (!p) return PENCIL_ERR_NOMEM;
+    p->ncells = ncells;
+    p->nedges = nedges;
+    cudaError_t e = cudaMalloc(&p->rowptr, sizeof(int) * ((size_t)ncells + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&p->col, sizeof(int) * col.size());
+    if (e == cudaSuccess) e = cudaMalloc(&p->e2c, sizeof(int) * ((size_t)2 * nedges + 2));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->rowptr, count.data(), sizeof(int) * ((size_t)ncells + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nedges > 0)
+        e = cudaMemcpy(p->e2c, e2c, sizeof(int) * (size_t)2 * nedges, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p->rowptr);
+        cudaFree(p->col);
+        cudaFree(p->e2c);
+        delete p;
+        return e == cudaErrorMemoryAllocation ? PENCIL_ERR_NOMEM : cuda_fail(e);
+    }
+    *out = p;
+    return PENCIL_OK;
+}
+
+int pencil_op2_inc(const pencil_op2_plan *p, const double *edge, double *cell, int mode, void *stream) {
+    if (!p || !edge || !cell) return PENCIL_ERR_NULL;
+    if (mode != PENCIL_OP2_ORDERED && mode != PENCIL_OP2_ATOMIC) return PENCIL_ERR_ARG;
+    const uintptr_t eb = (uintptr_t)edge, cb = (uintptr_t)cell;
+    const size_t en = sizeof(double) * (size_t)p->nedges, cn = sizeof(double) * (size_t)p->ncells;
+    if (en && eb < cb + cn && cb < eb + en) return PENCIL_ERR_ALIAS;
+    cudaPointerAttributes a;
+    for (const void *q : {(const void *)edge, (const void *)cell}) {
+        if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+            cudaGetLastError();
+            return PENCIL_ERR_PTR;
+        }
+        if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return PENCIL_ERR_PTR;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (mode == PENCIL_OP2_ORDERED) {
+        op2_ordered_kernel<<<(p->ncells + 255) / 256, 256, 0, s>>>(p->rowptr, p->col, edge, cell, p->ncells);
+    } else if (p->nedges > 0) {
+        op2_atomic_kernel<<<(p->nedges + 255) / 256, 256, 0, s>>>(p->e2c, edge, cell, p->nedges);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
+}
+
+int pencil_op2_plan_destroy(pencil_op2_plan *p) {
+    if (!p) return PENCIL_OK;
+    cudaFree(p->rowptr);
+    cudaFree(p->col);
+    cudaFree(p->e2c);
+    delete p;
+    return PENCIL_OK;
+}
+
+}  // extern "C"

@@ -48,6 +48,7 @@ SEEDS = {
     "jacobi8192": 0x5EED0003,
     "batch512": 0x5EED0004,
     "serve": 0x5EED0005,
+    "op2mesh": 0x5EED0006,
 }
 
 
