@@ -341,6 +341,8 @@ def measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g, serve_seconds=SE
         "residuals": [float(x) for x in res.cpu()]}
     del u0, u, ws
     out["batched_512"] = measure_batched(torch, pg, dev, stream)
+    out["op2_inc_2048x2048_cells"] = measure_op2(torch, pg, dev, stream)
+    out["chain_8192x8192x3"] = measure_chain(torch, pg, dev, stream, d_img, d_out)
     out["serving"] = measure_serving(torch, pg, dev, serve_seconds)
     return out
 
@@ -370,6 +372,56 @@ def measure_serving(torch, pg, dev, seconds):
                       "offered_gpx_s": round(sum(r.h * r.w for r in tr.requests) / dur / 1e9, 3),
                       "served": served.summary(), "plain": plain.summary()}
         del pool, bank
+    return res
+
+
+def measure_chain(torch, pg, dev, stream, d_img, d_out):
+    """Two filters in a row on the 3 x 8192^2 FP32 image: the fused chain
+    kernel against two conv2d passes through a temporary (same bits).  HBM
+    basis: 8 B per pixel fused (read in, write out), 16 B for two passes."""
+    hbm = measured_peaks().get("hbm_gbs") or 6800.0
+    sraw = stream.cuda_stream
+    tmp = torch.empty_like(d_img)
+    res = {}
+    for k1s, k2s in ((3, 3), (5, 5), (7, 7)):
+        k1 = torch.from_numpy(synth.filter_f32(60 + k1s, k1s, k1s)).to(dev)
+        k2 = torch.from_numpy(synth.gaussian_2d_f32(k2s // 2, 1.0)).to(dev)
+        ms_f = _time_stream(torch, stream, lambda: pg.pencil_conv2d_chain(C, H, W, d_img, k1s, k1s, k1, k2s, k2s, k2,
+                                                                          d_out[0], pg.PENCIL_F32, 0, sraw), 10)
+
+        def two():
+            pg.pencil_conv2d_ex(C, H, W, d_img, k1s, k1s, k1, tmp, pg.PENCIL_F32, 0, sraw)
+            pg.pencil_conv2d_ex(C, H, W, tmp, k2s, k2s, k2, d_out[0], pg.PENCIL_F32, 0, sraw)
+        ms_t = _time_stream(torch, stream, two, 10)
+        flop = 2 * (k1s * k1s + k2s * k2s) * PX_PER_PASS
+        res[f"{k1s}x{k1s}->{k2s}x{k2s}"] = {
+            "fused_ms": round(ms_f, 4), "two_pass_ms": round(ms_t, 4), "speedup": round(ms_t / ms_f, 3),
+            "fused_hbm_frac": round(8 * PX_PER_PASS / (ms_f * 1e-3) / 1e9 / hbm, 4),
+            "fused_fp32_frac": round(flop / (ms_f * 1e-3) / 1e12 / fp32_peak_tflops(), 4)}
+    del tmp
+    return res
+
+
+def measure_op2(torch, pg, dev, stream):
+    """The OP2 edge-to-cell increment on a 2048 x 2048-cell mesh with shuffled
+    labels (8.4 M edges): the ordered kernel (the sequential loop's bits)
+    against FP64 atomics.  Algorithmic bytes per call: each edge's value and
+    two cell indices once (16 B), each cell read and written once (16 B)."""
+    hbm = measured_peaks().get("hbm_gbs") or 6800.0
+    ncells, e2c = synth.mesh_edges(synth.SEEDS["op2mesh"], 2048, 2048)
+    nedges = len(e2c)
+    edge = torch.from_numpy(2.0 * synth.u01_f64(synth.SEEDS["op2mesh"] ^ 0x0E, nedges) - 1.0).to(dev)
+    cell = torch.from_numpy(synth.u01_f64(synth.SEEDS["op2mesh"] ^ 0x0C, ncells)).to(dev)
+    plan = pg.pencil_op2_plan_create(ncells, nedges, e2c)
+    alg = 16 * nedges + 16 * ncells
+    res = {"cells": ncells, "edges": nedges, "algorithmic_bytes": alg}
+    try:
+        for name, mode in (("ordered", pg.PENCIL_OP2_ORDERED), ("atomic", pg.PENCIL_OP2_ATOMIC)):
+            ms = _time_stream(torch, stream, lambda: pg.pencil_op2_inc(plan, edge, cell, mode, stream.cuda_stream), 20)
+            res[name] = {"ms": round(ms, 4), "gedges_s": round(nedges / ms / 1e6, 2),
+                         "hbm_frac": round(alg / (ms * 1e-3) / 1e9 / hbm, 4)}
+    finally:
+        pg.pencil_op2_plan_destroy(plan)
     return res
 
 
@@ -543,6 +595,24 @@ def run_case(name, reps):
             pg.pencil_batch_run(plan, imgs)
         torch.cuda.synchronize()
         pg.pencil_batch_destroy(plan)
+    elif name.startswith("chain"):
+        K = int(name[5:])
+        c, h, w = 2, 4096, 4096
+        img = torch.from_numpy(synth.image_f32(1, c, h, w)).to(dev)
+        k = torch.from_numpy(synth.filter_f32(2, K, K)).to(dev)
+        out = torch.empty_like(img)
+        for _ in range(reps):
+            pg.pencil_conv2d_chain(c, h, w, img, K, K, k, K, K, k, out, pg.PENCIL_F32)
+    elif name.startswith("op2"):
+        ncells, e2c = synth.mesh_edges(synth.SEEDS["op2mesh"], 2048, 2048)
+        edge = torch.from_numpy(synth.u01_f64(1, len(e2c))).to(dev)
+        cell = torch.zeros(ncells, dtype=torch.float64, device=dev)
+        plan = pg.pencil_op2_plan_create(ncells, len(e2c), e2c)
+        mode = pg.PENCIL_OP2_ATOMIC if name == "op2-atomic" else pg.PENCIL_OP2_ORDERED
+        for _ in range(reps):
+            pg.pencil_op2_inc(plan, edge, cell, mode)
+        torch.cuda.synchronize()
+        pg.pencil_op2_plan_destroy(plan)
     elif name.startswith("jacobi"):
         t = int(name.split("t")[-1]) if "t" in name[6:] else 1
         n = 8192
@@ -560,7 +630,7 @@ def run_case(name, reps):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default=None,
-                    help="profile one kernel on a reduced workload: conv3, conv7, conv15, sep15, batch, jacobi, jacobi-t5")
+                    help="profile one kernel on a reduced workload: conv3, conv7, conv15, sep15, batch, jacobi, jacobi-t5, op2-ordered, op2-atomic, chain3, chain5, chain7")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=600)

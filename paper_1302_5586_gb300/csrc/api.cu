@@ -232,6 +232,29 @@ int pencil_conv2d_sep_ex(int c, int h, int w, const void *in, int kx, const floa
     return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
 }
 
+int pencil_conv2d_chain(int c, int h, int w, const void *in, int kh1, int kw1, const float *k1, int kh2,
+                        int kw2, const float *k2, void *out, int dtype, int flags, void *stream) {
+    if (c <= 0 || kh1 <= 0 || kw1 <= 0 || kh2 <= 0 || kw2 <= 0 || (flags & ~(PENCIL_CONV_GENERIC | 0xF00)) != 0 ||
+        ((flags >> 8) & 0xF) > PENCIL_BORDER_WRAP)
+        return PENCIL_ERR_ARG;
+    if (dtype != PENCIL_F32 && dtype != PENCIL_F16) return PENCIL_ERR_ARG;
+    if ((flags >> 8) & 0xF) return PENCIL_ERR_UNSUPPORTED;  // clamp-to-edge only
+    int st = check_dims(h, w);
+    if (st) return st;
+    if (!in || !k1 || !k2 || !out) return PENCIL_ERR_NULL;
+    if (chain_generic_smem(kh2, kw2) > 200 * 1024) return PENCIL_ERR_UNSUPPORTED;
+    const size_t nb = (size_t)c * h * w * elem_size(dtype);
+    if (overlaps(out, nb, in, nb) || overlaps(out, nb, k1, sizeof(float) * (size_t)kh1 * kw1) ||
+        overlaps(out, nb, k2, sizeof(float) * (size_t)kh2 * kw2))
+        return PENCIL_ERR_ALIAS;
+    if (kind_of(in) != Mem::Device || kind_of(out) != Mem::Device || kind_of(k1) != Mem::Device ||
+        kind_of(k2) != Mem::Device)
+        return PENCIL_ERR_PTR;
+    cudaError_t e = launch_conv2d_chain(dtype, c, h, w, in, kh1, kw1, k1, kh2, kw2, k2, out,
+                                        (flags & PENCIL_CONV_GENERIC) != 0, (cudaStream_t)stream);
+    return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
+}
+
 int pencil_conv2d(int h, int w, const float *in, int kh, int kw, const float *k, float *out) {
     if (kh <= 0 || kw <= 0) return PENCIL_ERR_ARG;
     int st = check_dims(h, w);

@@ -79,7 +79,8 @@ struct SepCfg {
     static constexpr int P = round_up(AX, 8);
     static constexpr int SW = TW + 2 * P;
     static constexpr int SH = TH + KY - 1;
-    static constexpr int NX = round_up(P - AX + C + KX - 1, 4);
+    static constexpr int M0 = (P - AX) & ~3;  // first 16-byte chunk a row pass reads
+    static constexpr int NX = round_up(P - AX - M0 + C + KX - 1, 4);
     // in place: the row-pass results overwrite the staged tile (row stride SW)
     static constexpr size_t smem_f32 = sizeof(float) * (size_t)(SH * SW + (INPLACE ? 0 : SH * TW));
     static constexpr size_t smem(size_t esz) { return smem_f32 + (esz == 2 ? 2 * (size_t)SH * SW : 0); }
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
             const int idx = threadIdx.x + k * NT;
             if (idx < ITEMS) {
                 const int r = idx / QPR, q = idx - r * QPR;
-                const float *sp = s_in + r * SW + q * C;
+                const float *sp = s_in + r * SW + q * C + Cfg::M0;
                 float x[NX];
 #pragma unroll
                 for (int m = 0; m < NX; m += 4) {
@@ -131,9 +132,9 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                 float tv[C];
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
-                    float sum = __fmul_rn(fx[0], x[P - AX + c]);
+                    float sum = __fmul_rn(fx[0], x[P - AX - Cfg::M0 + c]);
 #pragma unroll
-                    for (int b = 1; b < KX; ++b) sum = __fmaf_rn(fx[b], x[P - AX + c + b], sum);
+                    for (int b = 1; b < KX; ++b) sum = __fmaf_rn(fx[b], x[P - AX - Cfg::M0 + c + b], sum);
                     tv[c] = sum;
                 }
                 const float4 t4 = make_float4(tv[0], tv[1], tv[2], tv[3]);

@@ -261,7 +261,6 @@ struct DirectCfg {
     static constexpr int SW = TW + 2 * P;
     static constexpr int SH = TH + KH - 1;
     static constexpr int KWP = round_up(KW, 4);     // filter row padded to LDS.128
-    static constexpr int NX = round_up(P - AW + C + KW - 1, 4);
     static constexpr size_t smem_f32 = sizeof(float) * (size_t)(SH * SW + KH * KWP);
     // binary16 staging area appended for FP16 images
     static constexpr size_t smem(size_t esz) { return smem_f32 + (esz == 2 ? 2 * (size_t)SH * SW : 0); }
@@ -304,20 +303,17 @@ __device__ __forceinline__ void direct_row(int r, const float *__restrict__ xrow
     }
 }
 
-// Compute and store one TH x TW output tile with origin (y0, x0) from a
-// staged tile s_in (see stage_tile) and staged filter rows s_k.
-template <typename T, int KH, int KW, int TX, int TY, int R, int G>
-__device__ __forceinline__ void direct_compute(const float *__restrict__ s_in,
-                                               const float *__restrict__ s_k, T *__restrict__ dst,
-                                               int h, int w, bool vec_ok, int y0, int x0) {
-    using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
-    constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, KWP = Cfg::KWP, NX = Cfg::NX,
-                  AW = Cfg::AW, GS = Cfg::GS;
-    constexpr int B0 = P - AW;  // x index of tap 0 for column 0
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    const float *srow = s_in + (ty * R) * SW + tx * C;
-
-    float acc[R][G * 4];
+// The R x (G*4) block of output sums whose taps start at srow (row stride SW;
+// tap (a, b) of column c of group g is srow[a * SW + g * GS + B0 + c + b]),
+// from zero, in the documented order.  Each staged row is read from the
+// 16-byte chunk that holds tap 0 of column 0 onwards, only as far as the taps
+// of column 3 reach.
+template <int KH, int KW, int R, int G, int GS, int SW, int KWP, int B0_>
+__device__ __forceinline__ void direct_accumulate(const float *__restrict__ srow_,
+                                                  const float *__restrict__ s_k, float (&acc)[R][G * 4]) {
+    constexpr int M0 = B0_ & ~3, B0 = B0_ - M0;
+    constexpr int NX = round_up(B0 + 4 + KW - 1, 4);
+    const float *srow = srow_ + M0;
 #pragma unroll
     for (int o = 0; o < R; ++o)
 #pragma unroll
@@ -338,6 +334,20 @@ __device__ __forceinline__ void direct_compute(const float *__restrict__ s_in,
 #pragma unroll
     for (int r = EPI; r < NR; ++r)
         direct_row<true, R, G, GS, KH, KW, KWP, NX, B0>(r, srow + r * SW, s_k, acc);
+}
+
+// Compute and store one TH x TW output tile with origin (y0, x0) from a
+// staged tile s_in (see stage_tile) and staged filter rows s_k.
+template <typename T, int KH, int KW, int TX, int TY, int R, int G>
+__device__ __forceinline__ void direct_compute(const float *__restrict__ s_in,
+                                               const float *__restrict__ s_k, T *__restrict__ dst,
+                                               int h, int w, bool vec_ok, int y0, int x0) {
+    using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
+    constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, KWP = Cfg::KWP, AW = Cfg::AW, GS = Cfg::GS;
+    constexpr int B0 = P - AW;  // x index of tap 0 for column 0
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    float acc[R][G * 4];
+    direct_accumulate<KH, KW, R, G, GS, SW, KWP, B0>(s_in + (ty * R) * SW + tx * C, s_k, acc);
 
 #pragma unroll
     for (int g = 0; g < G; ++g) {

@@ -52,6 +52,14 @@ cudaError_t launch_conv2d_sep(int dtype, int c, int h, int w, const void *in, in
                               const float *gx, int ky, const float *gy, void *out,
                               cudaStream_t s, int border = 0);
 
+// out = conv(conv(in, k1), k2) in one kernel, clamp-to-edge, the intermediate
+// rounded to the storage type; generic forces the runtime-size kernel.
+cudaError_t launch_conv2d_chain(int dtype, int c, int h, int w, const void *in, int kh1, int kw1,
+                                const float *k1, int kh2, int kw2, const float *k2, void *out,
+                                bool generic, cudaStream_t s);
+// Shared memory the generic chain kernel needs for a second filter of kh2 x kw2.
+size_t chain_generic_smem(int kh2, int kw2);
+
 // ----------------------------------------------------------------- jacobi
 size_t jacobi_workspace_bytes(int h, int w);
 cudaError_t jacobi_run(int h, int w, float *u, int iters, int check_every, double *res,
