@@ -28,7 +28,20 @@ __global__ void __launch_bounds__(256)
     if (c >= ncells) return;
     double acc = cell[c];
     const int k1 = __ldg(rowptr + c + 1);
-    for (int k = __ldg(rowptr + c); k < k1; ++k) acc = __dadd_rn(acc, __ldg(edge + __ldg(col + k)));
+    // groups of up to 4 contributions: all their index and value loads are
+    // issued before the additions, which stay in list order
+    for (int k = __ldg(rowptr + c); k < k1; k += 4) {
+        const int n = min(4, k1 - k);
+        int e[4];
+        double v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) e[j] = j < n ? __ldg(col + k + j) : 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = j < n ? __ldg(edge + e[j]) : 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j < n) acc = __dadd_rn(acc, v[j]);
+    }
     cell[c] = acc;
 }
 
