@@ -287,8 +287,8 @@ cudaError_t run_sep(int c, int h, int w, const T *in, const float *gx, const flo
 template <typename T>
 cudaError_t run_sep_any(int c, int h, int w, const T *in, int kx, const float *gx, int ky,
                         const float *gy, T *out, bool vec_ok, int border, cudaStream_t s) {
-    // Tiles from timing sweeps at 8192 x 8192 x 3 FP32; the 15-tap tile is 256
-    // rows tall (the row pass recomputes 14 halo rows per tile, 5% of it).
+    // Tiles from timing sweeps at 8192 x 8192 x 3 FP32; the 15-tap tile is 128
+    // rows tall (its row pass recomputes 14 halo rows per tile, 11% extra).
     if (kx == ky) {
         switch (kx) {
             case 3: return run_sep<T, 3, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, border, s);
