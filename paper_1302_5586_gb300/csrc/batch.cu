@@ -1,18 +1,23 @@
-// batch.cu -- many images, each with its own size and filter side, in one
-// persistent kernel launch replayed from a CUDA graph.
+// batch.cu -- many images, each with its own size and filter side, convolved
+// by one graph launch of persistent kernels, one kernel per filter side.
 //
-// The host builds a tile table: images are ordered by cost (filter side,
-// then tile count, descending) so the most expensive tiles start first, and
-// every tile of image i gets the entry i.  The table, the image descriptors
-// and a header {next, total} are copied to a device buffer owned by the plan;
-// the kernel's CTAs (a resident grid: SMs x CTAs per SM) take tile indices
-// from `next` with one atomicAdd per tile, look the image up, and run the same
-// tile body as the standalone direct kernel; each CTA has two staging slots,
-// so the copies of its next tile run while the current one is computed -- so every batched pixel is the
-// same bits as pencil_conv2d_ex on that image alone.  The kernel reads the
-// tile count from the device header, so one captured graph serves every
-// batch the plan runs.
+// The host builds a tile table grouped by filter side (within a side, images
+// with more tiles first) and a queue header {next, total, start} per side;
+// every tile of image i gets the entry i.  Header, image descriptors and
+// table are copied to a device buffer owned by the plan.  The graph launches,
+// for every side present in the batch, a resident grid (SMs x CTAs per SM)
+// of that side's kernel; its CTAs take tile indices from the side's `next`
+// with one atomicAdd per tile, look the image up, and run the same tile body
+// as the standalone direct kernel, so every batched pixel is the same bits as
+// pencil_conv2d_ex on that image alone.  One kernel per side keeps each
+// kernel's code small (one tile body, two tile heights) and gives it its own
+// register budget and shared-memory slot size, so small filters run more CTAs
+// per SM.  FP32 kernels have two staging slots: the copies of a CTA's next
+// tile run while the current one is computed.  Kernels read the tile counts
+// from the device headers, so the graph captured for a set of sides serves
+// every batch with that set.
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -25,9 +30,9 @@ namespace {
 using namespace tile;
 
 struct BatchHeader {
-    int next;   // next tile to hand out
-    int total;  // tiles in this batch
-    int n;      // images
+    int next;   // next tile of this side's segment to hand out
+    int total;  // tiles of this side in the batch
+    int start;  // first table entry of the segment
     int pad;
 };
 
@@ -40,7 +45,8 @@ struct BatchImage {
     int vec_ok, pad;
 };
 
-constexpr int BT = 128;  // threads per CTA of the batched kernel
+constexpr int BT = 128;     // threads per CTA of the batched kernels
+constexpr int kSides = 8;   // filter sides 1, 3, ..., 15; side index = ks / 2
 
 // Tile shapes (all 128 threads): variant 0 = 32 x 128, variant 1 = 16 x 128.
 // Sides up to 7 use one 4-column group per thread; larger sides two groups.
@@ -53,11 +59,29 @@ __host__ __device__ constexpr int brows(int k, int v) { return k <= 7 ? (v == 0 
 template <int K, int V>
 using BCfg = DirectCfg<K, K, btx(K), bty(K), brows(K, V), bg(K)>;
 
-// A staging slot: filter rows (up to 15 x 16) | FP32 tile | binary16 tile.
-constexpr int kSlotK = 15 * 16;
-constexpr int kSlotIn = BCfg<15, 0>::SH * BCfg<15, 0>::SW;  // the largest staged tile
-static_assert(BCfg<7, 0>::SH * BCfg<7, 0>::SW <= kSlotIn, "slot too small");
-__host__ __device__ constexpr int slot_floats(int esz) { return kSlotK + kSlotIn + (esz == 2 ? kSlotIn / 2 : 0); }
+// A staging slot of side K: filter rows | FP32 tile (variant 0, the larger) |
+// binary16 tile.
+template <int K>
+struct Slot {
+    static constexpr int KF = K * BCfg<K, 0>::KWP;  // a multiple of 4 floats
+    static constexpr int IN = BCfg<K, 0>::SH * BCfg<K, 0>::SW;
+    static_assert(BCfg<K, 1>::SH * BCfg<K, 1>::SW <= IN, "variant 1 tile larger than the slot");
+    __host__ __device__ static constexpr int floats(int esz) { return KF + IN + (esz == 2 ? IN / 2 : 0); }
+};
+constexpr int nslot(size_t esz) { return esz == 2 ? 1 : 2; }
+template <int K>
+constexpr size_t batch_smem(size_t esz) {
+    return nslot(esz) * sizeof(float) * (size_t)Slot<K>::floats((int)esz);
+}
+// CTAs per SM the register budget is sized for: as many as the shared memory
+// allows, except where the tile body would spill at that budget (FP32 side 7,
+// binary16 sides 11 and up).
+constexpr int batch_reg_cap(int k, size_t esz) { return esz == 2 ? (k >= 11 ? 4 : 8) : (k == 7 ? 4 : 8); }
+template <int K>
+constexpr int batch_minb(size_t esz) {
+    return std::min<int>(batch_reg_cap(K, esz),
+                         std::max<int>(1, (int)((228 * 1024) / (batch_smem<K>(esz) + 1024))));
+}
 
 // Issue the copies of one tile (filter and halo tile) into a slot; one commit group.
 template <typename T, int K, int V>
@@ -65,42 +89,29 @@ __device__ __forceinline__ void issue_tile(const BatchImage &d, int y0, int x0, 
     using Cfg = BCfg<K, V>;
     stage_filter_async<K, K, Cfg::KWP, BT>(d.k, slot);
     stage_issue<T, Cfg::SH, Cfg::SW, BT>(static_cast<const T *>(d.in), d.h, d.w, y0 - Cfg::AH, x0 - Cfg::P,
-                                         d.vec_ok, slot + kSlotK,
-                                         reinterpret_cast<T *>(slot + kSlotK + kSlotIn));
+                                         d.vec_ok, slot + Slot<K>::KF,
+                                         reinterpret_cast<T *>(slot + Slot<K>::KF + Slot<K>::IN));
 }
 
 // Widen (binary16) and compute one staged tile.
 template <typename T, int K, int V>
 __device__ __forceinline__ void compute_tile(const BatchImage &d, int y0, int x0, float *slot) {
     using Cfg = BCfg<K, V>;
-    stage_widen<T, Cfg::SH, Cfg::SW, BT>(slot + kSlotK, reinterpret_cast<const T *>(slot + kSlotK + kSlotIn));
-    direct_compute<T, K, K, btx(K), bty(K), brows(K, V), bg(K)>(slot + kSlotK, slot, static_cast<T *>(d.out),
+    stage_widen<T, Cfg::SH, Cfg::SW, BT>(slot + Slot<K>::KF,
+                                         reinterpret_cast<const T *>(slot + Slot<K>::KF + Slot<K>::IN));
+    direct_compute<T, K, K, btx(K), bty(K), brows(K, V), bg(K)>(slot + Slot<K>::KF, slot, static_cast<T *>(d.out),
                                                                d.h, d.w, d.vec_ok, y0, x0);
 }
 
-template <typename T, bool ISSUE>
+template <typename T, int K, bool ISSUE>
 __device__ __forceinline__ void tile_op(const BatchImage &d, int y0, int x0, float *slot) {
-#define PENCIL_BATCH_CASE(K)                                                     \
-    case K:                                                                      \
-        if (d.var == 0) {                                                        \
-            if (ISSUE) issue_tile<T, K, 0>(d, y0, x0, slot);                     \
-            else compute_tile<T, K, 0>(d, y0, x0, slot);                         \
-        } else {                                                                 \
-            if (ISSUE) issue_tile<T, K, 1>(d, y0, x0, slot);                     \
-            else compute_tile<T, K, 1>(d, y0, x0, slot);                         \
-        }                                                                        \
-        break;
-    switch (d.ks) {
-        PENCIL_BATCH_CASE(1)
-        PENCIL_BATCH_CASE(3)
-        PENCIL_BATCH_CASE(5)
-        PENCIL_BATCH_CASE(7)
-        PENCIL_BATCH_CASE(9)
-        PENCIL_BATCH_CASE(11)
-        PENCIL_BATCH_CASE(13)
-        default: PENCIL_BATCH_CASE(15)
+    if (d.var == 0) {
+        if (ISSUE) issue_tile<T, K, 0>(d, y0, x0, slot);
+        else compute_tile<T, K, 0>(d, y0, x0, slot);
+    } else {
+        if (ISSUE) issue_tile<T, K, 1>(d, y0, x0, slot);
+        else compute_tile<T, K, 1>(d, y0, x0, slot);
     }
-#undef PENCIL_BATCH_CASE
 }
 
 __device__ __forceinline__ void tile_origin(const BatchImage &d, int t, int &y0, int &x0) {
@@ -110,27 +121,28 @@ __device__ __forceinline__ void tile_origin(const BatchImage &d, int t, int &y0,
     x0 = tx * kTileW;
 }
 
-// NSLOT = 2: while tile i is computed from one staging slot, the copies of
-// tile i+1 are already in flight into the other.  NSLOT = 1 (binary16, whose
-// slots are larger): the next tile's copies are issued after the compute.
-template <typename T, int NSLOT>
-__global__ void __launch_bounds__(BT, 4)
+// The tiles of one filter side.  NSLOT = 2: while tile i is computed from
+// one staging slot, the copies of tile i+1 are already in flight into the
+// other.  NSLOT = 1 (binary16, whose slots are larger): the next tile's
+// copies are issued after the compute.
+template <typename T, int K, int NSLOT, int MINB>
+__global__ void __launch_bounds__(BT, MINB)
     conv2d_batch_kernel(BatchHeader *__restrict__ hdr, const BatchImage *__restrict__ imgs,
                         const int *__restrict__ tile_img) {
     extern __shared__ __align__(16) float smem[];
     __shared__ int s_next;
-    constexpr int SLOT = slot_floats(sizeof(T));
-    const int total = hdr->total;
+    constexpr int SLOT = Slot<K>::floats(sizeof(T));
+    const int total = hdr->total, start = hdr->start;
     if (threadIdx.x == 0) s_next = atomicAdd(&hdr->next, 1);
     __syncthreads();
     int t = s_next;
     if (t >= total) return;
     __syncthreads();
     if (threadIdx.x == 0) s_next = atomicAdd(&hdr->next, 1);
-    BatchImage d = imgs[__ldg(tile_img + t)];
+    BatchImage d = imgs[__ldg(tile_img + start + t)];
     int y0, x0;
-    tile_origin(d, t, y0, x0);
-    tile_op<T, true>(d, y0, x0, smem);
+    tile_origin(d, start + t, y0, x0);
+    tile_op<T, K, true>(d, y0, x0, smem);
     __syncthreads();
     int tn = s_next;
     for (int i = 0; t < total; ++i) {
@@ -139,20 +151,20 @@ __global__ void __launch_bounds__(BT, 4)
         BatchImage dn;
         int yn = 0, xn = 0;
         if (tn < total) {
-            dn = imgs[__ldg(tile_img + tn)];
-            tile_origin(dn, tn, yn, xn);
+            dn = imgs[__ldg(tile_img + start + tn)];
+            tile_origin(dn, start + tn, yn, xn);
         }
         if (NSLOT == 2 && tn < total) {
-            tile_op<T, true>(dn, yn, xn, nxt);
+            tile_op<T, K, true>(dn, yn, xn, nxt);
             cp_async_wait_prev();  // the current tile's group has landed
         } else {
             cp_async_wait_all();
         }
         __syncthreads();  // every thread has read s_next (end of the previous iteration)
         if (threadIdx.x == 0) s_next = atomicAdd(&hdr->next, 1);
-        tile_op<T, false>(d, y0, x0, cur);
+        tile_op<T, K, false>(d, y0, x0, cur);
         __syncthreads();  // `cur` is free; s_next is visible
-        if (NSLOT == 1 && tn < total) tile_op<T, true>(dn, yn, xn, nxt);
+        if (NSLOT == 1 && tn < total) tile_op<T, K, true>(dn, yn, xn, nxt);
         t = tn;
         d = dn;
         y0 = yn;
@@ -161,10 +173,32 @@ __global__ void __launch_bounds__(BT, 4)
     }
 }
 
-constexpr int nslot(size_t esz) { return esz == 2 ? 1 : 2; }
+using BatchKernel = void (*)(BatchHeader *, const BatchImage *, const int *);
 
-// Dynamic shared memory of the batched kernel.
-size_t batch_smem(size_t esz) { return nslot(esz) * sizeof(float) * (size_t)slot_floats((int)esz); }
+struct SideKernel {
+    BatchKernel fn;
+    size_t smem;
+};
+
+template <typename T, int K>
+SideKernel side_kernel() {
+    constexpr size_t esz = sizeof(T);
+    return {conv2d_batch_kernel<T, K, nslot(esz), batch_minb<K>(esz)>, batch_smem<K>(esz)};
+}
+
+template <typename T>
+SideKernel side_kernel(int idx) {
+    switch (idx) {
+        case 0: return side_kernel<T, 1>();
+        case 1: return side_kernel<T, 3>();
+        case 2: return side_kernel<T, 5>();
+        case 3: return side_kernel<T, 7>();
+        case 4: return side_kernel<T, 9>();
+        case 5: return side_kernel<T, 11>();
+        case 6: return side_kernel<T, 13>();
+        default: return side_kernel<T, 15>();
+    }
+}
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -183,17 +217,21 @@ struct pencil_batch {
     void *hbuf[2] = {nullptr, nullptr};  // pinned host staging (ping-pong)
     cudaEvent_t uploaded[2] = {nullptr, nullptr};
     int flip = 0;
-    int grid = 0;
-    size_t smem = 0;
-    cudaGraphExec_t exec = nullptr;
+    int grid[kSides] = {};       // resident grid of each side's kernel
+    size_t smem[kSides] = {};    // its dynamic shared memory
+    BatchKernel fn[kSides] = {};
+    std::map<unsigned, cudaGraphExec_t> exec;  // graph per set of sides present
     std::mutex mu;
 };
 
 namespace {
 
+size_t head_bytes(int max_images) {
+    return align256(sizeof(BatchHeader) * kSides) + align256(sizeof(BatchImage) * (size_t)max_images);
+}
+
 size_t table_bytes(int max_images, long long max_tiles) {
-    return align256(sizeof(BatchHeader)) + align256(sizeof(BatchImage) * (size_t)max_images) +
-           sizeof(int) * (size_t)max_tiles;
+    return head_bytes(max_images) + sizeof(int) * (size_t)max_tiles;
 }
 
 size_t elem_size(int dtype) { return dtype == PENCIL_F16 ? 2 : 4; }
@@ -233,33 +271,46 @@ bool batch_disjoint(int n, const pencil_image *imgs, size_t esz) {
     return true;
 }
 
-cudaError_t capture_graph(pencil_batch *b) {
+// The graph for a set of sides (bit i = side 2i+1): one launch per side, largest first.
+cudaError_t graph_for(pencil_batch *b, unsigned mask, cudaGraphExec_t *out) {
+    auto it = b->exec.find(mask);
+    if (it != b->exec.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
     cudaStream_t cs;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
     BatchHeader *hdr = static_cast<BatchHeader *>(b->dbuf);
-    BatchImage *imgs = reinterpret_cast<BatchImage *>(static_cast<char *>(b->dbuf) + align256(sizeof(BatchHeader)));
-    int *tile_img = reinterpret_cast<int *>(reinterpret_cast<char *>(imgs) +
-                                            align256(sizeof(BatchImage) * (size_t)b->max_images));
+    BatchImage *imgs = reinterpret_cast<BatchImage *>(static_cast<char *>(b->dbuf) +
+                                                      align256(sizeof(BatchHeader) * kSides));
+    int *tile_img = reinterpret_cast<int *>(static_cast<char *>(b->dbuf) + head_bytes(b->max_images));
     cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        if (b->dtype == PENCIL_F32)
-            conv2d_batch_kernel<float, 2><<<b->grid, BT, b->smem, cs>>>(hdr, imgs, tile_img);
-        else
-            conv2d_batch_kernel<__half, 1><<<b->grid, BT, b->smem, cs>>>(hdr, imgs, tile_img);
-        cudaError_t le = cudaGetLastError();
+        cudaError_t le = cudaSuccess;
+        for (int i = kSides - 1; i >= 0 && le == cudaSuccess; --i)
+            if (mask & (1u << i)) {
+                b->fn[i]<<<b->grid[i], BT, b->smem[i], cs>>>(hdr + i, imgs, tile_img);
+                le = cudaGetLastError();
+            }
         e = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = le;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
+    if (e == cudaSuccess) {
+        b->exec[mask] = x;
+        *out = x;
+    }
     return e;
 }
 
 void release(pencil_batch *b) {
-    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto &kv : b->exec) cudaGraphExecDestroy(kv.second);
+    b->exec.clear();
     for (int i = 0; i < 2; ++i) {
         if (b->uploaded[i]) cudaEventDestroy(b->uploaded[i]);
         if (b->hbuf[i]) cudaFreeHost(b->hbuf[i]);
@@ -283,22 +334,23 @@ int pencil_batch_create(int dtype, int max_images, long long max_tiles, pencil_b
     b->max_images = max_images;
     b->max_tiles = max_tiles;
     b->bytes = table_bytes(max_images, max_tiles);
-    b->smem = batch_smem(elem_size(dtype));
     cudaError_t e = cudaMalloc(&b->dbuf, b->bytes);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaMallocHost(&b->hbuf[i], b->bytes);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded[i], cudaEventDisableTiming);
     }
-    if (e == cudaSuccess) {
-        auto kern = dtype == PENCIL_F32 ? conv2d_batch_kernel<float, 2> : conv2d_batch_kernel<__half, 1>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-        int per_sm = 0, dev = 0, sms = 0;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT, b->smem);
-        if (e == cudaSuccess) e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        b->grid = std::max(1, per_sm) * sms;
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int i = 0; i < kSides && e == cudaSuccess; ++i) {
+        const SideKernel sk = dtype == PENCIL_F32 ? side_kernel<float>(i) : side_kernel<__half>(i);
+        b->fn[i] = sk.fn;
+        b->smem[i] = sk.smem;
+        e = cudaFuncSetAttribute(sk.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sk.smem);
+        int per_sm = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sk.fn, BT, sk.smem);
+        b->grid[i] = std::max(1, per_sm) * sms;
     }
-    if (e == cudaSuccess) e = capture_graph(b);
     if (e != cudaSuccess) {
         release(b);
         delete b;
@@ -339,7 +391,7 @@ int pencil_batch_run(pencil_batch *b, int n, const pencil_image *imgs, void *str
         if (!image_ok(imgs[i])) return PENCIL_ERR_ARG;
     if (!batch_disjoint(n, imgs, esz)) return PENCIL_ERR_ALIAS;
     std::lock_guard<std::mutex> lk(b->mu);
-    // cost order: larger filter side first, then more tiles
+    // grouped by filter side (largest first); within a side, more tiles first
     std::vector<int> order(n);
     std::vector<long long> nt(n);
     for (int i = 0; i < n; ++i) {
@@ -360,9 +412,11 @@ int pencil_batch_run(pencil_batch *b, int n, const pencil_image *imgs, void *str
     if (e != cudaSuccess) return cuda_fail(e);
     char *h = static_cast<char *>(b->hbuf[slot]);
     BatchHeader *hh = reinterpret_cast<BatchHeader *>(h);
-    BatchImage *hi = reinterpret_cast<BatchImage *>(h + align256(sizeof(BatchHeader)));
-    int *ht = reinterpret_cast<int *>(reinterpret_cast<char *>(hi) + align256(sizeof(BatchImage) * (size_t)b->max_images));
+    BatchImage *hi = reinterpret_cast<BatchImage *>(h + align256(sizeof(BatchHeader) * kSides));
+    int *ht = reinterpret_cast<int *>(h + head_bytes(b->max_images));
     const int vec = b->dtype == PENCIL_F16 ? 8 : 4;
+    for (int i = 0; i < kSides; ++i) hh[i] = BatchHeader{0, 0, 0, 0};
+    unsigned mask = 0;
     long long base = 0;
     for (int j = 0; j < n; ++j) {
         const pencil_image &im = imgs[order[j]];
@@ -379,18 +433,21 @@ int pencil_batch_run(pencil_batch *b, int n, const pencil_image *imgs, void *str
         d.vec_ok = (im.w % vec == 0) && ((uintptr_t)im.in % 16 == 0) && ((uintptr_t)im.out % 16 == 0);
         d.pad = 0;
         for (long long t = 0; t < nt[order[j]]; ++t) ht[base + t] = j;
+        BatchHeader &sh = hh[im.ks / 2];
+        if (!(mask & (1u << (im.ks / 2)))) sh.start = (int)base;  // the side's segment begins here
+        mask |= 1u << (im.ks / 2);
+        sh.total += (int)nt[order[j]];
         base += nt[order[j]];
     }
-    hh->next = 0;
-    hh->total = (int)total;
-    hh->n = n;
-    hh->pad = 0;
-    // copy header + descriptors + the used part of the tile table
-    const size_t head = align256(sizeof(BatchHeader)) + align256(sizeof(BatchImage) * (size_t)b->max_images);
+    cudaGraphExec_t x = nullptr;
+    e = graph_for(b, mask, &x);
+    if (e != cudaSuccess) return cuda_fail(e);
+    // copy headers + descriptors + the used part of the tile table
     cudaStream_t s = (cudaStream_t)stream;
-    e = cudaMemcpyAsync(b->dbuf, h, head + sizeof(int) * (size_t)total, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(b->dbuf, h, head_bytes(b->max_images) + sizeof(int) * (size_t)total,
+                        cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(b->uploaded[slot], s);
-    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(x, s);
     return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
 }
 
