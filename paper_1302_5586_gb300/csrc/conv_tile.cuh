@@ -106,9 +106,8 @@ __device__ __forceinline__ void stage_issue(const T *__restrict__ src, int h, in
     constexpr int V = Io<T>::VEC;
     constexpr int CPR = SW / V;
     constexpr bool F16 = sizeof(T) == 2;
-    for (int idx = threadIdx.x; idx < SH * CPR; idx += NT) {
-        const int r = idx / CPR;
-        const int q = idx - r * CPR;
+    // chunk q of staged row r
+    auto chunk = [&](int r, int q) {
         const int gc = x0 + q * V;
         int gr;
         if constexpr (ANYB) {
@@ -120,7 +119,7 @@ __device__ __forceinline__ void stage_issue(const T *__restrict__ src, int h, in
                 } else {
                     *reinterpret_cast<float4 *>(s + r * SW + q * V) = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                continue;
+                return;
             }
         } else {
             gr = clampi(y0 + r, 0, h - 1);
@@ -165,6 +164,17 @@ __device__ __forceinline__ void stage_issue(const T *__restrict__ src, int h, in
                 }
             }
         }
+    };
+    // A thread keeps one chunk column and steps down the rows (no division
+    // per chunk); when a row has more chunks than the CTA has threads, the
+    // chunks are dealt out in order.
+    constexpr int RPP = NT / CPR;
+    if constexpr (RPP >= 1) {
+        const int q = threadIdx.x % CPR, r0 = threadIdx.x / CPR;
+        if (r0 < RPP)
+            for (int r = r0; r < SH; r += RPP) chunk(r, q);
+    } else {
+        for (int idx = threadIdx.x; idx < SH * CPR; idx += NT) chunk(idx / CPR, idx % CPR);
     }
     cp_async_commit();
 }
