@@ -247,129 +247,185 @@ __global__ void __launch_bounds__(256) residual_finish_kernel(const double *__re
 }
 
 // ------------------------------------------------------ temporal tiling
-// T sweeps per HBM round trip.  A CTA stages a (BH+2T) x 136 window of the
-// iterate in shared memory (twice: ping-pong buffers), runs up to T sweeps
-// over the whole window, and writes back the BH x BW core, which is still
-// exact after T sweeps because stale data at the window's edge moves inward
-// by one point per sweep.  Each warp owns RS rows; lane l owns the float4
-// column chunk [4+4l, 8+4l), with left/right neighbours from adjacent lanes.
-// Per point the update is the same FP32 expression as the one-sweep kernel,
-// so the iterate is the same bits for every T.  Residuals of iterates that
-// fall inside the pass are accumulated from the staged values of the core.
-template <int T, int NTHREADS = 512>
-struct TileCfg {
-    static constexpr int NT = NTHREADS;
-    static constexpr int WARPS = NT / 32;
-    static constexpr int SWP = 136;                 // 4 + 32 chunks * 4 + 4
-    static constexpr int P = round_up(T + 3, 4);    // core starts at column P
-    static constexpr int BW = SWP - 2 * P;          // core width
-    static constexpr int RS = (64 + 2 * T - 2 + WARPS - 1) / WARPS;
-    static constexpr int BH = WARPS * RS - 2 * T + 2;  // core height
-    static constexpr int SH = BH + 2 * T;           // staged rows
-    static constexpr size_t smem = 2 * (size_t)SH * SWP * sizeof(float);
+// Up to T sweeps per HBM round trip with the tile held in registers.  A CTA
+// owns a window of NW*RS rows x 128 columns (lane l: columns 4l .. 4l+3; warp
+// k: rows k*RS .. k*RS+RS-1) and its core, rows [T, NW*RS-T) x columns
+// [P, 128-P) with P = T rounded up to 4.  It loads the window once, runs the
+// sweeps on registers -- each warp updates its rows top to bottom, taking
+// left/right neighbours from adjacent lanes (shuffles) and the rows just
+// outside its band from the neighbouring warps through shared memory (one
+// barrier per sweep) -- and writes the core back.  Window rows 0 and NW*RS-1
+// and columns 0 and 127 have no neighbours and take their own values in
+// their place; the wrong values this makes move inward one point per sweep,
+// like stale halo data, so after T sweeps the core is exact.  Grid boundary
+// points keep their values.  Per point the update is the same FP32
+// expression as the one-sweep kernel, so the iterate is the same bits for
+// every T.  Residuals of iterates inside the pass are accumulated, over core
+// points, during the sweep that updates them.
+template <int T>
+struct RegCfg {
+    static constexpr int NW = 8;              // warps
+    static constexpr int RS = 16;             // rows per warp
+    static constexpr int NT = 32 * NW;
+    static constexpr int W = 128;             // window columns: 32 lanes x 4
+    static constexpr int SH = NW * RS;        // window rows
+    static constexpr int P = round_up(T, 4);  // core starts at window column P (16-byte aligned)
+    static constexpr int BW = W - 2 * P;      // core columns
+    static constexpr int BH = SH - 2 * T;     // core rows
 };
 
-template <int T, int NT = 512>
-__global__ void __launch_bounds__(NT)
-    jacobi_tiled_kernel(const float *__restrict__ u, float *__restrict__ v, int h, int w,
-                        int nsweeps, int iter0, int check_every, double *__restrict__ partials,
-                        int nblk) {
-    using Cfg = TileCfg<T, NT>;
-    constexpr int SWP = Cfg::SWP, SH = Cfg::SH, P = Cfg::P, BW = Cfg::BW, BH = Cfg::BH,
-                  RS = Cfg::RS;
-    extern __shared__ __align__(16) float smem[];
-    float *A = smem;
-    float *B = smem + SH * SWP;
-    const int gy0 = blockIdx.y * BH - T;  // global row of staged row 0
-    const int gx0 = blockIdx.x * BW - P;  // global column of staged column 0 (multiple of 4)
-    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-
-    // stage the window into A with cp.async (out-of-grid chunks are 0); B is
-    // fully rewritten on its compute region every sweep, so only its border
-    // (rows 0 and SH-1, columns 0-3 and 132-135) is set, to 0: stale values
-    // there move inward one point per sweep and never reach the core
-    for (int idx = threadIdx.x; idx < SH * (SWP / 4); idx += Cfg::NT) {
-        const int r = idx / (SWP / 4), q = idx - r * (SWP / 4);
-        const int gr = gy0 + r, gc = gx0 + 4 * q;
-        float *dst = A + r * SWP + 4 * q;
-        if (gr >= 0 && gr < h && gc >= 0 && gc < w)
-            cp_async16(dst, u + (size_t)gr * w + gc);
-        else
-            *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r == 0 || r == SH - 1 || q == 0 || q == SWP / 4 - 1)
-            *reinterpret_cast<float4 *>(B + r * SWP + 4 * q) = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    cp_async_commit();
-    cp_async_wait_all();
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int c0 = 4 + 4 * lane;  // this lane's chunk
-    bool cint[4], ccore[4];
+// One sweep over a warp's RS rows, row r held in y[OFF + r].  DOWN: rows
+// are updated top to bottom and new row r goes to y[OFF + r - 1] (the slot of
+// old row r-1, dead once row r is done); otherwise bottom to top into
+// y[OFF + r + 1].  A DOWN sweep from OFF = 1 and an up sweep from OFF = 0
+// bring the band back to its slots without a register copy.  above/below:
+// the rows just outside the band (old values).  EDGE: the window reaches the
+// grid boundary, so points there (and outside the grid) keep their values.
+template <int RS, bool DOWN, int OFF, bool EDGE, bool RESID>
+__device__ __forceinline__ void reg_sweep(float4 (&y)[RS + 1], const float4 above, const float4 below, int g_first,
+                                          int h, const bool (&cint)[4], bool core_cols, int core_lo, int core_hi,
+                                          float &hi, float &lo) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const int gc = gx0 + c0 + e;
-        cint[e] = gc >= 1 && gc <= w - 2;
-        ccore[e] = cint[e] && (c0 + e) >= P && (c0 + e) < P + BW;
-    }
-    const int rbeg = 1 + wp * RS;
-    int slot = 0;
-    for (int t = 0; t < nsweeps; ++t) {
-        const int it = iter0 + t;
-        const bool resid = check_every > 0 && it > 0 && (it % check_every) == 0;
-        float hi = 0.f, lo = 0.f;
-        float4 up = *reinterpret_cast<const float4 *>(A + (rbeg - 1) * SWP + c0);
-        float4 cur = *reinterpret_cast<const float4 *>(A + rbeg * SWP + c0);
-#pragma unroll 3
-        for (int rr = 0; rr < RS; ++rr) {
-            const int r = rbeg + rr;
-            const float4 dn = *reinterpret_cast<const float4 *>(A + (r + 1) * SWP + c0);
-            // neighbours from adjacent lanes; the warp's two edge values are
-            // broadcast loads that every lane issues (no divergent branch)
-            const float lfe = A[r * SWP + 3], rte = A[r * SWP + 132];
-            float lf = __shfl_up_sync(FULL, cur.w, 1);
-            float rt = __shfl_down_sync(FULL, cur.x, 1);
-            lf = lane == 0 ? lfe : lf;
-            rt = lane == 31 ? rte : rt;
-            const int gr = gy0 + r;
-            const bool rint = gr >= 1 && gr <= h - 2;
-            const float sx = nsum(up.x, dn.x, lf, cur.y);
-            const float sy = nsum(up.y, dn.y, cur.x, cur.z);
-            const float sz = nsum(up.z, dn.z, cur.y, cur.w);
-            const float sw = nsum(up.w, dn.w, cur.z, rt);
-            float4 n;
-            n.x = (rint && cint[0]) ? __fmul_rn(0.25f, sx) : cur.x;
-            n.y = (rint && cint[1]) ? __fmul_rn(0.25f, sy) : cur.y;
-            n.z = (rint && cint[2]) ? __fmul_rn(0.25f, sz) : cur.z;
-            n.w = (rint && cint[3]) ? __fmul_rn(0.25f, sw) : cur.w;
-            *reinterpret_cast<float4 *>(B + r * SWP + c0) = n;
-            if (resid && rint && r >= T && r < T + BH) {
-                if (ccore[0]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.x), sx), hi, lo);
-                if (ccore[1]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.y), sy), hi, lo);
-                if (ccore[2]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.z), sz), hi, lo);
-                if (ccore[3]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.w), sw), hi, lo);
-            }
-            up = cur;
-            cur = dn;
+    for (int k = 0; k < RS; ++k) {
+        const int r = DOWN ? k : RS - 1 - k;
+        const float4 cur = y[OFF + r];
+        const float4 upv = r > 0 ? y[OFF + r - 1] : above;
+        const float4 dn = r + 1 < RS ? y[OFF + r + 1] : below;
+        const float lf = __shfl_up_sync(FULL, cur.w, 1);    // lane 0: its own value (window column 0)
+        const float rt = __shfl_down_sync(FULL, cur.x, 1);  // lane 31: its own value (window column 127)
+        const float sx = nsum(upv.x, dn.x, lf, cur.y);
+        const float sy = nsum(upv.y, dn.y, cur.x, cur.z);
+        const float sz = nsum(upv.z, dn.z, cur.y, cur.w);
+        const float sw = nsum(upv.w, dn.w, cur.z, rt);
+        float4 nv = make_float4(__fmul_rn(0.25f, sx), __fmul_rn(0.25f, sy), __fmul_rn(0.25f, sz),
+                                __fmul_rn(0.25f, sw));
+        const int g = g_first + r;
+        if (EDGE) {
+            const bool rint = g >= 1 && g <= h - 2;
+            nv.x = (rint && cint[0]) ? nv.x : cur.x;
+            nv.y = (rint && cint[1]) ? nv.y : cur.y;
+            nv.z = (rint && cint[2]) ? nv.z : cur.z;
+            nv.w = (rint && cint[3]) ? nv.w : cur.w;
         }
-        if (resid) {  // uniform across the block
-            block_sum_store_n<Cfg::NT>((double)hi + (double)lo, partials + (size_t)slot * nblk + bid);
-            ++slot;
+        if (RESID && core_cols && g >= core_lo && g < core_hi && g >= 1 && g <= h - 2) {
+            if (cint[0]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.x), sx), hi, lo);
+            if (cint[1]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.y), sy), hi, lo);
+            if (cint[2]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.z), sz), hi, lo);
+            if (cint[3]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.w), sw), hi, lo);
         }
-        __syncthreads();
-        float *tmp = A;
-        A = B;
-        B = tmp;
+        y[DOWN ? OFF + r - 1 : OFF + r + 1] = nv;
     }
+}
 
-    // write the core back
-    constexpr int CQ = BW / 4;
-    for (int idx = threadIdx.x; idx < BH * CQ; idx += Cfg::NT) {
-        const int r = idx / CQ, q = idx - r * CQ;
-        const int gr = blockIdx.y * BH + r, gc = blockIdx.x * BW + 4 * q;
-        if (gr < h && gc < w)
-            *reinterpret_cast<float4 *>(v + (size_t)gr * w + gc) =
-                *reinterpret_cast<const float4 *>(A + (T + r) * SWP + P + 4 * q);
+// One sweep (DOWN from slots 1..RS, or up from slots 0..RS-1), with the band
+// edge rows exchanged first and, on checkpoint iterates, the residual partial
+// of the warp recorded in wres.
+template <int RS, int NW, bool DOWN, bool EDGE>
+__device__ __forceinline__ void reg_step(float4 (&y)[RS + 1], int t, int iter0, int check_every, float4 *xch,
+                                         double *wres, int &slot, int g_first, int h, const bool (&cint)[4],
+                                         bool core_cols, int core_lo, int core_hi) {
+    constexpr int OFF = DOWN ? 1 : 0;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int it = iter0 + t;
+    const bool resid = check_every > 0 && it > 0 && it % check_every == 0;
+    // band edge rows to the neighbours (double-buffered by sweep parity)
+    float4 *xb = xch + (t & 1) * (NW * 2 * 32);
+    xb[(wp * 2 + 0) * 32 + lane] = y[OFF];
+    xb[(wp * 2 + 1) * 32 + lane] = y[OFF + RS - 1];
+    __syncthreads();
+    const float4 above = wp > 0 ? xb[((wp - 1) * 2 + 1) * 32 + lane] : y[OFF];
+    const float4 below = wp < NW - 1 ? xb[((wp + 1) * 2 + 0) * 32 + lane] : y[OFF + RS - 1];
+    if (resid) {
+        float hi = 0.f, lo = 0.f;
+        reg_sweep<RS, DOWN, OFF, EDGE, true>(y, above, below, g_first, h, cint, core_cols, core_lo, core_hi, hi, lo);
+        // this iterate's partial: fixed butterfly per warp, warps in order later
+        double d = (double)hi + (double)lo;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(FULL, d, off);
+        if (lane == 0) wres[slot * NW + wp] = d;
+        ++slot;
+    } else {
+        float hi = 0.f, lo = 0.f;
+        reg_sweep<RS, DOWN, OFF, EDGE, false>(y, above, below, g_first, h, cint, core_cols, core_lo, core_hi, hi,
+                                              lo);
+    }
+}
+
+template <int T, bool EDGE>
+__device__ __forceinline__ void jacobi_reg_body(const float *__restrict__ u, float *__restrict__ v, int h, int w,
+                                                int n, int gy0, int gx0, int iter0, int check_every,
+                                                float4 *xch, double *wres) {
+    using Cfg = RegCfg<T>;
+    constexpr int RS = Cfg::RS, NW = Cfg::NW, P = Cfg::P, BW = Cfg::BW;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int gc0 = gx0 + 4 * lane;
+    const bool chunk_in = gc0 >= 0 && gc0 < w;  // w % 4 == 0: a chunk is wholly in or out
+    const bool core_cols = 4 * lane >= P && 4 * lane < P + BW && gc0 < w;
+    bool cint[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) cint[e] = gc0 + e >= 1 && gc0 + e <= w - 2;
+    const int g_first = gy0 + wp * RS;  // global row of this warp's first row
+    const int core_lo = gy0 + T, core_hi = min(h, gy0 + T + Cfg::BH);
+
+    float4 y[RS + 1];  // row r in y[1 + r] between pairs of sweeps
+    y[0] = z4;
+#pragma unroll
+    for (int r = 0; r < RS; ++r) {
+        const int g = g_first + r;
+        y[1 + r] = (g >= 0 && g < h && chunk_in) ? __ldg(reinterpret_cast<const float4 *>(u + (size_t)g * w + gc0))
+                                                 : z4;
+    }
+    int slot = 0;
+    int t = 0;
+#pragma unroll 1
+    for (; t + 1 < n; t += 2) {
+        reg_step<RS, NW, true, EDGE>(y, t, iter0, check_every, xch, wres, slot, g_first, h, cint, core_cols,
+                                     core_lo, core_hi);
+        reg_step<RS, NW, false, EDGE>(y, t + 1, iter0, check_every, xch, wres, slot, g_first, h, cint, core_cols,
+                                      core_lo, core_hi);
+    }
+    const int base = (t < n) ? 0 : 1;  // an odd count ends with one more DOWN sweep
+    if (t < n)
+        reg_step<RS, NW, true, EDGE>(y, t, iter0, check_every, xch, wres, slot, g_first, h, cint, core_cols,
+                                     core_lo, core_hi);
+    // the core back to HBM
+    if (core_cols) {
+#pragma unroll
+        for (int r = 0; r < RS; ++r) {
+            const int g = g_first + r;
+            if (g >= core_lo && g < core_hi)
+                *reinterpret_cast<float4 *>(v + (size_t)g * w + gc0) = base ? y[1 + r] : y[r];
+        }
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(RegCfg<T>::NT, 2)
+    jacobi_reg_kernel(const float *__restrict__ u, float *__restrict__ v, int h, int w, int n, int iter0,
+                      int check_every, double *__restrict__ partials, int nblk) {
+    using Cfg = RegCfg<T>;
+    __shared__ float4 xch[2 * Cfg::NW * 2 * 32];
+    __shared__ double wres[T * Cfg::NW];
+    const int gy0 = blockIdx.y * Cfg::BH - T;       // global row of window row 0
+    const int gx0 = blockIdx.x * Cfg::BW - Cfg::P;  // global column of window column 0 (multiple of 4)
+    if (gy0 <= 0 || gy0 + Cfg::SH - 1 >= h - 1 || gx0 <= 0 || gx0 + Cfg::W - 1 >= w - 1)
+        jacobi_reg_body<T, true>(u, v, h, w, n, gy0, gx0, iter0, check_every, xch, wres);
+    else
+        jacobi_reg_body<T, false>(u, v, h, w, n, gy0, gx0, iter0, check_every, xch, wres);
+    __syncthreads();
+    if (threadIdx.x == 0 && check_every > 0) {
+        const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+        int slot = 0;
+        for (int t = 0; t < n; ++t) {
+            const int it = iter0 + t;
+            if (it > 0 && it % check_every == 0) {
+                double sum = wres[slot * Cfg::NW];
+                for (int k = 1; k < Cfg::NW; ++k) sum += wres[slot * Cfg::NW + k];
+                partials[(size_t)slot * nblk + bid] = sum;
+                ++slot;
+            }
+        }
     }
 }
 
@@ -405,41 +461,38 @@ cudaError_t finish(const double *partials, int n, double *res, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+constexpr int kTmax = 10;  // most sweeps per pass
+
 template <int T>
-int tiled_nblk(int h, int w) {
-    using Cfg = TileCfg<T, 512>;
-    return ((w + Cfg::BW - 1) / Cfg::BW) * ((h + Cfg::BH - 1) / Cfg::BH);
+int reg_nblk(int h, int w) {
+    return ((w + RegCfg<T>::BW - 1) / RegCfg<T>::BW) * ((h + RegCfg<T>::BH - 1) / RegCfg<T>::BH);
 }
 
-// Partials capacity for every supported T (T slots per pass at most).
+// Partials capacity for every supported T (T checkpoints per pass at most).
 size_t tiled_partials(int h, int w) {
     size_t m = 0;
-    m = std::max(m, (size_t)tiled_nblk<2>(h, w) * 2);
-    m = std::max(m, (size_t)tiled_nblk<4>(h, w) * 4);
-    m = std::max(m, (size_t)tiled_nblk<5>(h, w) * 5);
-    m = std::max(m, (size_t)tiled_nblk<8>(h, w) * 8);
-    m = std::max(m, (size_t)tiled_nblk<10>(h, w) * 10);
+    m = std::max(m, (size_t)reg_nblk<2>(h, w) * 2);
+    m = std::max(m, (size_t)reg_nblk<4>(h, w) * 4);
+    m = std::max(m, (size_t)reg_nblk<5>(h, w) * 5);
+    m = std::max(m, (size_t)reg_nblk<8>(h, w) * 8);
+    m = std::max(m, (size_t)reg_nblk<10>(h, w) * 10);
     return m;
 }
 
-// Sweeps `iters` times from u (ping-pong with v) using T-sweep passes of at
-// most `per_pass` sweeps; residuals of checkpoint iterates inside a pass go
+// Sweeps `iters` times from u (ping-pong with v) using passes of at most
+// `per_pass` (<= T) sweeps; residuals of checkpoint iterates inside a pass go
 // to res.  Returns the buffer holding the final iterate through *final.
 template <int T>
 cudaError_t run_tiled(int h, int w, float *u, float *v, int iters, int per_pass, int ce,
                       double *res, double *partials, cudaStream_t s, float **final) {
-    using Cfg = TileCfg<T, 512>;
-    auto kern = jacobi_tiled_kernel<T, 512>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Cfg::smem);
-    if (e != cudaSuccess) return e;
+    using Cfg = RegCfg<T>;
     const dim3 grid((w + Cfg::BW - 1) / Cfg::BW, (h + Cfg::BH - 1) / Cfg::BH);
     const int nblk = (int)(grid.x * grid.y);
     float *cur = u, *nxt = v;
     for (int iter = 0; iter < iters;) {
         const int n = std::min(per_pass, iters - iter);
-        kern<<<grid, Cfg::NT, Cfg::smem, s>>>(cur, nxt, h, w, n, iter, ce, partials, nblk);
-        e = cudaGetLastError();
+        jacobi_reg_kernel<T><<<grid, Cfg::NT, 0, s>>>(cur, nxt, h, w, n, iter, ce, partials, nblk);
+        cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         int slot = 0;
         for (int t = 0; t < n; ++t) {
@@ -470,10 +523,12 @@ static double *partials_of(void *ws, int h, int w) {
                                       align256(sizeof(float) * (size_t)h * (size_t)w));
 }
 
-// Sweeps per pass actually used for a request (0 = library choice).
-static int choose_t(int temporal_t, bool vec) {
+// Sweeps per pass actually used for a request (0 = library choice: 10 on
+// grids large enough that the halo work of a 128 x 128 tile pays off, else 4;
+// measured on GB300, 8192^2 x 100 sweeps: T = 4/5/8/10 take 3.8/3.6/3.3/3.2 ms).
+static int choose_t(int temporal_t, bool vec, int h, int w) {
     if (!vec) return 1;
-    if (temporal_t == 0) return 5;
+    if (temporal_t == 0) return (h >= 512 && w >= 512) ? 10 : 4;
     return std::min(temporal_t, 10);
 }
 
@@ -488,7 +543,7 @@ cudaError_t jacobi_run(int h, int w, float *u, int iters, int check_every, doubl
     float *v = static_cast<float *>(ws);
     double *partials = partials_of(ws, h, w);
     const Plan p = make_plan(h, w, u, v);
-    const int t = choose_t(temporal_t, p.vec);
+    const int t = choose_t(temporal_t, p.vec, h, w);
     float *cur = u;
     cudaError_t e = cudaSuccess;
     if (t >= 2) {
