@@ -41,7 +41,7 @@ PX_PER_STEP = PX_PER_PASS * PASSES
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
-SERVE_SECONDS = 10.0
+SERVE_SECONDS = 60.0
 WORKLOAD = ("conv2d clamp-to-edge, 3 planar channels of 8192x8192 FP32, filters 3x3/7x7/15x15 "
             "direct (normalised U[0,1) weights) + 15x15 Gaussian sigma=3 separable")
 
@@ -630,7 +630,7 @@ def run_case(name, reps):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default=None,
-                    help="profile one kernel on a reduced workload: conv3, conv7, conv15, sep15, batch, jacobi, jacobi-t5, op2-ordered, op2-atomic, chain3, chain5, chain7")
+                    help="profile one kernel on a reduced workload: conv3, conv7, conv15, sep15, batch, jacobi, jacobi-tN (N sweeps per pass), op2-ordered, op2-atomic, chain3, chain5, chain7")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=600)

@@ -287,7 +287,7 @@ cudaError_t run_sep(int c, int h, int w, const T *in, const float *gx, const flo
 template <typename T>
 cudaError_t run_sep_any(int c, int h, int w, const T *in, int kx, const float *gx, int ky,
                         const float *gy, T *out, bool vec_ok, int border, cudaStream_t s) {
-    // Tiles from timing sweeps at 8192 x 8192 x 3 FP32; the 15-tap tile is 128
+    // Tiles from timing sweeps at 8192 x 8192 x 3; the FP32 15-tap tile is 128
     // rows tall (its row pass recomputes 14 halo rows per tile, 11% extra).
     if (kx == ky) {
         switch (kx) {
@@ -297,7 +297,9 @@ cudaError_t run_sep_any(int c, int h, int w, const T *in, int kx, const float *g
             case 9: return run_sep<T, 9, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
             case 11: return run_sep<T, 11, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
             case 13: return run_sep<T, 13, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
-            case 15: return run_sep<T, 15, 16, 8, 16, 4, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 15:  // binary16: the taller tile's staging area would cost CTAs per SM
+                if (sizeof(T) == 4) return run_sep<T, 15, 16, 8, 16, 4, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+                return run_sep<T, 15, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
             default: break;
         }
     }
