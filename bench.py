@@ -377,8 +377,9 @@ def measure_serving(torch, pg, dev, seconds):
 
 def measure_chain(torch, pg, dev, stream, d_img, d_out):
     """Two filters in a row on the 3 x 8192^2 FP32 image: the fused chain
-    kernel against two conv2d passes through a temporary (same bits).  HBM
-    basis: 8 B per pixel fused (read in, write out), 16 B for two passes."""
+    kernel (forced) against two conv2d passes through a temporary (same bits),
+    and what pencil_conv2d_chain picks by default.  HBM basis: 8 B per pixel
+    fused (read in, write out), 16 B for two passes."""
     hbm = measured_peaks().get("hbm_gbs") or 6800.0
     sraw = stream.cuda_stream
     tmp = torch.empty_like(d_img)
@@ -387,6 +388,9 @@ def measure_chain(torch, pg, dev, stream, d_img, d_out):
         k1 = torch.from_numpy(synth.filter_f32(60 + k1s, k1s, k1s)).to(dev)
         k2 = torch.from_numpy(synth.gaussian_2d_f32(k2s // 2, 1.0)).to(dev)
         ms_f = _time_stream(torch, stream, lambda: pg.pencil_conv2d_chain(C, H, W, d_img, k1s, k1s, k1, k2s, k2s, k2,
+                                                                          d_out[0], pg.PENCIL_F32,
+                                                                          pg.PENCIL_CHAIN_FUSED, sraw), 10)
+        ms_l = _time_stream(torch, stream, lambda: pg.pencil_conv2d_chain(C, H, W, d_img, k1s, k1s, k1, k2s, k2s, k2,
                                                                           d_out[0], pg.PENCIL_F32, 0, sraw), 10)
 
         def two():
@@ -396,6 +400,7 @@ def measure_chain(torch, pg, dev, stream, d_img, d_out):
         flop = 2 * (k1s * k1s + k2s * k2s) * PX_PER_PASS
         res[f"{k1s}x{k1s}->{k2s}x{k2s}"] = {
             "fused_ms": round(ms_f, 4), "two_pass_ms": round(ms_t, 4), "speedup": round(ms_t / ms_f, 3),
+            "library_choice_ms": round(ms_l, 4),
             "fused_hbm_frac": round(8 * PX_PER_PASS / (ms_f * 1e-3) / 1e9 / hbm, 4),
             "fused_fp32_frac": round(flop / (ms_f * 1e-3) / 1e12 / fp32_peak_tflops(), 4)}
     del tmp

@@ -62,6 +62,8 @@ enum { PENCIL_F32 = 0, PENCIL_F16 = 1 };
  * specialised one exists.  The result is the same bits; the flag exists so
  * that the fixed per-pixel order can be checked across kernels. */
 #define PENCIL_CONV_GENERIC 1
+/* pencil_conv2d_chain: run the fused kernel even where two passes are faster */
+#define PENCIL_CHAIN_FUSED 2
 
 /* Border modes for the _ex conv2d calls, passed in flags as PENCIL_BORDER(m);
  * index i of an axis of length n reads (the plain calls always clamp):
@@ -131,13 +133,18 @@ int pencil_conv2d_sep_ex(int c, int h, int w, const void *in, int kx, const floa
  * through HBM (the fusion of dependent stencils, Sec. 2.2.3).  The result is
  * bit-identical to two pencil_conv2d_ex calls through a temporary of the same
  * dtype: the intermediate is rounded to the storage type and the second
- * filter reads it clamped at the image edge.  Clamp-to-edge only.  Square odd
- * sides 3, 5, 7 for both filters use the tiled kernel, any other sides a
- * generic one (PENCIL_CONV_GENERIC forces it).  Every array is device memory
+ * filter reads it clamped at the image edge.  Clamp-to-edge only.  Fusion
+ * pays while the chain is bound by memory traffic: when both filters have
+ * sides up to 5 the call runs the fused kernel (square odd sides 3 and 5 a
+ * tiled one, other sides a generic one), otherwise two passes through a
+ * temporary from a library-owned stream-ordered pool (kept for reuse until
+ * pencil_shutdown) -- the same bits either way.
+ * PENCIL_CHAIN_FUSED forces the fused kernel (tiled for square odd sides
+ * 3, 5, 7), PENCIL_CONV_GENERIC the generic fused one.  Every array is device memory
  * (in, out: c*h*w elements of dtype; k1: kh1*kw1, k2: kh2*kw2 FP32).
  * Errors: ARG, NULL, ALIAS (out overlaps in, k1 or k2), PTR, UNSUPPORTED (a
  * border mode other than clamp, or a second filter too large for on-chip
- * memory), CUDA. */
+ * memory), NOMEM (the temporary), CUDA. */
 int pencil_conv2d_chain(int c, int h, int w, const void *in, int kh1, int kw1, const float *k1,
                         int kh2, int kw2, const float *k2, void *out, int dtype, int flags,
                         void *stream);
@@ -304,7 +311,9 @@ int pencil_jacobi2d_until(int h, int w, float *u, int max_iters, int check_every
  * The over-relaxed variant of the sequential untilconverged loop (Sec. 3.2):
  * it needs O(n) sweeps where the Jacobi sweep needs O(n^2).  Residuals every
  * check_every sweeps as for pencil_jacobi2d_ex.  u, res_out, workspace:
- * device memory; workspace of pencil_rbsor2d_workspace_size(h, w) bytes.
+ * device memory; workspace of pencil_rbsor2d_workspace_size(h, w) bytes (a
+ * second grid for the tiled passes, which read one grid and write the other,
+ * and the residual partials).
  * Errors: ARG, NULL, ALIAS, PTR, NOMEM, CUDA. */
 size_t pencil_rbsor2d_workspace_size(int h, int w);
 int pencil_rbsor2d_ex(int h, int w, float *u, int iters, float omega, int check_every,
@@ -359,8 +368,9 @@ int pencil_version(void);
 /* The cudaError_t of the calling thread's most recent PENCIL_ERR_CUDA, or 0. */
 int pencil_last_cuda_error(void);
 
-/* Release the library's device pool (plain calls' scratch). Safe to call
- * more than once; later plain calls allocate again. */
+/* Release the library's device pools (plain calls' scratch, the temporaries
+ * of pencil_conv2d_chain).  Call when no library work is in flight.  Safe to
+ * call more than once; later calls allocate again. */
 void pencil_shutdown(void);
 
 #ifdef __cplusplus

@@ -188,6 +188,7 @@ def pencil_conv2d_chain(c, h, w, inp, kh1, kw1, k1, kh2, kw2, k2, out, dtype, fl
                                      dtype, flags, _stream(stream)), "pencil_conv2d_chain")
 
 
+PENCIL_CHAIN_FUSED = 2
 PENCIL_OP2_ORDERED = 0
 PENCIL_OP2_ATOMIC = 1
 

@@ -74,7 +74,38 @@ struct Pool {
         }
         return streams[i];
     }
+    // A stream-ordered allocation pool per device for temporaries of
+    // stream-ordered calls; it keeps its memory for reuse (release threshold
+    // = unlimited) until pencil_shutdown, and leaves the device's default pool
+    // alone.  Caller holds mu.
+    static constexpr int kMaxDev = 64;
+    cudaMemPool_t mpool[kMaxDev] = {};
+    cudaMemPool_t stream_pool() {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        if (!mpool[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            if (cudaMemPoolCreate(&mpool[dev], &props) != cudaSuccess) {
+                cudaGetLastError();
+                mpool[dev] = nullptr;
+                return nullptr;
+            }
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(mpool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        return mpool[dev];
+    }
     void release() {
+        for (int d = 0; d < kMaxDev; ++d) {
+            if (mpool[d]) cudaMemPoolDestroy(mpool[d]);  // freed once its last block is
+            mpool[d] = nullptr;
+        }
         for (int i = 0; i < kSlots; ++i) {
             if (buf[i]) cudaFree(buf[i]);
             buf[i] = nullptr;
@@ -234,7 +265,8 @@ int pencil_conv2d_sep_ex(int c, int h, int w, const void *in, int kx, const floa
 
 int pencil_conv2d_chain(int c, int h, int w, const void *in, int kh1, int kw1, const float *k1, int kh2,
                         int kw2, const float *k2, void *out, int dtype, int flags, void *stream) {
-    if (c <= 0 || kh1 <= 0 || kw1 <= 0 || kh2 <= 0 || kw2 <= 0 || (flags & ~(PENCIL_CONV_GENERIC | 0xF00)) != 0 ||
+    if (c <= 0 || kh1 <= 0 || kw1 <= 0 || kh2 <= 0 || kw2 <= 0 ||
+        (flags & ~(PENCIL_CONV_GENERIC | PENCIL_CHAIN_FUSED | 0xF00)) != 0 ||
         ((flags >> 8) & 0xF) > PENCIL_BORDER_WRAP)
         return PENCIL_ERR_ARG;
     if (dtype != PENCIL_F32 && dtype != PENCIL_F16) return PENCIL_ERR_ARG;
@@ -250,8 +282,32 @@ int pencil_conv2d_chain(int c, int h, int w, const void *in, int kh1, int kw1, c
     if (kind_of(in) != Mem::Device || kind_of(out) != Mem::Device || kind_of(k1) != Mem::Device ||
         kind_of(k2) != Mem::Device)
         return PENCIL_ERR_PTR;
-    cudaError_t e = launch_conv2d_chain(dtype, c, h, w, in, kh1, kw1, k1, kh2, kw2, k2, out,
-                                        (flags & PENCIL_CONV_GENERIC) != 0, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool fuse = (flags & (PENCIL_CONV_GENERIC | PENCIL_CHAIN_FUSED)) != 0 ||
+                      std::max(std::max(kh1, kw1), std::max(kh2, kw2)) <= 5;
+    if (fuse) {
+        cudaError_t e = launch_conv2d_chain(dtype, c, h, w, in, kh1, kw1, k1, kh2, kw2, k2, out,
+                                            (flags & PENCIL_CONV_GENERIC) != 0, s);
+        return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
+    }
+    // compute-bound chain: two passes through a stream-ordered temporary
+    void *tmp = nullptr;
+    cudaMemPool_t mp = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(pool().mu);
+        mp = pool().stream_pool();
+    }
+    if (!mp) return PENCIL_ERR_NOMEM;
+    cudaError_t e = cudaMallocFromPoolAsync(&tmp, nb, mp, s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return PENCIL_ERR_NOMEM;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = launch_conv2d(dtype, c, h, w, in, kh1, kw1, k1, tmp, s);
+    if (e == cudaSuccess) e = launch_conv2d(dtype, c, h, w, tmp, kh2, kw2, k2, out, s);
+    const cudaError_t ef = cudaFreeAsync(tmp, s);
+    if (e == cudaSuccess) e = ef;
     return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
 }
 

@@ -170,49 +170,8 @@ __global__ void __launch_bounds__(JT)
 // u + omega * (0.25f * ((up + down) + (left + right)) - u)   [fma(omega, d, u)]
 // in FP32 in exactly that order.  A point's four neighbours have the other
 // colour and are not written in this pass, so the pass has no read-after-write
-// dependence; a thread writes back its whole float4, the other colour's
-// values unchanged.
-template <int COLOR>
-__global__ void __launch_bounds__(JT) rbsor_v4_kernel(float *__restrict__ u, int h, int w, float omega) {
-    const int lane = threadIdx.x & 31;
-    const int q = blockIdx.x * JT + threadIdx.x;
-    const int j0 = q * 4;
-    const bool colok = j0 < w;
-    const int w4 = w >> 2;
-    const int i0 = blockIdx.y * JR;
-    float4 *U = reinterpret_cast<float4 *>(u);
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 up = (colok && i0 > 0) ? U[(size_t)(i0 - 1) * w4 + q] : z4;
-    float4 cur = (colok && i0 < h) ? U[(size_t)i0 * w4 + q] : z4;
-#pragma unroll 4
-    for (int o = 0; o < JR; ++o) {
-        const int i = i0 + o;
-        if (i >= h) break;
-        const float4 dn = (colok && i + 1 < h) ? U[(size_t)(i + 1) * w4 + q] : z4;
-        float lf = __shfl_up_sync(FULL, cur.w, 1);
-        float rt = __shfl_down_sync(FULL, cur.x, 1);
-        if (lane == 0) lf = (colok && j0 > 0) ? u[(size_t)i * w + j0 - 1] : 0.f;
-        if (lane == 31) rt = (colok && j0 + 4 < w) ? u[(size_t)i * w + j0 + 4] : 0.f;
-        if (colok && i > 0 && i < h - 1) {
-            const int par = (i + j0) & 1;  // colour of column j0 in this row
-            float4 n = cur;
-            const float s[4] = {nsum(up.x, dn.x, lf, cur.y), nsum(up.y, dn.y, cur.x, cur.z),
-                                nsum(up.z, dn.z, cur.y, cur.w), nsum(up.w, dn.w, cur.z, rt)};
-            float c[4] = {cur.x, cur.y, cur.z, cur.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int j = j0 + e;
-                if (((par + e) & 1) == COLOR && j > 0 && j < w - 1)
-                    c[e] = __fmaf_rn(omega, __fsub_rn(__fmul_rn(0.25f, s[e]), c[e]), c[e]);
-            }
-            n = make_float4(c[0], c[1], c[2], c[3]);
-            U[(size_t)i * w4 + q] = n;
-        }
-        up = cur;
-        cur = dn;
-    }
-}
-
+// dependence.  This scalar kernel serves grids whose rows are not 16-byte
+// aligned; aligned grids take the register tiles below.
 template <int COLOR>
 __global__ void __launch_bounds__(JT) rbsor_s_kernel(float *__restrict__ u, int h, int w, float omega) {
     const int j = blockIdx.x * JT + threadIdx.x;
@@ -429,6 +388,105 @@ __global__ void __launch_bounds__(RegCfg<T>::NT, 2)
     }
 }
 
+// Red-black SOR passes with the tile in registers: the same 128 x 128
+// window of 8 warps x 16 rows as the Jacobi tiles.  A sweep is two colour
+// phases; in each, the points of one colour ((i + j) even first) take
+// u <- fma(omega, 0.25*s - u, u), s = (up + down) + (left + right), in place:
+// their neighbours all have the other colour, so the phase reads none of its
+// own results.  Band edge rows are exchanged through shared memory before
+// every phase.  Wrong values at the window edges move inward two points per
+// sweep, so the core is the window minus 2T rows and P columns (P = 2T
+// rounded up to 4) on each side.  Reads u, writes the core to v.
+template <int T>
+struct SorCfg {
+    static constexpr int NW = 8, RS = 16, NT = 32 * NW, W = 128, SH = NW * RS;
+    static constexpr int P = round_up(2 * T, 4);
+    static constexpr int BW = W - 2 * P;
+    static constexpr int BH = SH - 4 * T;
+};
+
+template <int RS, bool EDGE>
+__device__ __forceinline__ void sor_phase(float4 (&x)[RS], const float4 above, const float4 below, int color,
+                                          int g_first, int h, const bool (&cint)[4], float omega) {
+#pragma unroll
+    for (int r = 0; r < RS; ++r) {
+        const float4 cur = x[r];
+        const float4 up = r > 0 ? x[r - 1] : above;
+        const float4 dn = r + 1 < RS ? x[r + 1] : below;
+        const int g = g_first + r;
+        // columns of this lane are 4-aligned, so the colour's points are
+        // e = a and e = a + 2 with a = (colour + g) & 1
+        const int a = (color + g) & 1;
+        const bool rint = !EDGE || (g >= 1 && g <= h - 2);
+        if (a == 0) {
+            const float lf = __shfl_up_sync(FULL, cur.w, 1);  // lane 0: its own value (window edge)
+            const float s0 = nsum(up.x, dn.x, lf, cur.y);
+            const float s2 = nsum(up.z, dn.z, cur.y, cur.w);
+            if (rint && (!EDGE || cint[0])) x[r].x = __fmaf_rn(omega, __fsub_rn(__fmul_rn(0.25f, s0), cur.x), cur.x);
+            if (rint && (!EDGE || cint[2])) x[r].z = __fmaf_rn(omega, __fsub_rn(__fmul_rn(0.25f, s2), cur.z), cur.z);
+        } else {
+            const float rt = __shfl_down_sync(FULL, cur.x, 1);  // lane 31: its own value (window edge)
+            const float s1 = nsum(up.y, dn.y, cur.x, cur.z);
+            const float s3 = nsum(up.w, dn.w, cur.z, rt);
+            if (rint && (!EDGE || cint[1])) x[r].y = __fmaf_rn(omega, __fsub_rn(__fmul_rn(0.25f, s1), cur.y), cur.y);
+            if (rint && (!EDGE || cint[3])) x[r].w = __fmaf_rn(omega, __fsub_rn(__fmul_rn(0.25f, s3), cur.w), cur.w);
+        }
+    }
+}
+
+template <int T, bool EDGE>
+__device__ __forceinline__ void rbsor_reg_body(const float *__restrict__ u, float *__restrict__ v, int h, int w,
+                                               int n, float omega, int gy0, int gx0, float4 *xch) {
+    using Cfg = SorCfg<T>;
+    constexpr int RS = Cfg::RS, NW = Cfg::NW, P = Cfg::P, BW = Cfg::BW;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int gc0 = gx0 + 4 * lane;
+    const bool chunk_in = gc0 >= 0 && gc0 < w;  // w % 4 == 0: a chunk is wholly in or out
+    const bool core_cols = 4 * lane >= P && 4 * lane < P + BW && gc0 < w;
+    bool cint[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) cint[e] = gc0 + e >= 1 && gc0 + e <= w - 2;
+    const int g_first = gy0 + wp * RS;
+    const int core_lo = gy0 + 2 * T, core_hi = min(h, gy0 + 2 * T + Cfg::BH);
+    float4 x[RS];
+#pragma unroll
+    for (int r = 0; r < RS; ++r) {
+        const int g = g_first + r;
+        x[r] = (g >= 0 && g < h && chunk_in) ? __ldg(reinterpret_cast<const float4 *>(u + (size_t)g * w + gc0)) : z4;
+    }
+#pragma unroll 1
+    for (int k = 0; k < 2 * n; ++k) {  // phase k: colour k & 1
+        float4 *xb = xch + (k & 1) * (NW * 2 * 32);
+        xb[(wp * 2 + 0) * 32 + lane] = x[0];
+        xb[(wp * 2 + 1) * 32 + lane] = x[RS - 1];
+        __syncthreads();
+        const float4 above = wp > 0 ? xb[((wp - 1) * 2 + 1) * 32 + lane] : x[0];
+        const float4 below = wp < NW - 1 ? xb[((wp + 1) * 2 + 0) * 32 + lane] : x[RS - 1];
+        sor_phase<RS, EDGE>(x, above, below, k & 1, g_first, h, cint, omega);
+    }
+    if (core_cols) {
+#pragma unroll
+        for (int r = 0; r < RS; ++r) {
+            const int g = g_first + r;
+            if (g >= core_lo && g < core_hi) *reinterpret_cast<float4 *>(v + (size_t)g * w + gc0) = x[r];
+        }
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(SorCfg<T>::NT, 2)
+    rbsor_reg_kernel(const float *__restrict__ u, float *__restrict__ v, int h, int w, int n, float omega) {
+    using Cfg = SorCfg<T>;
+    __shared__ float4 xch[2 * Cfg::NW * 2 * 32];
+    const int gy0 = blockIdx.y * Cfg::BH - 2 * T;   // global row of window row 0
+    const int gx0 = blockIdx.x * Cfg::BW - Cfg::P;  // global column of window column 0 (multiple of 4)
+    if (gy0 <= 0 || gy0 + Cfg::SH - 1 >= h - 1 || gx0 <= 0 || gx0 + Cfg::W - 1 >= w - 1)
+        rbsor_reg_body<T, true>(u, v, h, w, n, omega, gy0, gx0, xch);
+    else
+        rbsor_reg_body<T, false>(u, v, h, w, n, omega, gy0, gx0, xch);
+}
+
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct Plan {
@@ -460,8 +518,6 @@ cudaError_t finish(const double *partials, int n, double *res, cudaStream_t s) {
     residual_finish_kernel<<<1, 256, 0, s>>>(partials, n, res);
     return cudaGetLastError();
 }
-
-constexpr int kTmax = 10;  // most sweeps per pass
 
 template <int T>
 int reg_nblk(int h, int w) {
@@ -593,10 +649,13 @@ cudaError_t residual_run(int h, int w, const float *u, double *res, void *ws, cu
 // ------------------------------------------------ SOR and converge-to-tol
 namespace pencil {
 
+// Workspace: a second grid (the tiled passes ping-pong) and the residual partials.
 size_t rbsor_workspace_bytes(int h, int w) {
     const size_t nb = (size_t)((w + JT - 1) / JT) * (size_t)((h + JR - 1) / JR);
-    return align256(sizeof(double) * nb);
+    return align256(sizeof(float) * (size_t)h * (size_t)w) + align256(sizeof(double) * nb);
 }
+
+constexpr int kSorT = 5;  // sweeps per tiled SOR pass (halo 2T: measured best on 8192^2)
 
 cudaError_t rbsor_run(int h, int w, float *u, int iters, float omega, int check_every, double *res,
                       void *ws, cudaStream_t s) {
@@ -605,16 +664,37 @@ cudaError_t rbsor_run(int h, int w, float *u, int iters, float omega, int check_
         if (nres > 0) return cudaMemsetAsync(res, 0, sizeof(double) * (size_t)nres, s);
         return cudaSuccess;
     }
-    double *partials = static_cast<double *>(ws);
-    const Plan p = make_plan(h, w, u, nullptr);
-    for (int k = 1; k <= iters; ++k) {
-        if (p.vec) {
-            rbsor_v4_kernel<0><<<p.grid, JT, 0, s>>>(u, h, w, omega);
-            rbsor_v4_kernel<1><<<p.grid, JT, 0, s>>>(u, h, w, omega);
-        } else {
-            rbsor_s_kernel<0><<<p.grid, JT, 0, s>>>(u, h, w, omega);
-            rbsor_s_kernel<1><<<p.grid, JT, 0, s>>>(u, h, w, omega);
+    float *v = static_cast<float *>(ws);
+    double *partials = reinterpret_cast<double *>(static_cast<char *>(ws) +
+                                                  align256(sizeof(float) * (size_t)h * (size_t)w));
+    const Plan p = make_plan(h, w, u, v);
+    if (p.vec) {
+        // tiled passes of up to kSorT sweeps, ending at every checkpoint; u/v ping-pong
+        using Cfg = SorCfg<kSorT>;
+        const dim3 grid((w + Cfg::BW - 1) / Cfg::BW, (h + Cfg::BH - 1) / Cfg::BH);
+        float *cur = u, *nxt = v;
+        for (int k = 0; k < iters;) {
+            int n = std::min(kSorT, iters - k);
+            if (check_every > 0) n = std::min(n, check_every - k % check_every);
+            rbsor_reg_kernel<kSorT><<<grid, Cfg::NT, 0, s>>>(cur, nxt, h, w, n, omega);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            std::swap(cur, nxt);
+            k += n;
+            if (check_every > 0 && k % check_every == 0) {
+                const Plan q = make_plan(h, w, cur, nullptr);
+                e = sweep<true, false>(q, cur, nullptr, h, w, partials, s);
+                if (e == cudaSuccess) e = finish(partials, q.nblocks, res + (k / check_every - 1), s);
+                if (e != cudaSuccess) return e;
+            }
         }
+        if (cur != u) return cudaMemcpyAsync(u, cur, sizeof(float) * (size_t)h * (size_t)w,
+                                             cudaMemcpyDeviceToDevice, s);
+        return cudaSuccess;
+    }
+    for (int k = 1; k <= iters; ++k) {  // rows not 16-byte aligned: one kernel per colour
+        rbsor_s_kernel<0><<<p.grid, JT, 0, s>>>(u, h, w, omega);
+        rbsor_s_kernel<1><<<p.grid, JT, 0, s>>>(u, h, w, omega);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (check_every > 0 && k % check_every == 0) {

@@ -61,10 +61,11 @@ def test_chain_equals_two_passes_f32(k1s, k2s, shape):
     k2 = synth.filter_f32(11 * k2s + 1, k2s, k2s)
     a = chain(img, k1, k2)
     np.testing.assert_array_equal(bits(a), bits(two_pass(img, k1, k2)))
+    np.testing.assert_array_equal(bits(a), bits(chain(img, k1, k2, flags=pg.PENCIL_CHAIN_FUSED)))
     np.testing.assert_array_equal(bits(a), bits(chain(img, k1, k2, flags=pg.PENCIL_CONV_GENERIC)))
 
 
-@pytest.mark.parametrize("k1s,k2s", [(3, 3), (5, 5), (7, 3), (3, 7), (5, 7)])
+@pytest.mark.parametrize("k1s,k2s", [(3, 3), (5, 5), (7, 3), (3, 7), (5, 7), (7, 7)])
 @pytest.mark.parametrize("shape", [(2, 75, 304), (1, 130, 257), (1, 3, 2), (1, 260, 136)])
 def test_chain_equals_two_passes_f16(k1s, k2s, shape):
     dev()
@@ -74,6 +75,7 @@ def test_chain_equals_two_passes_f16(k1s, k2s, shape):
     k2 = synth.filter_f32(5 * k2s, k2s, k2s)
     a = chain(img, k1, k2, pg.PENCIL_F16)
     np.testing.assert_array_equal(bits(a), bits(two_pass(img, k1, k2, pg.PENCIL_F16)))
+    np.testing.assert_array_equal(bits(a), bits(chain(img, k1, k2, pg.PENCIL_F16, pg.PENCIL_CHAIN_FUSED)))
     np.testing.assert_array_equal(bits(a), bits(chain(img, k1, k2, pg.PENCIL_F16, pg.PENCIL_CONV_GENERIC)))
 
 
@@ -86,6 +88,7 @@ def test_generic_pairs_equal_two_passes(kk):
     k1 = synth.filter_f32(a1 + 3 * b1, a1, b1)
     k2 = synth.filter_f32(a2 + 5 * b2 + 100, a2, b2)
     np.testing.assert_array_equal(bits(chain(img, k1, k2)), bits(two_pass(img, k1, k2)))
+    np.testing.assert_array_equal(bits(chain(img, k1, k2, flags=pg.PENCIL_CHAIN_FUSED)), bits(two_pass(img, k1, k2)))
 
 
 def _oracle_chain(img, k1, k2, store):
@@ -102,12 +105,14 @@ def test_chain_matches_oracle(k1s, k2s):
     k1 = synth.filter_f32(91 + k1s, k1s, k1s)
     k2 = synth.filter_f32(93 + k2s, k2s, k2s)
     z, b2, b12 = _oracle_chain(img, k1, k2, np.float32)
-    got = chain(img, k1, k2).astype(np.float64)
-    assert np.all(np.abs(got - z) <= F32_TOL * (b2 + b12))
+    for fl in (0, pg.PENCIL_CHAIN_FUSED):
+        got = chain(img, k1, k2, flags=fl).astype(np.float64)
+        assert np.all(np.abs(got - z) <= F32_TOL * (b2 + b12))
     img16 = synth.to_f16(img)
     z, b2, b12 = _oracle_chain(img16, k1, k2, np.float16)
-    got = chain(img16, k1, k2, pg.PENCIL_F16).astype(np.float64)
-    assert np.all(np.abs(got - z) <= F16_TOL * (b2 + b12))
+    for fl in (0, pg.PENCIL_CHAIN_FUSED):
+        got = chain(img16, k1, k2, pg.PENCIL_F16, fl).astype(np.float64)
+        assert np.all(np.abs(got - z) <= F16_TOL * (b2 + b12))
 
 
 def test_delta_filters_compose_shifts():
@@ -155,6 +160,9 @@ def test_errors():
     assert ei.value.status == -3
     with pytest.raises(pg.PencilError) as ei:
         pg.pencil_conv2d_chain(2, 16, 16, x, 0, 3, k, 3, 3, k, o, pg.PENCIL_F32)
+    assert ei.value.status == -1
+    with pytest.raises(pg.PencilError) as ei:
+        pg.pencil_conv2d_chain(2, 16, 16, x, 3, 3, k, 3, 3, k, o, pg.PENCIL_F32, 4)
     assert ei.value.status == -1
     with pytest.raises(pg.PencilError) as ei:
         pg.pencil_conv2d_chain(2, 16, 16, x.cpu(), 3, 3, k, 3, 3, k, o, pg.PENCIL_F32)
