@@ -251,7 +251,9 @@ cudaError_t run_direct_k(int K, int c, int h, int w, const T *in, const float *k
     // two column groups so each filter-row load feeds eight FMA chains).
     switch (K) {
         case 1: return run_direct<T, 1, 32, 8, 4, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
-        case 3: return run_direct<T, 3, 32, 8, 4, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
+        case 3:  // binary16 (half the bytes per pixel): taller threads, fewer staged rows per output
+            if (sizeof(T) == 2) return run_direct<T, 3, 32, 4, 8, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
+            return run_direct<T, 3, 32, 8, 4, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
         case 5: return run_direct<T, 5, 32, 4, 4, 2, 6>(c, h, w, in, k, out, vec_ok, border, s);
         case 7: return run_direct<T, 7, 32, 4, 8, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
         case 9: return run_direct<T, 9, 32, 4, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
