@@ -13,6 +13,9 @@
  *     VLA form; C++ and CUDA callers see the ABI-identical pointer form.
  *   - Images are dense row-major [h][w] (pitch = w elements); multi-channel
  *     images are planar [c][h][w]; filters are row-major [kh][kw] FP32.
+ *     Sizes: h*w up to 2^40 elements, h up to PENCIL_MAX_ROWS rows and c up
+ *     to PENCIL_MAX_CHANNELS channels (CUDA grid limits); larger return
+ *     PENCIL_ERR_UNSUPPORTED.
  *   - Plain calls (no suffix) are synchronous and keep the sequential meaning
  *     of the loop nest (Sec. 2): they accept host or device memory for every
  *     array and return when the result is in place.
@@ -61,6 +64,8 @@ enum { PENCIL_F32 = 0, PENCIL_F16 = 1 };
 /* pencil_conv2d_ex flag: run the generic (any-size) kernel even where a
  * specialised one exists.  The result is the same bits; the flag exists so
  * that the fixed per-pixel order can be checked across kernels. */
+#define PENCIL_MAX_ROWS 524280      /* 65535 row blocks of 8 */
+#define PENCIL_MAX_CHANNELS 65535
 #define PENCIL_CONV_GENERIC 1
 /* pencil_conv2d_chain: run the fused kernel even where two passes are faster */
 #define PENCIL_CHAIN_FUSED 2

@@ -189,6 +189,8 @@ def pencil_conv2d_chain(c, h, w, inp, kh1, kw1, k1, kh2, kw2, k2, out, dtype, fl
 
 
 PENCIL_CHAIN_FUSED = 2
+PENCIL_MAX_ROWS = 524280
+PENCIL_MAX_CHANNELS = 65535
 PENCIL_OP2_ORDERED = 0
 PENCIL_OP2_ATOMIC = 1
 

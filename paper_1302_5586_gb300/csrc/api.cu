@@ -126,6 +126,7 @@ Pool &pool() {
 int check_dims(int h, int w) {
     if (h <= 0 || w <= 0) return PENCIL_ERR_ARG;
     if ((int64_t)h * (int64_t)w > ((int64_t)1 << 40)) return PENCIL_ERR_ARG;
+    if (h > PENCIL_MAX_ROWS) return PENCIL_ERR_UNSUPPORTED;
     return PENCIL_OK;
 }
 
@@ -230,6 +231,7 @@ int pencil_conv2d_ex(int c, int h, int w, const void *in, int kh, int kw, const 
     if (dtype != PENCIL_F32 && dtype != PENCIL_F16) return PENCIL_ERR_ARG;
     int st = check_dims(h, w);
     if (st) return st;
+    if (c > PENCIL_MAX_CHANNELS) return PENCIL_ERR_UNSUPPORTED;
     if (!in || !k || !out) return PENCIL_ERR_NULL;
     const size_t nb = (size_t)c * h * w * elem_size(dtype);
     if (overlaps(out, nb, in, nb) || overlaps(out, nb, k, sizeof(float) * (size_t)kh * kw))
@@ -250,6 +252,7 @@ int pencil_conv2d_sep_ex(int c, int h, int w, const void *in, int kx, const floa
     if (dtype != PENCIL_F32 && dtype != PENCIL_F16) return PENCIL_ERR_ARG;
     int st = check_dims(h, w);
     if (st) return st;
+    if (c > PENCIL_MAX_CHANNELS) return PENCIL_ERR_UNSUPPORTED;
     if (!in || !gx || !gy || !out) return PENCIL_ERR_NULL;
     if (kx > PENCIL_MAX_SPECIALISED_K || ky > PENCIL_MAX_SPECIALISED_K) return PENCIL_ERR_UNSUPPORTED;
     const size_t nb = (size_t)c * h * w * elem_size(dtype);
@@ -273,6 +276,7 @@ int pencil_conv2d_chain(int c, int h, int w, const void *in, int kh1, int kw1, c
     if ((flags >> 8) & 0xF) return PENCIL_ERR_UNSUPPORTED;  // clamp-to-edge only
     int st = check_dims(h, w);
     if (st) return st;
+    if (c > PENCIL_MAX_CHANNELS) return PENCIL_ERR_UNSUPPORTED;
     if (!in || !k1 || !k2 || !out) return PENCIL_ERR_NULL;
     if (chain_generic_smem(kh2, kw2) > 200 * 1024) return PENCIL_ERR_UNSUPPORTED;
     const size_t nb = (size_t)c * h * w * elem_size(dtype);
@@ -442,7 +446,7 @@ int pencil_jacobi2d_until(int h, int w, float *u, int max_iters, int check_every
     if (max_iters < 0 || check_every < 1 || max_iters % check_every != 0 || temporal_t < 0 ||
         !(tol >= 0.0))
         return PENCIL_ERR_ARG;
-    if (check_dims(h, w)) return PENCIL_ERR_ARG;
+    if (int st0 = check_dims(h, w)) return st0;
     int st = check_iterative(h, w, u, max_iters / check_every, res_out, workspace, ws_bytes,
                              jacobi_workspace_bytes(h, w));
     if (st) return st;
@@ -459,7 +463,7 @@ size_t pencil_rbsor2d_workspace_size(int h, int w) {
 int pencil_rbsor2d_ex(int h, int w, float *u, int iters, float omega, int check_every,
                       double *res_out, void *workspace, size_t ws_bytes, void *stream) {
     if (iters < 0 || check_every < 0 || !(omega > 0.0f && omega < 2.0f)) return PENCIL_ERR_ARG;
-    if (check_dims(h, w)) return PENCIL_ERR_ARG;
+    if (int st0 = check_dims(h, w)) return st0;
     const int nres = check_every > 0 ? iters / check_every : 0;
     int st = check_iterative(h, w, u, nres, res_out, workspace, ws_bytes, rbsor_workspace_bytes(h, w));
     if (st) return st;
@@ -475,7 +479,7 @@ int pencil_rbsor2d_until(int h, int w, float *u, int max_iters, float omega, int
     if (max_iters < 0 || check_every < 1 || max_iters % check_every != 0 ||
         !(omega > 0.0f && omega < 2.0f) || !(tol >= 0.0))
         return PENCIL_ERR_ARG;
-    if (check_dims(h, w)) return PENCIL_ERR_ARG;
+    if (int st0 = check_dims(h, w)) return st0;
     int st = check_iterative(h, w, u, max_iters / check_every, res_out, workspace, ws_bytes,
                              rbsor_workspace_bytes(h, w));
     if (st) return st;

@@ -69,6 +69,14 @@ def test_ex_argument_errors_before_cuda(lib):
     ws = pg.pencil_jacobi2d_workspace_size(8192, 8192)
     assert ws >= 8192 * 8192 * 4 and ws % 256 == 0
     assert pg.pencil_jacobi2d_workspace_size(0, 5) == 0
+    # CUDA grid limits: rows and channels beyond them are refused up front
+    tall = pg.PENCIL_MAX_ROWS + 1
+    assert lib.pencil_conv2d_ex(1, tall, 4, 1, 3, 3, 2, 3, 0, 0, None) == -8
+    assert lib.pencil_conv2d_ex(pg.PENCIL_MAX_CHANNELS + 1, 4, 4, 1, 3, 3, 2, 3, 0, 0, None) == -8
+    assert lib.pencil_conv2d_sep_ex(pg.PENCIL_MAX_CHANNELS + 1, 4, 4, 1, 3, 2, 3, 3, 5, 0, 0, None) == -8
+    assert lib.pencil_jacobi2d_ex(tall, 4, 1, 10, 0, None, 256, 1 << 40, 0, None) == -8
+    assert lib.pencil_rbsor2d_ex(tall, 4, 1, 10, 1.5, 0, None, 256, 1 << 40, None) == -8
+    assert lib.pencil_conv2d(tall, 4, 1, 3, 3, 2, 3) == -8
 
 
 def test_binding_refuses_missing_library(monkeypatch, tmp_path):
@@ -89,3 +97,13 @@ def test_batch_argument_errors_before_cuda(lib):
     assert lib.pencil_batch_set_variant(None, 3, 0) == -2
     assert lib.pencil_batch_run(None, 1, None, None) == -2
     assert lib.pencil_batch_destroy(None) == 0
+
+
+def test_binding_constants_match_the_header():
+    import re
+    text = open(pg.HEADER).read()
+    for name in ("PENCIL_MAX_ROWS", "PENCIL_MAX_CHANNELS", "PENCIL_CHAIN_FUSED", "PENCIL_CONV_GENERIC",
+                 "PENCIL_OP2_ORDERED", "PENCIL_OP2_ATOMIC", "PENCIL_F32", "PENCIL_F16"):
+        m = re.search(r"#define\s+%s\s+(\d+)" % name, text) or re.search(r"\b%s\s*=\s*(\d+)" % name, text)
+        assert m, name
+        assert getattr(pg, name) == int(m.group(1)), name
