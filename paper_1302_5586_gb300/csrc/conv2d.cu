@@ -27,6 +27,11 @@ namespace {
 
 using namespace tile;
 
+// Per-lane operations on a pair of FP32 values (fma.rn.f32x2, mul.rn.f32x2),
+// each lane rounded to nearest even exactly like the scalar operation.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
 template <typename T, int KH, int KW, int TX, int TY, int R, int G, int MINB, bool ANYB>
 __global__ void __launch_bounds__(TX *TY, MINB)
     conv2d_direct_kernel(const T *__restrict__ in, const float *__restrict__ k, T *__restrict__ out,
@@ -69,7 +74,11 @@ __global__ void __launch_bounds__(256)
 
 // --------------------------------------------------------- separable kernel
 // Row pass (kx taps) of the staged halo tile into shared memory, then the
-// column pass (ky taps) from it; nothing intermediate goes to HBM.
+// column pass (ky taps) from it; nothing intermediate goes to HBM.  PAIR bit 1
+// runs the row pass, bit 2 the column pass, on packed FP32 pairs (two adjacent
+// columns per instruction, the same bits as the scalar form; on GB300 a pair
+// instruction costs the issue slots of two scalar ones, so it pays only where
+// it shortens the schedule: measured per side, see sep_pair).
 template <int KX, int KY, int TX, int TY, int R, bool INPLACE = false>
 struct SepCfg {
     static constexpr int C = 4;
@@ -87,7 +96,7 @@ struct SepCfg {
 };
 
 template <typename T, int KX, int KY, int TX, int TY, int R, int MINB = 1, bool INPLACE = false,
-          bool ANYB = false>
+          bool ANYB = false, int PAIR = 0>
 __global__ void __launch_bounds__(TX *TY, MINB)
     conv2d_sep_kernel(const T *__restrict__ in, const float *__restrict__ gx,
                       const float *__restrict__ gy, T *__restrict__ out, int h, int w, bool vec_ok,
@@ -113,6 +122,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
         float fx[KX];
 #pragma unroll
         for (int b = 0; b < KX; ++b) fx[b] = __ldg(gx + b);
+        constexpr int X0 = P - AX - Cfg::M0;  // window index of tap 0 of column 0
         constexpr int QPR = TW / C;
         constexpr int ITEMS = SH * QPR;
         constexpr int PER = (ITEMS + NT - 1) / NT;  // items per thread
@@ -130,12 +140,24 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                     x[m] = v.x; x[m + 1] = v.y; x[m + 2] = v.z; x[m + 3] = v.w;
                 }
                 float tv[C];
+                if constexpr ((PAIR & 1) != 0) {
 #pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    float sum = __fmul_rn(fx[0], x[P - AX - Cfg::M0 + c]);
+                    for (int c = 0; c < C; c += 2) {
+                        float2 sum = mul2(make_float2(fx[0], fx[0]), make_float2(x[X0 + c], x[X0 + c + 1]));
 #pragma unroll
-                    for (int b = 1; b < KX; ++b) sum = __fmaf_rn(fx[b], x[P - AX - Cfg::M0 + c + b], sum);
-                    tv[c] = sum;
+                        for (int b = 1; b < KX; ++b)
+                            sum = fma2(make_float2(fx[b], fx[b]), make_float2(x[X0 + c + b], x[X0 + c + b + 1]), sum);
+                        tv[c] = sum.x;
+                        tv[c + 1] = sum.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        float sum = __fmul_rn(fx[0], x[X0 + c]);
+#pragma unroll
+                        for (int b = 1; b < KX; ++b) sum = __fmaf_rn(fx[b], x[X0 + c + b], sum);
+                        tv[c] = sum;
+                    }
                 }
                 const float4 t4 = make_float4(tv[0], tv[1], tv[2], tv[3]);
                 if (INPLACE)
@@ -164,19 +186,46 @@ __global__ void __launch_bounds__(TX *TY, MINB)
     for (int a = 0; a < KY; ++a) fy[a] = __ldg(gy + a);
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     float acc[R][C];
+    if constexpr ((PAIR & 2) != 0) {
+        float2 acc2[R][C / 2];
 #pragma unroll
-    for (int r = 0; r < R + KY - 1; ++r) {
-        const float4 v = *reinterpret_cast<const float4 *>(s_t + (ty * R + r) * TS + tx * C);
-        const float tv[C] = {v.x, v.y, v.z, v.w};
+        for (int r = 0; r < R + KY - 1; ++r) {
+            const float4 v = *reinterpret_cast<const float4 *>(s_t + (ty * R + r) * TS + tx * C);
+            const float2 tv[C / 2] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
 #pragma unroll
-        for (int o = 0; o < R; ++o) {
-            const int a = r - o;
-            if (a == 0) {
+            for (int o = 0; o < R; ++o) {
+                const int a = r - o;
+                if (a == 0) {
 #pragma unroll
-                for (int c = 0; c < C; ++c) acc[o][c] = __fmul_rn(fy[0], tv[c]);
-            } else if (a > 0 && a < KY) {
+                    for (int q = 0; q < C / 2; ++q) acc2[o][q] = mul2(make_float2(fy[0], fy[0]), tv[q]);
+                } else if (a > 0 && a < KY) {
 #pragma unroll
-                for (int c = 0; c < C; ++c) acc[o][c] = __fmaf_rn(fy[a], tv[c], acc[o][c]);
+                    for (int q = 0; q < C / 2; ++q) acc2[o][q] = fma2(make_float2(fy[a], fy[a]), tv[q], acc2[o][q]);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < R; ++o)
+#pragma unroll
+            for (int q = 0; q < C / 2; ++q) {
+                acc[o][2 * q] = acc2[o][q].x;
+                acc[o][2 * q + 1] = acc2[o][q].y;
+            }
+    } else {
+#pragma unroll
+        for (int r = 0; r < R + KY - 1; ++r) {
+            const float4 v = *reinterpret_cast<const float4 *>(s_t + (ty * R + r) * TS + tx * C);
+            const float tv[C] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int o = 0; o < R; ++o) {
+                const int a = r - o;
+                if (a == 0) {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) acc[o][c] = __fmul_rn(fy[0], tv[c]);
+                } else if (a > 0 && a < KY) {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) acc[o][c] = __fmaf_rn(fy[a], tv[c], acc[o][c]);
+                }
             }
         }
     }
@@ -272,12 +321,12 @@ cudaError_t run_generic(int c, int h, int w, const T *in, int kh, int kw, const 
     return cudaGetLastError();
 }
 
-template <typename T, int K, int TX, int TY, int R, int MINB = 1, bool INPLACE = false>
+template <typename T, int K, int TX, int TY, int R, int MINB = 1, bool INPLACE = false, int PAIR = 0>
 cudaError_t run_sep(int c, int h, int w, const T *in, const float *gx, const float *gy, T *out,
                     bool vec_ok, int border, cudaStream_t s) {
     using Cfg = SepCfg<K, K, TX, TY, R, INPLACE>;
-    auto kern = border == 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false>
-                            : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true>;
+    auto kern = border == 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR>
+                            : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR>;
     const size_t smem = Cfg::smem(sizeof(T));
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
@@ -286,22 +335,28 @@ cudaError_t run_sep(int c, int h, int w, const T *in, const float *gx, const flo
     return cudaGetLastError();
 }
 
+// Packed pair arithmetic in the separable passes (bit 1: row pass, bit 2:
+// column pass), where it measured faster on GB300 at 8192 x 8192 x 3.
+template <typename T>
+constexpr int sep_pair(int k) {
+    if (sizeof(T) == 4) return k == 15 ? 2 : 0;
+    return k == 5 || k == 9 ? 3 : (k >= 7 ? 2 : 0);
+}
+
 template <typename T>
 cudaError_t run_sep_any(int c, int h, int w, const T *in, int kx, const float *gx, int ky,
                         const float *gy, T *out, bool vec_ok, int border, cudaStream_t s) {
-    // Tiles from timing sweeps at 8192 x 8192 x 3; the FP32 15-tap tile is 128
-    // rows tall (its row pass recomputes 14 halo rows per tile, 11% extra).
+    // Tiles from timing sweeps at 8192 x 8192 x 3; the 15-tap tiles are 128
+    // rows tall (the row pass recomputes 14 halo rows per tile, 11% extra).
     if (kx == ky) {
         switch (kx) {
-            case 3: return run_sep<T, 3, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, border, s);
-            case 5: return run_sep<T, 5, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, border, s);
-            case 7: return run_sep<T, 7, 32, 8, 4>(c, h, w, in, gx, gy, out, vec_ok, border, s);
-            case 9: return run_sep<T, 9, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
-            case 11: return run_sep<T, 11, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
-            case 13: return run_sep<T, 13, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
-            case 15:  // binary16: the taller tile's staging area would cost CTAs per SM
-                if (sizeof(T) == 4) return run_sep<T, 15, 16, 8, 16, 4, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
-                return run_sep<T, 15, 16, 8, 8, 4, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 3: return run_sep<T, 3, 32, 8, 4, 1, false, sep_pair<T>(3)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 5: return run_sep<T, 5, 32, 8, 4, 1, false, sep_pair<T>(5)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 7: return run_sep<T, 7, 32, 8, 4, 1, false, sep_pair<T>(7)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 9: return run_sep<T, 9, 16, 8, 8, 4, true, sep_pair<T>(9)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 11: return run_sep<T, 11, 16, 8, 8, 4, true, sep_pair<T>(11)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 13: return run_sep<T, 13, 16, 8, 8, 4, true, sep_pair<T>(13)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 15: return run_sep<T, 15, 16, 8, 16, 4, true, sep_pair<T>(15)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
             default: break;
         }
     }
