@@ -572,13 +572,17 @@ def run_case(name, reps):
 
     dev = torch.device("cuda", 0)
     if name.startswith("conv"):
-        K = int(name[4:].split("-")[0])
+        f16 = name.endswith("h")
+        K = int(name[4:].rstrip("h").split("-")[0])
         c, h, w = 2, 4096, 4096
         img = torch.from_numpy(synth.image_f32(1, c, h, w)).to(dev)
+        if f16:  # binary16 storage: twice the pixels, so the image is still larger than L2
+            c = 4
+            img = torch.from_numpy(synth.to_f16(synth.image_f32(1, c, h, w))).to(dev)
         k = torch.from_numpy(synth.filter_f32(2, K, K)).to(dev)
         out = torch.empty_like(img)
         for _ in range(reps):
-            pg.pencil_conv2d_ex(c, h, w, img, K, K, k, out, pg.PENCIL_F32)
+            pg.pencil_conv2d_ex(c, h, w, img, K, K, k, out, pg.PENCIL_F16 if f16 else pg.PENCIL_F32)
     elif name == "sep15":
         c, h, w = 2, 4096, 4096
         img = torch.from_numpy(synth.image_f32(1, c, h, w)).to(dev)
@@ -635,7 +639,7 @@ def run_case(name, reps):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default=None,
-                    help="profile one kernel on a reduced workload: conv3, conv7, conv15, sep15, batch, jacobi, jacobi-tN (N sweeps per pass), op2-ordered, op2-atomic, chain3, chain5, chain7")
+                    help="profile one kernel on a reduced workload: conv3, conv7, conv15, conv3h (binary16), sep15, batch, jacobi, jacobi-tN (N sweeps per pass), op2-ordered, op2-atomic, chain3, chain5, chain7")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=600)

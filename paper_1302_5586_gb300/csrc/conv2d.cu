@@ -32,14 +32,14 @@ using namespace tile;
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
-template <typename T, int KH, int KW, int TX, int TY, int R, int G, int MINB, bool ANYB>
+template <typename T, int KH, int KW, int TX, int TY, int R, int G, int MINB, bool ANYB, bool HALFW = false>
 __global__ void __launch_bounds__(TX *TY, MINB)
     conv2d_direct_kernel(const T *__restrict__ in, const float *__restrict__ k, T *__restrict__ out,
                          int h, int w, bool vec_ok, int border) {
     using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
     extern __shared__ __align__(16) float smem[];
     const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
-    direct_tile<T, KH, KW, TX, TY, R, G, ANYB>(in + plane, k, out + plane, h, w, vec_ok,
+    direct_tile<T, KH, KW, TX, TY, R, G, ANYB, HALFW>(in + plane, k, out + plane, h, w, vec_ok,
                                                blockIdx.y * Cfg::TH, blockIdx.x * Cfg::TW, smem, border);
 }
 
@@ -278,13 +278,13 @@ cudaError_t set_smem(Kern kern, size_t bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename T, int K, int TX, int TY, int R, int G = 1, int MINB = 1>
+template <typename T, int K, int TX, int TY, int R, int G = 1, int MINB = 1, bool HALFW = false>
 cudaError_t run_direct(int c, int h, int w, const T *in, const float *k, T *out, bool vec_ok,
                        int border, cudaStream_t s) {
     using Cfg = DirectCfg<K, K, TX, TY, R, G>;
-    auto kern = border == 0 ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false>
-                            : conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, true>;
-    const size_t smem = Cfg::smem(sizeof(T));
+    auto kern = border == 0 ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW>
+                            : conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, true, HALFW>;
+    const size_t smem = HALFW ? Cfg::smem_half : Cfg::smem(sizeof(T));
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((w + Cfg::TW - 1) / Cfg::TW, (h + Cfg::TH - 1) / Cfg::TH, c);
@@ -298,13 +298,28 @@ cudaError_t run_direct_k(int K, int c, int h, int w, const T *in, const float *k
     // Tile shapes and register caps per side, from timing sweeps on GB300 at
     // 8192 x 8192 x 3 (small sides: occupancy for HBM streaming; large sides:
     // two column groups so each filter-row load feeds eight FMA chains).
+    // Binary16 images up to side 7 keep the tile binary16 in shared memory
+    // (HALFW): those kernels are bound by shared-memory traffic, which the
+    // FP32 copy doubles; from side 9 the widening in the inner loop costs more
+    // issue slots than it saves.
+    if constexpr (sizeof(T) == 2) {
+        switch (K) {
+            case 1: return run_direct<T, 1, 32, 4, 8, 1, 8, true>(c, h, w, in, k, out, vec_ok, border, s);
+            case 3: return run_direct<T, 3, 32, 4, 8, 1, 8, true>(c, h, w, in, k, out, vec_ok, border, s);
+            case 5: return run_direct<T, 5, 32, 4, 8, 1, 8, true>(c, h, w, in, k, out, vec_ok, border, s);
+            case 7: return run_direct<T, 7, 32, 4, 8, 1, 8, true>(c, h, w, in, k, out, vec_ok, border, s);
+            default: break;
+        }
+    } else {
+        switch (K) {
+            case 1: return run_direct<T, 1, 32, 8, 4, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
+            case 3: return run_direct<T, 3, 32, 8, 4, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
+            case 5: return run_direct<T, 5, 32, 4, 4, 2, 6>(c, h, w, in, k, out, vec_ok, border, s);
+            case 7: return run_direct<T, 7, 32, 4, 8, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
+            default: break;
+        }
+    }
     switch (K) {
-        case 1: return run_direct<T, 1, 32, 8, 4, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
-        case 3:  // binary16 (half the bytes per pixel): taller threads, fewer staged rows per output
-            if (sizeof(T) == 2) return run_direct<T, 3, 32, 4, 8, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
-            return run_direct<T, 3, 32, 8, 4, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
-        case 5: return run_direct<T, 5, 32, 4, 4, 2, 6>(c, h, w, in, k, out, vec_ok, border, s);
-        case 7: return run_direct<T, 7, 32, 4, 8, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
         case 9: return run_direct<T, 9, 32, 4, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
         case 11: return run_direct<T, 11, 32, 4, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
         case 13: return run_direct<T, 13, 32, 4, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);

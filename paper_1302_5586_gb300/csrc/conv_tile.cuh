@@ -274,22 +274,37 @@ struct DirectCfg {
     static constexpr size_t smem_f32 = sizeof(float) * (size_t)(SH * SW + KH * KWP);
     // binary16 staging area appended for FP16 images
     static constexpr size_t smem(size_t esz) { return smem_f32 + (esz == 2 ? 2 * (size_t)SH * SW : 0); }
+    // binary16 tile read as staged (no FP32 copy): filter rows, then the tile
+    static constexpr size_t smem_half = sizeof(float) * (size_t)(KH * KWP) + 2 * (size_t)SH * SW;
 };
+
+// Four consecutive staged values as FP32: one LDS.128 from an FP32 tile, or
+// one LDS.64 from a binary16 tile widened in registers (exact).  p is 16-byte
+// (FP32) or 8-byte (binary16) aligned.
+__device__ __forceinline__ void ld4s(const float *p, float *d) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+}
+__device__ __forceinline__ void ld4s(const __half *p, float *d) {
+    const uint2 v = *reinterpret_cast<const uint2 *>(p);
+    __half2 lo, hi;
+    memcpy(&lo, &v.x, 4);
+    memcpy(&hi, &v.y, 4);
+    const float2 a = __half22float2(lo), b = __half22float2(hi);
+    d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y;
+}
 
 // One staged input row r applied to every output row o that uses it (filter
 // row a = r - o).  CHECK tests a against [0, KH); for a compile-time r the test
 // folds away.
-template <bool CHECK, int R, int G, int GS, int KH, int KW, int KWP, int NX, int B0>
-__device__ __forceinline__ void direct_row(int r, const float *__restrict__ xrow,
+template <bool CHECK, int R, int G, int GS, int KH, int KW, int KWP, int NX, int B0, typename S>
+__device__ __forceinline__ void direct_row(int r, const S *__restrict__ xrow,
                                            const float *__restrict__ s_k, float (&acc)[R][G * 4]) {
     float x[G][NX];
 #pragma unroll
     for (int g = 0; g < G; ++g)
 #pragma unroll
-        for (int m = 0; m < NX; m += 4) {
-            const float4 v = *reinterpret_cast<const float4 *>(xrow + g * GS + m);
-            x[g][m] = v.x; x[g][m + 1] = v.y; x[g][m + 2] = v.z; x[g][m + 3] = v.w;
-        }
+        for (int m = 0; m < NX; m += 4) ld4s(xrow + g * GS + m, &x[g][m]);
 #pragma unroll
     for (int o = 0; o < R; ++o) {
         const int a = r - o;
@@ -316,14 +331,15 @@ __device__ __forceinline__ void direct_row(int r, const float *__restrict__ xrow
 // The R x (G*4) block of output sums whose taps start at srow (row stride SW;
 // tap (a, b) of column c of group g is srow[a * SW + g * GS + B0 + c + b]),
 // from zero, in the documented order.  Each staged row is read from the
-// 16-byte chunk that holds tap 0 of column 0 onwards, only as far as the taps
-// of column 3 reach.
-template <int KH, int KW, int R, int G, int GS, int SW, int KWP, int B0_>
-__device__ __forceinline__ void direct_accumulate(const float *__restrict__ srow_,
+// aligned group of four values that holds tap 0 of column 0 onwards, only as
+// far as the taps of column 3 reach.  S: the staged type (FP32, or binary16
+// widened as it is read).
+template <int KH, int KW, int R, int G, int GS, int SW, int KWP, int B0_, typename S = float>
+__device__ __forceinline__ void direct_accumulate(const S *__restrict__ srow_,
                                                   const float *__restrict__ s_k, float (&acc)[R][G * 4]) {
     constexpr int M0 = B0_ & ~3, B0 = B0_ - M0;
     constexpr int NX = round_up(B0 + 4 + KW - 1, 4);
-    const float *srow = srow_ + M0;
+    const S *srow = srow_ + M0;
 #pragma unroll
     for (int o = 0; o < R; ++o)
 #pragma unroll
@@ -337,19 +353,20 @@ __device__ __forceinline__ void direct_accumulate(const float *__restrict__ srow
     constexpr int EPI = (KH > PRO) ? KH : PRO;
 #pragma unroll
     for (int r = 0; r < PRO; ++r)
-        direct_row<true, R, G, GS, KH, KW, KWP, NX, B0>(r, srow + r * SW, s_k, acc);
+        direct_row<true, R, G, GS, KH, KW, KWP, NX, B0, S>(r, srow + r * SW, s_k, acc);
 #pragma unroll 1
     for (int r = PRO; r < EPI; ++r)
-        direct_row<false, R, G, GS, KH, KW, KWP, NX, B0>(r, srow + r * SW, s_k, acc);
+        direct_row<false, R, G, GS, KH, KW, KWP, NX, B0, S>(r, srow + r * SW, s_k, acc);
 #pragma unroll
     for (int r = EPI; r < NR; ++r)
-        direct_row<true, R, G, GS, KH, KW, KWP, NX, B0>(r, srow + r * SW, s_k, acc);
+        direct_row<true, R, G, GS, KH, KW, KWP, NX, B0, S>(r, srow + r * SW, s_k, acc);
 }
 
 // Compute and store one TH x TW output tile with origin (y0, x0) from a
-// staged tile s_in (see stage_tile) and staged filter rows s_k.
-template <typename T, int KH, int KW, int TX, int TY, int R, int G>
-__device__ __forceinline__ void direct_compute(const float *__restrict__ s_in,
+// staged tile s_in (see stage_tile; FP32, or the binary16 staging area read
+// directly) and staged filter rows s_k.
+template <typename T, int KH, int KW, int TX, int TY, int R, int G, typename S = float>
+__device__ __forceinline__ void direct_compute(const S *__restrict__ s_in,
                                                const float *__restrict__ s_k, T *__restrict__ dst,
                                                int h, int w, bool vec_ok, int y0, int x0) {
     using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
@@ -357,7 +374,7 @@ __device__ __forceinline__ void direct_compute(const float *__restrict__ s_in,
     constexpr int B0 = P - AW;  // x index of tap 0 for column 0
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     float acc[R][G * 4];
-    direct_accumulate<KH, KW, R, G, GS, SW, KWP, B0>(s_in + (ty * R) * SW + tx * C, s_k, acc);
+    direct_accumulate<KH, KW, R, G, GS, SW, KWP, B0, S>(s_in + (ty * R) * SW + tx * C, s_k, acc);
 
 #pragma unroll
     for (int g = 0; g < G; ++g) {
@@ -394,19 +411,33 @@ __device__ __forceinline__ void stage_filter(const float *__restrict__ k, float 
 
 // One TH x TW output tile with origin (y0, x0) of one plane: stage, compute,
 // store.  Called by every thread of an NT-thread block (it contains barriers);
-// `smem` must hold DirectCfg::smem(sizeof(T)) bytes.
-template <typename T, int KH, int KW, int TX, int TY, int R, int G, bool ANYB = false>
+// `smem` must hold DirectCfg::smem(sizeof(T)) bytes, or DirectCfg::smem_half
+// for HALFW.  HALFW (binary16 images): the tile stays binary16 in shared
+// memory and is widened as the windows are read -- half the shared-memory
+// traffic of an FP32 copy, for sides where that traffic is the limit.
+template <typename T, int KH, int KW, int TX, int TY, int R, int G, bool ANYB = false, bool HALFW = false>
 __device__ __forceinline__ void direct_tile(const T *__restrict__ src, const float *__restrict__ k,
                                             T *__restrict__ dst, int h, int w, bool vec_ok, int y0,
                                             int x0, float *__restrict__ smem, int border = 0) {
     using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
     constexpr int SW = Cfg::SW, SH = Cfg::SH, KWP = Cfg::KWP, AH = Cfg::AH, P = Cfg::P;
-    float *s_in = smem;
-    float *s_k = smem + SH * SW;
-    T *s16 = reinterpret_cast<T *>(smem + SH * SW + KH * KWP);
-    stage_filter<KH, KW, KWP, Cfg::NT>(k, s_k);
-    stage_tile<T, SH, SW, Cfg::NT, ANYB>(src, h, w, y0 - AH, x0 - P, vec_ok, s_in, s16, border);
-    direct_compute<T, KH, KW, TX, TY, R, G>(s_in, s_k, dst, h, w, vec_ok, y0, x0);
+    if constexpr (HALFW) {
+        static_assert(sizeof(T) == 2, "HALFW reads a binary16 tile");
+        float *s_k = smem;
+        T *s16 = reinterpret_cast<T *>(smem + KH * KWP);
+        stage_filter<KH, KW, KWP, Cfg::NT>(k, s_k);
+        stage_issue<T, SH, SW, Cfg::NT, ANYB>(src, h, w, y0 - AH, x0 - P, vec_ok, nullptr, s16, border);
+        cp_async_wait_all();
+        __syncthreads();
+        direct_compute<T, KH, KW, TX, TY, R, G, T>(s16, s_k, dst, h, w, vec_ok, y0, x0);
+    } else {
+        float *s_in = smem;
+        float *s_k = smem + SH * SW;
+        T *s16 = reinterpret_cast<T *>(smem + SH * SW + KH * KWP);
+        stage_filter<KH, KW, KWP, Cfg::NT>(k, s_k);
+        stage_tile<T, SH, SW, Cfg::NT, ANYB>(src, h, w, y0 - AH, x0 - P, vec_ok, s_in, s16, border);
+        direct_compute<T, KH, KW, TX, TY, R, G>(s_in, s_k, dst, h, w, vec_ok, y0, x0);
+    }
 }
 
 }  // namespace tile

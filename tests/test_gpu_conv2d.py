@@ -50,8 +50,8 @@ def test_direct_f32_matches_oracle(K, shape):
     assert_within(out, ref, bound, F32_TOL, f"K={K} shape={shape}")
 
 
-@pytest.mark.parametrize("K", [3, 7, 15])
-@pytest.mark.parametrize("shape", [(2, 75, 301), (1, 200, 520), (1, 3, 2)])
+@pytest.mark.parametrize("K", [1, 3, 5, 7, 15])
+@pytest.mark.parametrize("shape", [(2, 75, 301), (1, 200, 520), (1, 3, 2), (2, 40, 264)])
 def test_specialised_and_generic_kernels_agree_bitwise(K, shape):
     c, h, w = shape
     img = synth.image_f32(31 + K, c, h, w)
@@ -74,7 +74,7 @@ def test_generic_sizes_match_oracle(kh, kw):
     assert_within(out, ref, bound, F32_TOL, f"{kh}x{kw}")
 
 
-@pytest.mark.parametrize("K", [3, 7, 15])
+@pytest.mark.parametrize("K", [1, 3, 5, 7, 9, 15])
 @pytest.mark.parametrize("shape", [(2, 75, 304), (1, 130, 257)])
 def test_direct_f16_matches_oracle(K, shape):
     c, h, w = shape
@@ -156,7 +156,7 @@ def test_border_modes_match_oracle(border, shape):
     c, h, w = shape
     m = pg.BORDER_MODES[border]
     img = synth.image_f32(700 + m, c, h, w)
-    for K in (3, 7, 15):
+    for K in (3, 5, 7, 15):
         k = synth.filter_f32(710 + K, K, K)
         a = run_conv(img, k, flags=pg.PENCIL_BORDER(m)).cpu().numpy()
         b = run_conv(img, k, flags=pg.PENCIL_BORDER(m) | pg.PENCIL_CONV_GENERIC).cpu().numpy()
@@ -165,6 +165,8 @@ def test_border_modes_match_oracle(border, shape):
         assert_within(a, ref, bound, F32_TOL, f"{border} K={K}")
         img16 = synth.to_f16(img)
         a16 = run_conv(img16, k, pg.PENCIL_F16, pg.PENCIL_BORDER(m)).cpu().numpy()
+        b16 = run_conv(img16, k, pg.PENCIL_F16, pg.PENCIL_BORDER(m) | pg.PENCIL_CONV_GENERIC).cpu().numpy()
+        np.testing.assert_array_equal(a16.view(np.uint16), b16.view(np.uint16))
         ref16, bound16 = oracle.conv2d(img16, k, border=border)
         assert_within(a16, ref16, bound16, F16_TOL, f"f16 {border} K={K}")
     k = synth.filter_f32(720, 4, 6)
