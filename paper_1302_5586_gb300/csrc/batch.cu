@@ -59,24 +59,42 @@ __host__ __device__ constexpr int brows(int k, int v) { return k <= 7 ? (v == 0 
 template <int K, int V>
 using BCfg = DirectCfg<K, K, btx(K), bty(K), brows(K, V), bg(K)>;
 
+// Binary16 sides up to 7 compute from the staged binary16 tile (no FP32 copy;
+// the standalone kernels do the same).
+__host__ __device__ constexpr bool bhalfw(int k, size_t esz) { return esz == 2 && k <= 7; }
+// Rows that are not 16-byte aligned move in the widest copies and stores each
+// address allows on the memory-bound sides; larger sides keep 4-byte copies
+// (less code around their FMA loop), as the standalone kernels do.
+__host__ __device__ constexpr bool badapt(int k) { return k <= 5; }
+
 // A staging slot of side K: filter rows | FP32 tile (variant 0, the larger) |
-// binary16 tile.
+// binary16 tile; without the FP32 tile where the binary16 tile is read directly.
 template <int K>
 struct Slot {
     static constexpr int KF = K * BCfg<K, 0>::KWP;  // a multiple of 4 floats
     static constexpr int IN = BCfg<K, 0>::SH * BCfg<K, 0>::SW;
     static_assert(BCfg<K, 1>::SH * BCfg<K, 1>::SW <= IN, "variant 1 tile larger than the slot");
-    __host__ __device__ static constexpr int floats(int esz) { return KF + IN + (esz == 2 ? IN / 2 : 0); }
+    __host__ __device__ static constexpr int f16_off(int esz) { return KF + (bhalfw(K, esz) ? 0 : IN); }
+    __host__ __device__ static constexpr int floats(int esz) {
+        return bhalfw(K, esz) ? KF + IN / 2 : KF + IN + (esz == 2 ? IN / 2 : 0);
+    }
 };
-constexpr int nslot(size_t esz) { return esz == 2 ? 1 : 2; }
+// Two staging slots (the next tile's copies overlap the current compute),
+// except for binary16 tiles widened into an FP32 copy, whose slots are larger.
+template <int K>
+constexpr int nslot(size_t esz) { return esz == 2 && !bhalfw(K, esz) ? 1 : 2; }
 template <int K>
 constexpr size_t batch_smem(size_t esz) {
-    return nslot(esz) * sizeof(float) * (size_t)Slot<K>::floats((int)esz);
+    return nslot<K>(esz) * sizeof(float) * (size_t)Slot<K>::floats((int)esz);
 }
 // CTAs per SM the register budget is sized for: as many as the shared memory
-// allows, except where the tile body would spill at that budget (FP32 side 7,
-// binary16 sides 11 and up).
-constexpr int batch_reg_cap(int k, size_t esz) { return esz == 2 ? (k >= 11 ? 4 : 8) : (k == 7 ? 4 : 8); }
+// allows, except where the tile body would spill at that budget (side 7,
+// binary16 sides 3 and 5 with their two slots, binary16 sides 11 and up).
+constexpr int batch_reg_cap(int k, size_t esz) {
+    if (k == 7) return 4;
+    if (esz == 2) return k >= 11 ? 4 : (k == 3 ? 6 : (k == 5 ? 5 : 8));
+    return 8;
+}
 template <int K>
 constexpr int batch_minb(size_t esz) {
     return std::min<int>(batch_reg_cap(K, esz),
@@ -88,19 +106,26 @@ template <typename T, int K, int V>
 __device__ __forceinline__ void issue_tile(const BatchImage &d, int y0, int x0, float *slot) {
     using Cfg = BCfg<K, V>;
     stage_filter_async<K, K, Cfg::KWP, BT>(d.k, slot);
-    stage_issue<T, Cfg::SH, Cfg::SW, BT>(static_cast<const T *>(d.in), d.h, d.w, y0 - Cfg::AH, x0 - Cfg::P,
+    stage_issue<T, Cfg::SH, Cfg::SW, BT, false, badapt(K)>(static_cast<const T *>(d.in), d.h, d.w, y0 - Cfg::AH,
+                                                            x0 - Cfg::P,
                                          d.vec_ok, slot + Slot<K>::KF,
-                                         reinterpret_cast<T *>(slot + Slot<K>::KF + Slot<K>::IN));
+                                         reinterpret_cast<T *>(slot + Slot<K>::f16_off(sizeof(T))));
 }
 
-// Widen (binary16) and compute one staged tile.
+// Widen (binary16, unless read directly) and compute one staged tile.
 template <typename T, int K, int V>
 __device__ __forceinline__ void compute_tile(const BatchImage &d, int y0, int x0, float *slot) {
     using Cfg = BCfg<K, V>;
-    stage_widen<T, Cfg::SH, Cfg::SW, BT>(slot + Slot<K>::KF,
-                                         reinterpret_cast<const T *>(slot + Slot<K>::KF + Slot<K>::IN));
-    direct_compute<T, K, K, btx(K), bty(K), brows(K, V), bg(K)>(slot + Slot<K>::KF, slot, static_cast<T *>(d.out),
-                                                               d.h, d.w, d.vec_ok, y0, x0);
+    const T *s16 = reinterpret_cast<const T *>(slot + Slot<K>::f16_off(sizeof(T)));
+    if constexpr (bhalfw(K, sizeof(T))) {
+        direct_compute<T, K, K, btx(K), bty(K), brows(K, V), bg(K), T, badapt(K)>(s16, slot, static_cast<T *>(d.out),
+                                                                                  d.h, d.w, d.vec_ok, y0, x0);
+    } else {
+        stage_widen<T, Cfg::SH, Cfg::SW, BT>(slot + Slot<K>::KF, s16);
+        direct_compute<T, K, K, btx(K), bty(K), brows(K, V), bg(K), float, badapt(K)>(slot + Slot<K>::KF, slot,
+                                                                   static_cast<T *>(d.out), d.h, d.w, d.vec_ok,
+                                                                   y0, x0);
+    }
 }
 
 template <typename T, int K, bool ISSUE>
@@ -183,7 +208,7 @@ struct SideKernel {
 template <typename T, int K>
 SideKernel side_kernel() {
     constexpr size_t esz = sizeof(T);
-    return {conv2d_batch_kernel<T, K, nslot(esz), batch_minb<K>(esz)>, batch_smem<K>(esz)};
+    return {conv2d_batch_kernel<T, K, nslot<K>(esz), batch_minb<K>(esz)>, batch_smem<K>(esz)};
 }
 
 template <typename T>

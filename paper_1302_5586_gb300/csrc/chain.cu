@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(256, MINB)
     // 1. filters and the input region (clamped)
     stage_filter_async<K1, K1, Cfg::KWP1, NT>(k1, s_k1);
     stage_filter_async<K2, K2, Cfg::KWP2, NT>(k2, s_k2);
-    stage_issue<T, Cfg::XH, SWX, NT>(in + plane, h, w, yr0 - Cfg::A1, yc0 - Cfg::P1, vec_ok, s_x, s16);
+    stage_issue<T, Cfg::XH, SWX, NT, false, false>(in + plane, h, w, yr0 - Cfg::A1, yc0 - Cfg::P1, vec_ok, s_x,
+                                                 s16);
     stage_finish<T, Cfg::XH, SWX, NT>(s_x, s16);
 
     // 2. the intermediate region
@@ -152,7 +153,8 @@ __global__ void __launch_bounds__(256, MINB)
     }
 
     // 4. the second stencil
-    direct_compute<T, K2, K2, Cfg::TX, Cfg::TY, Cfg::R, Cfg::G>(s_y, s_k2, out + plane, h, w, vec_ok, y0, x0);
+    direct_compute<T, K2, K2, Cfg::TX, Cfg::TY, Cfg::R, Cfg::G, float, false>(s_y, s_k2, out + plane, h, w, vec_ok,
+                                                                              y0, x0);
 }
 
 // Generic fused chain: any sizes.  A 256-thread CTA owns a 16 x 32 output

@@ -32,14 +32,20 @@ using namespace tile;
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
-template <typename T, int KH, int KW, int TX, int TY, int R, int G, int MINB, bool ANYB, bool HALFW = false>
+// VMODE: how rows that are not 16-byte aligned are handled.  0: vec_ok at
+// run time, such rows staged in 4-byte copies and stored with scalar stores
+// (compute-bound sides: the least code around the FMA loop); 1: every row
+// aligned (compile-time); 2: rows not aligned, each chunk copied and stored
+// with the widest accesses its address allows (memory-bound sides).
+template <typename T, int KH, int KW, int TX, int TY, int R, int G, int MINB, bool ANYB, bool HALFW, int VMODE>
 __global__ void __launch_bounds__(TX *TY, MINB)
     conv2d_direct_kernel(const T *__restrict__ in, const float *__restrict__ k, T *__restrict__ out,
                          int h, int w, bool vec_ok, int border) {
     using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
     extern __shared__ __align__(16) float smem[];
     const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
-    direct_tile<T, KH, KW, TX, TY, R, G, ANYB, HALFW>(in + plane, k, out + plane, h, w, vec_ok,
+    const bool vok = VMODE == 0 ? vec_ok : VMODE == 1;
+    direct_tile<T, KH, KW, TX, TY, R, G, ANYB, HALFW, VMODE == 2>(in + plane, k, out + plane, h, w, vok,
                                                blockIdx.y * Cfg::TH, blockIdx.x * Cfg::TW, smem, border);
 }
 
@@ -95,12 +101,15 @@ struct SepCfg {
     static constexpr size_t smem(size_t esz) { return smem_f32 + (esz == 2 ? 2 * (size_t)SH * SW : 0); }
 };
 
-template <typename T, int KX, int KY, int TX, int TY, int R, int MINB = 1, bool INPLACE = false,
-          bool ANYB = false, int PAIR = 0>
+template <typename T, int KX, int KY, int TX, int TY, int R, int MINB, bool INPLACE, bool ANYB, int PAIR,
+          int VMODE>
 __global__ void __launch_bounds__(TX *TY, MINB)
     conv2d_sep_kernel(const T *__restrict__ in, const float *__restrict__ gx,
-                      const float *__restrict__ gy, T *__restrict__ out, int h, int w, bool vec_ok,
+                      const float *__restrict__ gy, T *__restrict__ out, int h, int w, bool vec_ok_,
                       int border) {
+    // VMODE as for the direct kernel
+    constexpr bool ADAPT = VMODE == 2;
+    const bool vec_ok = VMODE == 0 ? vec_ok_ : VMODE == 1;
     using Cfg = SepCfg<KX, KY, TX, TY, R, INPLACE>;
     constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, SH = Cfg::SH, TW = Cfg::TW,
                   NX = Cfg::NX, AX = Cfg::AX, AY = Cfg::AY, NT = Cfg::NT;
@@ -115,7 +124,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
     T *dst = out + plane;
     const int x0 = blockIdx.x * TW;
     const int y0 = blockIdx.y * Cfg::TH;
-    stage_tile<T, SH, SW, NT, ANYB>(src, h, w, y0 - AY, x0 - P, vec_ok, s_in, s16, border);
+    stage_tile<T, SH, SW, NT, ANYB, ADAPT>(src, h, w, y0 - AY, x0 - P, vec_ok, s_in, s16, border);
 
     // row pass: t[r][q*C + c] = sum_b gx[b] * in[r][q*C + c + b - AX]
     {
@@ -229,7 +238,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
             }
         }
     }
-    store_block<T, R>(dst, h, w, y0 + ty * R, x0 + tx * C, vec_ok, acc);
+    store_block<T, R, ADAPT>(dst, h, w, y0 + ty * R, x0 + tx * C, vec_ok, acc);
 }
 
 // Separable with runtime tap counts (fallback for sides without a
@@ -282,8 +291,17 @@ template <typename T, int K, int TX, int TY, int R, int G = 1, int MINB = 1, boo
 cudaError_t run_direct(int c, int h, int w, const T *in, const float *k, T *out, bool vec_ok,
                        int border, cudaStream_t s) {
     using Cfg = DirectCfg<K, K, TX, TY, R, G>;
-    auto kern = border == 0 ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW>
-                            : conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, true, HALFW>;
+    // sides up to 5 (memory-bound): an aligned-row kernel and an adaptive
+    // any-row kernel; larger sides: one kernel with vec_ok at run time
+    using Kern = decltype(&conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 0>);
+    Kern kern;
+    if constexpr (K <= 5)
+        kern = border != 0 ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, true, HALFW, 2>
+               : vec_ok    ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 1>
+                           : conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 2>;
+    else
+        kern = border != 0 ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, true, HALFW, 0>
+                           : conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 0>;
     const size_t smem = HALFW ? Cfg::smem_half : Cfg::smem(sizeof(T));
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
@@ -340,8 +358,15 @@ template <typename T, int K, int TX, int TY, int R, int MINB = 1, bool INPLACE =
 cudaError_t run_sep(int c, int h, int w, const T *in, const float *gx, const float *gy, T *out,
                     bool vec_ok, int border, cudaStream_t s) {
     using Cfg = SepCfg<K, K, TX, TY, R, INPLACE>;
-    auto kern = border == 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR>
-                            : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR>;
+    using Kern = decltype(&conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 0>);
+    Kern kern;
+    if constexpr (K <= 5)  // as for the direct kernels
+        kern = border != 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 2>
+               : vec_ok    ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 1>
+                           : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 2>;
+    else
+        kern = border != 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 0>
+                           : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 0>;
     const size_t smem = Cfg::smem(sizeof(T));
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;

@@ -24,6 +24,18 @@ struct Io<float> {
     __device__ __forceinline__ static void st4(float *p, const float *v) {
         *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
     }
+    // four values at any 4-byte aligned address: the widest stores it allows
+    __device__ __forceinline__ static void st4_any(float *p, const float *v) {
+        const unsigned a = (unsigned)(uintptr_t)p;
+        if ((a & 15) == 0) {
+            st4(p, v);
+        } else if ((a & 7) == 0) {
+            *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+            *reinterpret_cast<float2 *>(p + 2) = make_float2(v[2], v[3]);
+        } else {
+            p[0] = v[0]; p[1] = v[1]; p[2] = v[2]; p[3] = v[3];
+        }
+    }
     __device__ __forceinline__ static void ld16s(const float *p, float *d) {
         const float4 v = *reinterpret_cast<const float4 *>(p);
         d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
@@ -60,6 +72,19 @@ struct Io<__half> {
         memcpy(&u.y, &b, 4);
         *reinterpret_cast<uint2 *>(p) = u;
     }
+    // four values at any 2-byte aligned address: the widest stores it allows
+    __device__ __forceinline__ static void st4_any(__half *p, const float *v) {
+        const unsigned a = (unsigned)(uintptr_t)p;
+        if ((a & 7) == 0) {
+            st4(p, v);
+        } else if ((a & 3) == 0) {
+            *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(v[0], v[1]);
+            *reinterpret_cast<__half2 *>(p + 2) = __floats2half2_rn(v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) p[c] = __float2half_rn(v[c]);
+        }
+    }
 };
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
@@ -90,16 +115,23 @@ __device__ __forceinline__ int border_index(int i, int n, int mode) {
 
 // Stage s[r][c] = in[map(y0 + r)][map(x0 + c)] for r < SH, c < SW (as FP32),
 // map = the border mode (clamp-to-edge by default; zero mode stages zeros).
-// x0 is a multiple of VEC, SW a multiple of VEC.  vec_ok: rows are 16-byte
-// aligned (w % VEC == 0 and the plane base is 16-byte aligned).  Everything
-// goes through cp.async (all of a CTA's copies in flight at once): 16-byte
-// chunks inside aligned rows; otherwise 4-byte copies per element from the
-// clamped column (FP32) or per pair (binary16 rows that are 4-byte aligned);
-// only binary16 chunks that are neither use clamped scalar loads.
-// FP32 chunks land in s directly; binary16 chunks land in the staging area
-// `s16` and are widened into s afterwards.  Ends with a barrier.
-// ANYB = false compiles the clamp-to-edge staging only (border ignored).
-template <typename T, int SH, int SW, int NT, bool ANYB = false>
+// x0 is a multiple of VEC, SW a multiple of VEC.  Everything goes through
+// cp.async (all of a CTA's copies in flight at once).  vec_ok: every row is
+// 16-byte aligned (w % VEC == 0 and the plane base 16-byte aligned), so a
+// 16-byte chunk inside its row is one 16-byte copy.  Otherwise each chunk
+// inside its row takes the widest copies its own address allows (one
+// 16-byte, two 8-byte, or -- FP32 -- four 4-byte copies), so rows whose pitch
+// is not a multiple of 16 bytes still move mostly in wide copies.  Chunks
+// across the image edge take 4-byte copies per element from the column the
+// border mode selects (FP32); binary16 chunks that are not 4-byte aligned use
+// scalar loads.  FP32 chunks land in s directly; binary16 chunks land in the
+// staging area `s16` (widened into s afterwards, unless the caller reads
+// s16).  Commits one group.  ANYB = false compiles the clamp-to-edge staging
+// only (border ignored).  ADAPT = false leaves out the per-chunk alignment
+// tests (rows that are not 16-byte aligned then move in 4-byte copies): for
+// compute-bound kernels, where staging is a small part of the time and the
+// extra code costs registers; those kernels pass vec_ok at run time.
+template <typename T, int SH, int SW, int NT, bool ANYB = false, bool ADAPT = true>
 __device__ __forceinline__ void stage_issue(const T *__restrict__ src, int h, int w, int y0, int x0,
                                             bool vec_ok, float *__restrict__ s, T *__restrict__ s16,
                                             int border = 0) {
@@ -126,11 +158,20 @@ __device__ __forceinline__ void stage_issue(const T *__restrict__ src, int h, in
         }
         const T *row = src + (size_t)gr * (size_t)w;
         const bool inside = gc >= 0 && gc + V <= w;
-        if (vec_ok && inside) {
+        const unsigned mis = (unsigned)(uintptr_t)(row + gc) & 15u;
+        if (inside && (ADAPT ? (vec_ok || mis == 0) : vec_ok)) {
             if (F16)
                 cp_async16(s16 + r * SW + q * V, row + gc);
             else
                 cp_async16(s + r * SW + q * V, row + gc);
+        } else if (ADAPT && !vec_ok && inside && (mis & 7u) == 0) {
+            if (F16) {
+                cp_async8(s16 + r * SW + q * V, row + gc);
+                cp_async8(s16 + r * SW + q * V + V / 2, row + gc + V / 2);
+            } else {
+                cp_async8(s + r * SW + q * V, row + gc);
+                cp_async8(s + r * SW + q * V + V / 2, row + gc + V / 2);
+            }
         } else if (!F16) {
             // unaligned row or a chunk across the edge: one 4-byte copy per
             // element, from the column the border mode selects
@@ -147,7 +188,7 @@ __device__ __forceinline__ void stage_issue(const T *__restrict__ src, int h, in
                     cp_async4(d + e, row + clampi(gc + e, 0, w - 1));
                 }
             }
-        } else if (inside && ((uintptr_t)(row + gc) & 3) == 0) {
+        } else if (inside && (mis & 3u) == 0) {
             // binary16 row that is only 4-byte aligned: pairs of elements
             T *d16 = s16 + r * SW + q * V;
 #pragma unroll
@@ -219,26 +260,20 @@ __device__ __forceinline__ void stage_finish(float *__restrict__ s, const T *__r
     __syncthreads();
 }
 
-// Stage s[r][c] = in[map(y0 + r)][map(x0 + c)] for r < SH, c < SW (as FP32),
-// map = the border mode (clamp-to-edge by default; zero mode stages zeros).
-// x0 is a multiple of VEC, SW a multiple of VEC.  vec_ok: rows are 16-byte
-// aligned (w % VEC == 0 and the plane base is 16-byte aligned).  Everything
-// goes through cp.async (all of a CTA's copies in flight at once): 16-byte
-// chunks inside aligned rows; otherwise 4-byte copies per element from the
-// clamped column (FP32) or per pair (binary16 rows that are 4-byte aligned);
-// only binary16 chunks that are neither use clamped scalar loads.
-// FP32 chunks land in s directly; binary16 chunks land in the staging area
-// `s16` and are widened into s afterwards.  Ends with a barrier.
-template <typename T, int SH, int SW, int NT, bool ANYB = false>
+// stage_issue followed by stage_finish: the staged tile in s (as FP32), ready
+// after the closing barrier.
+template <typename T, int SH, int SW, int NT, bool ANYB = false, bool ADAPT = true>
 __device__ __forceinline__ void stage_tile(const T *__restrict__ src, int h, int w, int y0, int x0,
                                            bool vec_ok, float *__restrict__ s, T *__restrict__ s16,
                                            int border = 0) {
-    stage_issue<T, SH, SW, NT, ANYB>(src, h, w, y0, x0, vec_ok, s, s16, border);
+    stage_issue<T, SH, SW, NT, ANYB, ADAPT>(src, h, w, y0, x0, vec_ok, s, s16, border);
     stage_finish<T, SH, SW, NT>(s, s16);
 }
 
-// Write a thread's R x 4 block (rows y, cols x..x+3), bounds-checked.
-template <typename T, int R>
+// Write a thread's R x 4 block (rows y, cols x..x+3), bounds-checked.  Rows
+// that are not 16-byte aligned: the widest stores each address allows
+// (ADAPT), or scalar stores.
+template <typename T, int R, bool ADAPT = true>
 __device__ __forceinline__ void store_block(T *__restrict__ dst, int h, int w, int y, int x,
                                             bool vec_ok, const float (&acc)[R][4]) {
 #pragma unroll
@@ -248,6 +283,8 @@ __device__ __forceinline__ void store_block(T *__restrict__ dst, int h, int w, i
         T *row = dst + (size_t)i * (size_t)w;
         if (vec_ok && x + 4 <= w) {
             Io<T>::st4(row + x, acc[o]);
+        } else if (ADAPT && x + 4 <= w) {
+            Io<T>::st4_any(row + x, acc[o]);
         } else {
 #pragma unroll
             for (int c = 0; c < 4; ++c)
@@ -365,7 +402,7 @@ __device__ __forceinline__ void direct_accumulate(const S *__restrict__ srow_,
 // Compute and store one TH x TW output tile with origin (y0, x0) from a
 // staged tile s_in (see stage_tile; FP32, or the binary16 staging area read
 // directly) and staged filter rows s_k.
-template <typename T, int KH, int KW, int TX, int TY, int R, int G, typename S = float>
+template <typename T, int KH, int KW, int TX, int TY, int R, int G, typename S = float, bool ADAPT = true>
 __device__ __forceinline__ void direct_compute(const S *__restrict__ s_in,
                                                const float *__restrict__ s_k, T *__restrict__ dst,
                                                int h, int w, bool vec_ok, int y0, int x0) {
@@ -383,7 +420,7 @@ __device__ __forceinline__ void direct_compute(const S *__restrict__ s_in,
         for (int o = 0; o < R; ++o)
 #pragma unroll
             for (int c = 0; c < 4; ++c) blk[o][c] = acc[o][g * 4 + c];
-        store_block<T, R>(dst, h, w, y0 + ty * R, x0 + g * GS + tx * C, vec_ok, blk);
+        store_block<T, R, ADAPT>(dst, h, w, y0 + ty * R, x0 + g * GS + tx * C, vec_ok, blk);
     }
 }
 
@@ -415,7 +452,8 @@ __device__ __forceinline__ void stage_filter(const float *__restrict__ k, float 
 // for HALFW.  HALFW (binary16 images): the tile stays binary16 in shared
 // memory and is widened as the windows are read -- half the shared-memory
 // traffic of an FP32 copy, for sides where that traffic is the limit.
-template <typename T, int KH, int KW, int TX, int TY, int R, int G, bool ANYB = false, bool HALFW = false>
+template <typename T, int KH, int KW, int TX, int TY, int R, int G, bool ANYB = false, bool HALFW = false,
+          bool ADAPT = true>
 __device__ __forceinline__ void direct_tile(const T *__restrict__ src, const float *__restrict__ k,
                                             T *__restrict__ dst, int h, int w, bool vec_ok, int y0,
                                             int x0, float *__restrict__ smem, int border = 0) {
@@ -426,17 +464,17 @@ __device__ __forceinline__ void direct_tile(const T *__restrict__ src, const flo
         float *s_k = smem;
         T *s16 = reinterpret_cast<T *>(smem + KH * KWP);
         stage_filter<KH, KW, KWP, Cfg::NT>(k, s_k);
-        stage_issue<T, SH, SW, Cfg::NT, ANYB>(src, h, w, y0 - AH, x0 - P, vec_ok, nullptr, s16, border);
+        stage_issue<T, SH, SW, Cfg::NT, ANYB, ADAPT>(src, h, w, y0 - AH, x0 - P, vec_ok, nullptr, s16, border);
         cp_async_wait_all();
         __syncthreads();
-        direct_compute<T, KH, KW, TX, TY, R, G, T>(s16, s_k, dst, h, w, vec_ok, y0, x0);
+        direct_compute<T, KH, KW, TX, TY, R, G, T, ADAPT>(s16, s_k, dst, h, w, vec_ok, y0, x0);
     } else {
         float *s_in = smem;
         float *s_k = smem + SH * SW;
         T *s16 = reinterpret_cast<T *>(smem + SH * SW + KH * KWP);
         stage_filter<KH, KW, KWP, Cfg::NT>(k, s_k);
-        stage_tile<T, SH, SW, Cfg::NT, ANYB>(src, h, w, y0 - AH, x0 - P, vec_ok, s_in, s16, border);
-        direct_compute<T, KH, KW, TX, TY, R, G>(s_in, s_k, dst, h, w, vec_ok, y0, x0);
+        stage_tile<T, SH, SW, Cfg::NT, ANYB, ADAPT>(src, h, w, y0 - AH, x0 - P, vec_ok, s_in, s16, border);
+        direct_compute<T, KH, KW, TX, TY, R, G, float, ADAPT>(s_in, s_k, dst, h, w, vec_ok, y0, x0);
     }
 }
 
