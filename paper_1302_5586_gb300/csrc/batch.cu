@@ -12,8 +12,9 @@
 // pencil_conv2d_ex on that image alone.  One kernel per side keeps each
 // kernel's code small (one tile body, two tile heights) and gives it its own
 // register budget and shared-memory slot size, so small filters run more CTAs
-// per SM.  FP32 kernels have two staging slots: the copies of a CTA's next
-// tile run while the current one is computed.  Kernels read the tile counts
+// per SM.  Each side has one or two staging slots (two: the copies of a
+// CTA's next tile run while the current one is computed), chosen per side by
+// measurement, as is its CTA count per SM.  Kernels read the tile counts
 // from the device headers, so the graph captured for a set of sides serves
 // every batch with that set.
 #include <algorithm>
@@ -79,25 +80,24 @@ struct Slot {
         return bhalfw(K, esz) ? KF + IN / 2 : KF + IN + (esz == 2 ? IN / 2 : 0);
     }
 };
-// Two staging slots (the next tile's copies overlap the current compute),
-// except for binary16 tiles widened into an FP32 copy, whose slots are larger.
+// Staging slots and CTAs per SM (the register budget) per side, from sweeps
+// on GB300 over the 512-image benchmark batch.  Two slots let a CTA's next
+// tile copy while it computes the current one; where one slot wins, more
+// resident CTAs hide the copies better than the prefetch does.
+constexpr int kNslot[2][kSides] = {{2, 1, 1, 1, 1, 1, 2, 1},   // FP32, sides 1, 3, ..., 15
+                                   {2, 2, 1, 1, 1, 1, 1, 1}};  // binary16
+constexpr int kRegCap[2][kSides] = {{8, 8, 8, 8, 5, 4, 4, 4}, {8, 8, 8, 8, 6, 4, 4, 4}};
 template <int K>
-constexpr int nslot(size_t esz) { return esz == 2 && !bhalfw(K, esz) ? 1 : 2; }
+constexpr int nslot(size_t esz) { return kNslot[esz == 2][K / 2]; }
 template <int K>
 constexpr size_t batch_smem(size_t esz) {
     return nslot<K>(esz) * sizeof(float) * (size_t)Slot<K>::floats((int)esz);
 }
-// CTAs per SM the register budget is sized for: as many as the shared memory
-// allows, except where the tile body would spill at that budget (side 7,
-// binary16 sides 3 and 5 with their two slots, binary16 sides 11 and up).
-constexpr int batch_reg_cap(int k, size_t esz) {
-    if (k == 7) return 4;
-    if (esz == 2) return k >= 11 ? 4 : (k == 3 ? 6 : (k == 5 ? 5 : 8));
-    return 8;
-}
+// CTAs per SM the register budget is sized for: the table's, or fewer where
+// the shared memory holds fewer.
 template <int K>
 constexpr int batch_minb(size_t esz) {
-    return std::min<int>(batch_reg_cap(K, esz),
+    return std::min<int>(kRegCap[esz == 2][K / 2],
                          std::max<int>(1, (int)((228 * 1024) / (batch_smem<K>(esz) + 1024))));
 }
 

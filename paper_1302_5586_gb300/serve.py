@@ -126,6 +126,21 @@ class Server:
         self.plans = [b.pencil_batch_create(dtype, max_wave, max_tiles) for _ in range(streams)]
         self.max_wave = max_wave
         self.max_inflight = max_inflight
+        self.warm_up()
+
+    def warm_up(self):
+        """Before serving: load every filter side's kernels (batched and
+        standalone) and build each plan's one-side launch graphs, on a tiny
+        image, so the first requests do not pay those one-time costs."""
+        torch = self.torch
+        img = torch.zeros((16, 16), dtype=self.tdtype, device=self.dev)
+        out = torch.empty_like(img)
+        k = torch.zeros(15 * 15, dtype=torch.float32, device=self.dev)
+        for s, plan in zip(self.streams, self.plans):
+            for ks in range(1, 16, 2):
+                b.pencil_batch_run(plan, b.make_images([(img, out, k, 16, 16, ks)]), s.cuda_stream)
+                b.pencil_conv2d_ex(1, 16, 16, img, ks, ks, k, out, self.dtype, 0, s.cuda_stream)
+        torch.cuda.synchronize(self.dev)
 
     def close(self):
         self.torch.cuda.synchronize(self.dev)
