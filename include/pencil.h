@@ -373,6 +373,22 @@ int pencil_version(void);
 /* The cudaError_t of the calling thread's most recent PENCIL_ERR_CUDA, or 0. */
 int pencil_last_cuda_error(void);
 
+/* Status of the device-side waits since the last call: PENCIL_ERR_TIMEOUT if
+ * any kernel gave up a bounded wait (a tile load whose completion did not
+ * arrive within its limit of about a second; that tile's outputs were not
+ * written), else PENCIL_OK.  Clears the count.  Stream-ordered calls report
+ * their waits here, so call it after synchronising the streams that ran
+ * them.  The library's kernels never wait without a limit.  Errors: CUDA. */
+int pencil_device_status(void);
+
+/* Self-test of the bounded wait: one CTA waits up to limit_us microseconds
+ * (1 .. 1000000) on an mbarrier that no copy completes.  *completed = 0 when
+ * the wait ran out as it must (it is then counted, so pencil_device_status
+ * reports PENCIL_ERR_TIMEOUT once), 1 if it completed.  Synchronous.
+ * Errors: NULL, ARG, CUDA.  (The paper has no counterpart: this checks the
+ * library's own failure path without faulting or hanging the GPU.) */
+int pencil_selftest_wait_timeout(unsigned limit_us, int *completed);
+
 /* Release the library's device pools (plain calls' scratch, the temporaries
  * of pencil_conv2d_chain).  Call when no library work is in flight.  Safe to
  * call more than once; later calls allocate again. */

@@ -28,6 +28,8 @@ def PENCIL_BORDER(m):
     return m << 8
 PENCIL_MAX_SPECIALISED_K = 15
 
+PENCIL_OK = 0
+PENCIL_ERR_TIMEOUT = -7
 STATUS = {
     0: "PENCIL_OK", -1: "PENCIL_ERR_ARG", -2: "PENCIL_ERR_NULL", -3: "PENCIL_ERR_ALIAS",
     -4: "PENCIL_ERR_PTR", -5: "PENCIL_ERR_NOMEM", -6: "PENCIL_ERR_CUDA",
@@ -101,6 +103,8 @@ def lib():
         "pencil_strerror": (ctypes.c_char_p, [i]),
         "pencil_version": (i, []),
         "pencil_last_cuda_error": (i, []),
+        "pencil_device_status": (i, []),
+        "pencil_selftest_wait_timeout": (i, [ctypes.c_uint, ctypes.POINTER(i)]),
         "pencil_shutdown": (None, []),
     }
     for name, (res, args) in sig.items():
@@ -330,6 +334,22 @@ def pencil_strerror(status: int) -> str:
 
 def pencil_version() -> int:
     return lib().pencil_version()
+
+
+def pencil_device_status() -> int:
+    """PENCIL_OK, or -7 (PENCIL_ERR_TIMEOUT) if a device-side wait ran out
+    since the last call (returned, not raised: it is a status report)."""
+    st = lib().pencil_device_status()
+    if st not in (0, -7):
+        _check(st, "pencil_device_status")
+    return st
+
+
+def pencil_selftest_wait_timeout(limit_us: int) -> int:
+    """1 if the self-test's never-completing wait completed, 0 if it ran out."""
+    done = ctypes.c_int(-1)
+    _check(lib().pencil_selftest_wait_timeout(limit_us, ctypes.byref(done)), "pencil_selftest_wait_timeout")
+    return done.value
 
 
 def pencil_last_cuda_error() -> int:

@@ -217,6 +217,20 @@ int pencil_device_info(char *name, int len, int *sm_count, int *driver_version) 
 
 int pencil_last_cuda_error(void) { return g_last_cuda; }
 
+int pencil_device_status(void) {
+    unsigned n = 0;
+    cudaError_t e = wait_timeouts(&n, true);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return n ? PENCIL_ERR_TIMEOUT : PENCIL_OK;
+}
+
+int pencil_selftest_wait_timeout(unsigned limit_us, int *completed) {
+    if (!completed) return PENCIL_ERR_NULL;
+    if (limit_us == 0 || limit_us > 1000000) return PENCIL_ERR_ARG;
+    cudaError_t e = wait_selftest((uint64_t)limit_us * 1000ull, completed);
+    return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
+}
+
 void pencil_shutdown(void) {
     std::lock_guard<std::mutex> lk(pool().mu);
     pool().release();

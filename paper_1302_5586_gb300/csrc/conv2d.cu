@@ -8,19 +8,26 @@
 // generic and batched kernels return identical bits for the same pixel.
 //
 // Design (one GPU, HBM-streaming):
-//   * a CTA owns a TH x TW output tile; it stages the clamped halo tile
-//     (TH+kh-1) x (TW+2P) in shared memory as FP32 with 16-byte vector loads
-//     (float4 for FP32, 8 x binary16 for FP16), clamping rows per row and
-//     columns only in the chunks that cross an edge;
+//   * a CTA owns a TH x TW output tile and stages its halo tile
+//     (TH+kh-1) x (TW+2P) in shared memory.  Images whose rows are 16-byte
+//     aligned (clamp or zero border) are staged by the tensor memory
+//     accelerator: one cp.async.bulk.tensor box per CTA, completion on an
+//     mbarrier with a bounded wait, the clamp rebuilt in shared memory on
+//     edge tiles.  Other images use cp.async copies (16 bytes where the
+//     address allows), clamping rows per row and columns only in the chunks
+//     that cross an edge;
 //   * each thread computes R rows x C=4 columns in registers; for every
 //     staged input row it loads its (C+kw-1)-wide window once (LDS.128) and
 //     applies it to every output row that uses it (register blocking along
 //     rows), with the filter row fetched by a broadcast LDS.128;
 //   * the output is written with one 16-byte (FP32) or 8-byte (FP16) store per
 //     thread and row.
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 
 #include "conv_tile.cuh"
+#include "tma.cuh"
 
 namespace pencil {
 namespace {
@@ -47,6 +54,104 @@ __global__ void __launch_bounds__(TX *TY, MINB)
     const bool vok = VMODE == 0 ? vec_ok : VMODE == 1;
     direct_tile<T, KH, KW, TX, TY, R, G, ANYB, HALFW, VMODE == 2>(in + plane, k, out + plane, h, w, vok,
                                                blockIdx.y * Cfg::TH, blockIdx.x * Cfg::TW, smem, border);
+}
+
+// ---------------------------------------------------------- TMA-staged kernel
+// Tile loads that did not complete within their bounded wait (each such CTA
+// skipped its tile); read and cleared by pencil_device_status.
+__device__ unsigned int g_wait_timeouts;
+
+// Clamp-to-edge on a staged tile that holds zeros outside the image (a TMA
+// load fills out-of-range elements with zeros): rows above or below the
+// image take the nearest edge row, then columns left or right of it the
+// nearest edge column, so corners get both clamps.  (gy0, gx0): global
+// position of t[0][0].  Block-uniform; ends with a barrier when it writes.
+template <typename S, int SH, int SW, int NT>
+__device__ __forceinline__ void clamp_fixup(S *__restrict__ t, int h, int w, int gy0, int gx0) {
+    const int top = -gy0, bot = h - gy0;  // staged rows [top, bot) are inside the image
+    if (top > 0 || bot < SH) {
+        for (int idx = threadIdx.x; idx < SH * SW; idx += NT) {
+            const int r = idx / SW, c = idx - r * SW;
+            const int src = r < top ? top : (r >= bot ? bot - 1 : r);
+            if (src != r) t[idx] = t[src * SW + c];
+        }
+        __syncthreads();
+    }
+    const int left = -gx0, right = w - gx0;  // staged columns [left, right) are inside
+    if (left > 0 || right < SW) {
+        for (int idx = threadIdx.x; idx < SH * SW; idx += NT) {
+            const int r = idx / SW, c = idx - r * SW;
+            const int src = c < left ? left : (c >= right ? right - 1 : c);
+            if (src != c) t[idx] = t[r * SW + src];
+        }
+        __syncthreads();
+    }
+}
+
+// The direct kernel with its halo tile loaded by the tensor memory
+// accelerator: one thread arms an mbarrier and issues a single
+// cp.async.bulk.tensor copy of the (TH+kh-1) x (TW+2P) box of plane
+// blockIdx.z (rows 16-byte aligned, which the tensor map requires); the other
+// threads stage the filter meanwhile.  Out-of-image elements arrive as zeros:
+// the zero border as it is, clamp-to-edge after clamp_fixup.  The compute is
+// the shared tile body, so the bits are those of the cp.async kernel.
+// Shared memory: the staged tile (type T, first, 128-byte aligned), the FP32
+// copy of a binary16 tile unless HALFW, the filter rows.
+template <typename T, int KH, int KW, int TX, int TY, int R, int G, int MINB, bool HALFW, bool CLAMP>
+__global__ void __launch_bounds__(TX *TY, MINB)
+    conv2d_direct_tma_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ k,
+                             T *__restrict__ out, int h, int w) {
+    using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
+    constexpr int SW = Cfg::SW, SH = Cfg::SH, KWP = Cfg::KWP, NT = Cfg::NT;
+    constexpr bool F16 = sizeof(T) == 2;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t bar;
+    T *s_t = reinterpret_cast<T *>(smem);                                           // the TMA box
+    float *s_in = F16 ? reinterpret_cast<float *>(s_t + SH * SW) : smem;            // FP32 tile
+    float *s_k = F16 && HALFW ? s_in : s_in + SH * SW;                              // filter rows
+    const int y0 = blockIdx.y * Cfg::TH, x0 = blockIdx.x * Cfg::TW;
+    const int gy0 = y0 - Cfg::AH, gx0 = x0 - Cfg::P;
+    if ((tma::smem_addr(s_t) & 127u) != 0) {  // a TMA box needs a 128-byte aligned destination
+        if (threadIdx.x == 0) atomicAdd(&g_wait_timeouts, 1u);
+        return;
+    }
+
+    if (threadIdx.x == 0) tma::mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tma::mbar_arrive_expect_tx(&bar, (unsigned)(sizeof(T) * SH * SW));
+        tma::load_3d(s_t, &tmap, gx0, gy0, (int)blockIdx.z, &bar);
+    }
+    stage_filter<KH, KW, KWP, NT>(k, s_k);
+    const bool ok = __syncthreads_and(tma::mbar_wait(&bar, 0, tma::kLoadWaitNs));
+    if (!ok) {  // the copy did not complete in time: report, let it land, skip the tile
+        if (threadIdx.x == 0) atomicAdd(&g_wait_timeouts, 1u);
+        tma::mbar_wait(&bar, 0, tma::kLoadWaitNs);
+        return;
+    }
+    if (CLAMP) clamp_fixup<T, SH, SW, NT>(s_t, h, w, gy0, gx0);
+    T *dst = out + (size_t)h * (size_t)w * blockIdx.z;
+    if constexpr (F16 && HALFW) {
+        direct_compute<T, KH, KW, TX, TY, R, G, T, false>(s_t, s_k, dst, h, w, true, y0, x0);
+    } else {
+        stage_widen<T, SH, SW, NT>(s_in, s_t);
+        direct_compute<T, KH, KW, TX, TY, R, G, float, false>(s_in, s_k, dst, h, w, true, y0, x0);
+    }
+}
+
+// The bounded wait on its own: an mbarrier that expects 16 bytes no copy
+// delivers, waited on for limit_ns; a wait that runs out is counted like a
+// tile load's.  result: 1 if the wait completed, 0 if it ran out.
+__global__ void wait_selftest_kernel(uint64_t limit_ns, int *result) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) tma::mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) tma::mbar_arrive_expect_tx(&bar, 16u);
+    const bool ok = __syncthreads_and(tma::mbar_wait(&bar, 0, limit_ns));
+    if (threadIdx.x == 0) {
+        if (!ok) atomicAdd(&g_wait_timeouts, 1u);
+        *result = ok ? 1 : 0;
+    }
 }
 
 // ------------------------------------------------------------ generic kernel
@@ -287,10 +392,56 @@ cudaError_t set_smem(Kern kern, size_t bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// cuTensorMapEncodeTiled from the driver (no link-time dependency on it),
+// or null where the driver does not offer it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// Tensor map of a [c][h][w] image with rows 16-byte aligned, box (bw, bh, 1);
+// false if it cannot be made (the caller then stages with cp.async).
+template <typename T>
+bool image_tensor_map(CUtensorMap *m, const T *base, int c, int h, int w, int bw, int bh) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)c};
+    const cuuint64_t strides[2] = {(cuuint64_t)w * sizeof(T), (cuuint64_t)h * (cuuint64_t)w * sizeof(T)};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1u};
+    const cuuint32_t elem[3] = {1u, 1u, 1u};
+    return enc(m, sizeof(T) == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+               const_cast<T *>(base), dims, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <typename T, int K, int TX, int TY, int R, int G = 1, int MINB = 1, bool HALFW = false>
 cudaError_t run_direct(int c, int h, int w, const T *in, const float *k, T *out, bool vec_ok,
                        int border, cudaStream_t s) {
     using Cfg = DirectCfg<K, K, TX, TY, R, G>;
+    // Aligned rows with the clamp or zero border: TMA staging (a box side is
+    // at most 256 elements; wider tiles keep cp.async).
+    if constexpr (Cfg::SW <= 256 && Cfg::SH <= 256) {
+        CUtensorMap tmap;
+        if (vec_ok && (border == 0 || border == 1) && image_tensor_map<T>(&tmap, in, c, h, w, Cfg::SW, Cfg::SH)) {
+            auto kern = border == 0 ? conv2d_direct_tma_kernel<T, K, K, TX, TY, R, G, MINB, HALFW, true>
+                                    : conv2d_direct_tma_kernel<T, K, K, TX, TY, R, G, MINB, HALFW, false>;
+            const size_t smem = HALFW ? Cfg::smem_half : Cfg::smem(sizeof(T));
+            cudaError_t e = set_smem(kern, smem);
+            if (e != cudaSuccess) return e;
+            dim3 grid((w + Cfg::TW - 1) / Cfg::TW, (h + Cfg::TH - 1) / Cfg::TH, c);
+            kern<<<grid, Cfg::NT, smem, s>>>(tmap, k, out, h, w);
+            return cudaGetLastError();
+        }
+    }
     // sides up to 5 (memory-bound): an aligned-row kernel and an adaptive
     // any-row kernel; larger sides: one kernel with vec_ok at run time
     using Kern = decltype(&conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 0>);
@@ -405,6 +556,30 @@ cudaError_t run_sep_any(int c, int h, int w, const T *in, int kx, const float *g
     conv2d_sep_generic_kernel<T><<<grid, 256, smem, s>>>(in, gx, gy, out, h, w, kx, ky, border);
     return cudaGetLastError();
 }
+
+}  // namespace
+
+cudaError_t wait_selftest(uint64_t limit_ns, int *completed) {
+    int *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(int));
+    if (e != cudaSuccess) return e;
+    wait_selftest_kernel<<<1, 64>>>(limit_ns, d);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(completed, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e;
+}
+
+cudaError_t wait_timeouts(unsigned *n, bool clear) {
+    cudaError_t e = cudaMemcpyFromSymbol(n, g_wait_timeouts, sizeof(unsigned));
+    if (e == cudaSuccess && clear && *n) {
+        const unsigned zero = 0;
+        e = cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof(unsigned));
+    }
+    return e;
+}
+
+namespace {
 
 bool rows_aligned(const void *p, int w, int vec) {
     return (w % vec == 0) && ((uintptr_t)p % 16 == 0);

@@ -57,6 +57,13 @@ cudaError_t launch_conv2d_sep(int dtype, int c, int h, int w, const void *in, in
                               const float *gx, int ky, const float *gy, void *out,
                               cudaStream_t s, int border = 0);
 
+// Tile loads whose bounded wait ran out since the last clear (each skipped its
+// tile); clear resets the count.
+cudaError_t wait_timeouts(unsigned *n, bool clear);
+// Run the bounded mbarrier wait against a barrier that never completes, for
+// limit_ns; *completed = 1 if it completed (it should not), 0 if it ran out.
+cudaError_t wait_selftest(uint64_t limit_ns, int *completed);
+
 // out = conv(conv(in, k1), k2) in one kernel, clamp-to-edge, the intermediate
 // rounded to the storage type; generic forces the runtime-size kernel.
 cudaError_t launch_conv2d_chain(int dtype, int c, int h, int w, const void *in, int kh1, int kw1,
