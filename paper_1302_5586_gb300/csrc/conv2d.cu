@@ -203,33 +203,60 @@ struct SepCfg {
     static constexpr int NX = round_up(P - AX - M0 + C + KX - 1, 4);
     // in place: the row-pass results overwrite the staged tile (row stride SW)
     static constexpr size_t smem_f32 = sizeof(float) * (size_t)(SH * SW + (INPLACE ? 0 : SH * TW));
-    static constexpr size_t smem(size_t esz) { return smem_f32 + (esz == 2 ? 2 * (size_t)SH * SW : 0); }
+    // the binary16 staging area follows, 128-byte aligned (a TMA box destination)
+    static constexpr size_t off16 = (smem_f32 + 127) / 128 * 128;
+    static constexpr size_t smem(size_t esz) { return esz == 2 ? off16 + 2 * (size_t)SH * SW : smem_f32; }
 };
 
+// VMODE 0-2 as for the direct kernel (cp.async staging); 3: rows 16-byte
+// aligned, clamp (border 0) or zero (border 1) border, the halo tile loaded
+// as one TMA box of `tmap` (unused by the other modes), as the direct TMA
+// kernel does.
 template <typename T, int KX, int KY, int TX, int TY, int R, int MINB, bool INPLACE, bool ANYB, int PAIR,
           int VMODE>
 __global__ void __launch_bounds__(TX *TY, MINB)
-    conv2d_sep_kernel(const T *__restrict__ in, const float *__restrict__ gx,
-                      const float *__restrict__ gy, T *__restrict__ out, int h, int w, bool vec_ok_,
-                      int border) {
-    // VMODE as for the direct kernel
-    constexpr bool ADAPT = VMODE == 2;
-    const bool vec_ok = VMODE == 0 ? vec_ok_ : VMODE == 1;
+    conv2d_sep_kernel(const __grid_constant__ CUtensorMap tmap, const T *__restrict__ in,
+                      const float *__restrict__ gx, const float *__restrict__ gy, T *__restrict__ out, int h,
+                      int w, bool vec_ok_, int border) {
+    constexpr bool ADAPT = VMODE == 2, TMA = VMODE == 3;
+    const bool vec_ok = VMODE == 0 ? vec_ok_ : VMODE != 2;
     using Cfg = SepCfg<KX, KY, TX, TY, R, INPLACE>;
     constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, SH = Cfg::SH, TW = Cfg::TW,
                   NX = Cfg::NX, AX = Cfg::AX, AY = Cfg::AY, NT = Cfg::NT;
     constexpr int TS = INPLACE ? SW : TW;  // row stride of the row-pass results
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
     float *s_in = smem;
     float *s_t = INPLACE ? smem : smem + SH * SW;
-    T *s16 = reinterpret_cast<T *>(smem + Cfg::smem_f32 / sizeof(float));
+    T *s16 = reinterpret_cast<T *>(smem + Cfg::off16 / sizeof(float));
 
     const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
     const T *src = in + plane;
     T *dst = out + plane;
     const int x0 = blockIdx.x * TW;
     const int y0 = blockIdx.y * Cfg::TH;
-    stage_tile<T, SH, SW, NT, ANYB, ADAPT>(src, h, w, y0 - AY, x0 - P, vec_ok, s_in, s16, border);
+    if constexpr (TMA) {
+        __shared__ __align__(8) uint64_t bar;
+        T *s_box = sizeof(T) == 2 ? s16 : reinterpret_cast<T *>(s_in);
+        if ((tma::smem_addr(s_box) & 127u) != 0) {  // a TMA box needs a 128-byte aligned destination
+            if (threadIdx.x == 0) atomicAdd(&g_wait_timeouts, 1u);
+            return;
+        }
+        if (threadIdx.x == 0) tma::mbar_init(&bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tma::mbar_arrive_expect_tx(&bar, (unsigned)(sizeof(T) * SH * SW));
+            tma::load_3d(s_box, &tmap, x0 - P, y0 - AY, (int)blockIdx.z, &bar);
+        }
+        if (!__syncthreads_and(tma::mbar_wait(&bar, 0, tma::kLoadWaitNs))) {
+            if (threadIdx.x == 0) atomicAdd(&g_wait_timeouts, 1u);
+            tma::mbar_wait(&bar, 0, tma::kLoadWaitNs);
+            return;
+        }
+        if (border == 0) clamp_fixup<T, SH, SW, NT>(s_box, h, w, y0 - AY, x0 - P);
+        stage_widen<T, SH, SW, NT>(s_in, s16);
+    } else {
+        stage_tile<T, SH, SW, NT, ANYB, ADAPT>(src, h, w, y0 - AY, x0 - P, vec_ok, s_in, s16, border);
+    }
 
     // row pass: t[r][q*C + c] = sum_b gx[b] * in[r][q*C + c + b - AX]
     {
@@ -511,18 +538,23 @@ cudaError_t run_sep(int c, int h, int w, const T *in, const float *gx, const flo
     using Cfg = SepCfg<K, K, TX, TY, R, INPLACE>;
     using Kern = decltype(&conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 0>);
     Kern kern;
-    if constexpr (K <= 5)  // as for the direct kernels
+    CUtensorMap tmap = {};
+    static_assert(Cfg::SW <= 256 && Cfg::SH <= 256, "a TMA box side is at most 256 elements");
+    if (vec_ok && (border == 0 || border == 1) && image_tensor_map<T>(&tmap, in, c, h, w, Cfg::SW, Cfg::SH)) {
+        kern = conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 3>;  // TMA staging
+    } else if constexpr (K <= 5) {  // as for the direct kernels
         kern = border != 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 2>
                : vec_ok    ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 1>
                            : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 2>;
-    else
+    } else {
         kern = border != 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 0>
                            : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 0>;
+    }
     const size_t smem = Cfg::smem(sizeof(T));
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((w + Cfg::TW - 1) / Cfg::TW, (h + Cfg::TH - 1) / Cfg::TH, c);
-    kern<<<grid, Cfg::NT, smem, s>>>(in, gx, gy, out, h, w, vec_ok, border);
+    kern<<<grid, Cfg::NT, smem, s>>>(tmap, in, gx, gy, out, h, w, vec_ok, border);
     return cudaGetLastError();
 }
 

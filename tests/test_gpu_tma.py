@@ -81,3 +81,35 @@ def test_bounded_wait_runs_out_and_is_reported():
     a = conv(img, k, pg.PENCIL_F32, 0)
     b = conv(img, k, pg.PENCIL_F32, pg.PENCIL_CONV_GENERIC)
     np.testing.assert_array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+@pytest.mark.parametrize("dtype", [pg.PENCIL_F32, pg.PENCIL_F16])
+@pytest.mark.parametrize("border", ["clamp", "zero"])
+def test_tma_separable_matches_oracle(dtype, border):
+    """The separable kernels' TMA staging on the same edge shapes.  Clamp: the
+    separable oracle; zero: the 2-D oracle with the exact outer-product
+    weights, plus the rounding slack of those weights in FP32."""
+    flags = pg.PENCIL_BORDER(pg.BORDER_MODES[border])
+    tol = F16_TOL if dtype == pg.PENCIL_F16 else F32_TOL
+    for K in (3, 7, 9, 15):
+        gx = synth.gaussian_taps_f32(K // 2, 1.0 + K / 5)
+        gy = synth.filter_f32(950 + K, 1, K).ravel()
+        for shape in SHAPES:
+            c, h, w = shape
+            img = synth.image_f32(960 + K, c, h, w)
+            if dtype == pg.PENCIL_F16:
+                img = synth.to_f16(img)
+            d_in = to_dev(img)
+            d_out = torch.empty_like(d_in)
+            pg.pencil_conv2d_sep_ex(c, h, w, d_in, K, to_dev(gx), K, to_dev(gy), d_out, dtype, flags)
+            torch.cuda.synchronize()
+            out = d_out.cpu().numpy().astype(np.float64)
+            if border == "clamp":
+                ref, bound = oracle.conv2d_sep(img, gx, gy)
+                slack = 0.0
+            else:
+                k2 = np.outer(gy.astype(np.float64), gx.astype(np.float64))
+                ref, bound = oracle.conv2d(img, k2.astype(np.float32), border="zero")
+                slack = np.abs(k2 - k2.astype(np.float32).astype(np.float64)).sum() * np.abs(img.astype(np.float64)).max()
+            assert np.all(np.abs(out - ref) <= tol * bound + slack), f"K={K} shape={shape}"
+    assert pg.pencil_device_status() == pg.PENCIL_OK
