@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
     conv2d_direct_kernel(const T *__restrict__ in, const float *__restrict__ k, T *__restrict__ out,
                          int h, int w, bool vec_ok, int border) {
     using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
     const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
     const bool vok = VMODE == 0 ? vec_ok : VMODE == 1;
     direct_tile<T, KH, KW, TX, TY, R, G, ANYB, HALFW, VMODE == 2>(in + plane, k, out + plane, h, w, vok,
@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(256)
                               const float *__restrict__ gy, T *__restrict__ out, int h, int w,
                               int kx, int ky, int border) {
     // tile 32 x 32 outputs, 256 threads
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
     const int SH = 32 + ky - 1;
     float *s_t = smem;                  // SH x 32
     const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
@@ -471,7 +471,7 @@ cudaError_t run_direct(int c, int h, int w, const T *in, const float *k, T *out,
     }
     // sides up to 5 (memory-bound): an aligned-row kernel and an adaptive
     // any-row kernel; larger sides: one kernel with vec_ok at run time
-    using Kern = decltype(&conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 0>);
+    using Kern = void (*)(const T *, const float *, T *, int, int, bool, int);
     Kern kern;
     if constexpr (K <= 5)
         kern = border != 0 ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, true, HALFW, 2>
@@ -493,7 +493,9 @@ cudaError_t run_direct_k(int K, int c, int h, int w, const T *in, const float *k
                          bool vec_ok, int border, cudaStream_t s) {
     // Tile shapes and register caps per side, from timing sweeps on GB300 at
     // 8192 x 8192 x 3 (small sides: occupancy for HBM streaming; large sides:
-    // two column groups so each filter-row load feeds eight FMA chains).
+    // two column groups so each filter-row load feeds eight FMA chains).  All
+    // tiles are 128 columns wide, so the staged box (at most 144 columns)
+    // fits one TMA load.
     // Binary16 images up to side 7 keep the tile binary16 in shared memory
     // (HALFW): those kernels are bound by shared-memory traffic, which the
     // FP32 copy doubles; from side 9 the widening in the inner loop costs more
@@ -510,15 +512,15 @@ cudaError_t run_direct_k(int K, int c, int h, int w, const T *in, const float *k
         switch (K) {
             case 1: return run_direct<T, 1, 32, 8, 4, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
             case 3: return run_direct<T, 3, 32, 8, 4, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
-            case 5: return run_direct<T, 5, 32, 4, 4, 2, 6>(c, h, w, in, k, out, vec_ok, border, s);
+            case 5: return run_direct<T, 5, 32, 4, 8, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
             case 7: return run_direct<T, 7, 32, 4, 8, 1, 8>(c, h, w, in, k, out, vec_ok, border, s);
             default: break;
         }
     }
     switch (K) {
-        case 9: return run_direct<T, 9, 32, 4, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
-        case 11: return run_direct<T, 11, 32, 4, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
-        case 13: return run_direct<T, 13, 32, 4, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
+        case 9: return run_direct<T, 9, 16, 8, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
+        case 11: return run_direct<T, 11, 16, 8, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
+        case 13: return run_direct<T, 13, 16, 8, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
         case 15: return run_direct<T, 15, 16, 8, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
         default: return cudaErrorInvalidValue;
     }
@@ -536,7 +538,7 @@ template <typename T, int K, int TX, int TY, int R, int MINB = 1, bool INPLACE =
 cudaError_t run_sep(int c, int h, int w, const T *in, const float *gx, const float *gy, T *out,
                     bool vec_ok, int border, cudaStream_t s) {
     using Cfg = SepCfg<K, K, TX, TY, R, INPLACE>;
-    using Kern = decltype(&conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 0>);
+    using Kern = void (*)(const CUtensorMap, const T *, const float *, const float *, T *, int, int, bool, int);
     Kern kern;
     CUtensorMap tmap = {};
     static_assert(Cfg::SW <= 256 && Cfg::SH <= 256, "a TMA box side is at most 256 elements");
