@@ -70,7 +70,7 @@ def measured_peaks():
 
 
 KERNEL_SOURCES = ["paper_1302_5586_gb300/csrc/conv2d.cu", "paper_1302_5586_gb300/csrc/conv_tile.cuh",
-                  "paper_1302_5586_gb300/csrc/internal.cuh"]
+                  "paper_1302_5586_gb300/csrc/internal.cuh", "paper_1302_5586_gb300/csrc/tma.cuh"]
 
 
 def sources_sha(paths=KERNEL_SOURCES):
@@ -228,7 +228,8 @@ def run_ours(args, rank, world, local_rank):
     achieved = flops_15 / (k15_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
     traffic = traffic_record("conv2d_direct_f32_15x15_8192x8192x3")
-    roofline = {"bound": "alu", "kernel": "conv2d_direct_kernel<float,15,15,16,8,4,2,3>", "achieved": round(achieved, 3),
+    roofline = {"bound": "alu", "kernel": "conv2d_direct_tma_kernel<float,15,15,16,8,4,2,3,false,true>",
+                "achieved": round(achieved, 3),
                 "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "launch_ms": round(k15_ms, 4), "algorithmic_bytes": 8 * PX_PER_PASS, "traffic": traffic}
