@@ -139,11 +139,10 @@ int pencil_conv2d_sep_ex(int c, int h, int w, const void *in, int kx, const floa
  * bit-identical to two pencil_conv2d_ex calls through a temporary of the same
  * dtype: the intermediate is rounded to the storage type and the second
  * filter reads it clamped at the image edge.  Clamp-to-edge only.  Fusion
- * pays while the chain is bound by memory traffic: when both filters have
- * sides up to 5 the call runs the fused kernel (square odd sides 3 and 5 a
- * tiled one, other sides a generic one), otherwise two passes through a
- * temporary from a library-owned stream-ordered pool (kept for reuse until
- * pencil_shutdown) -- the same bits either way.
+ * pays while the chain is bound by memory traffic: for two 3x3 filters the
+ * call runs the fused kernel, otherwise two passes through a temporary from
+ * a library-owned stream-ordered pool (kept for reuse until pencil_shutdown)
+ * -- the same bits either way.
  * PENCIL_CHAIN_FUSED forces the fused kernel (tiled for square odd sides
  * 3, 5, 7), PENCIL_CONV_GENERIC the generic fused one.  Every array is device memory
  * (in, out: c*h*w elements of dtype; k1: kh1*kw1, k2: kh2*kw2 FP32).

