@@ -341,6 +341,7 @@ def measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g, serve_seconds=SE
         "hbm_frac_16B_per_point_sweep": round(16 * n * n * 100 / (ms * 1e-3) / 1e9 / hbm, 4),
         "residuals": [float(x) for x in res.cpu()]}
     del u0, u, ws
+    out["plain_512x512_5x5"] = measure_small(torch, pg, dev, stream)
     out["batched_512"] = measure_batched(torch, pg, dev, stream)
     out["op2_inc_2048x2048_cells"] = measure_op2(torch, pg, dev, stream)
     out["chain_8192x8192x3"] = measure_chain(torch, pg, dev, stream, d_img, d_out)
@@ -429,6 +430,60 @@ def measure_op2(torch, pg, dev, stream):
     finally:
         pg.pencil_op2_plan_destroy(plan)
     return res
+
+
+def measure_small(torch, pg, dev, stream):
+    """The small plain case: one 512 x 512 FP32 image, 5 x 5 normalised
+    filter (1 MiB in, 1 MiB out: resident in the 129 MB L2, so launch latency
+    and L2 bandwidth bound it, not HBM).  Device time per launch (events
+    around 200 back-to-back launches, median of 5) and host wall time of the
+    synchronous plain call on device pointers."""
+    n, K = 512, 5
+    x = torch.from_numpy(synth.image_f32(synth.SEEDS["conv512"], 1, n, n)).to(dev)
+    k = torch.from_numpy(synth.filter_f32(synth.SEEDS["conv512"] + 1, K, K)).to(dev)
+    y = torch.empty_like(x)
+    sraw = stream.cuda_stream
+    reps = []
+    for _ in range(5):
+        reps.append(_time_stream(torch, stream, lambda: pg.pencil_conv2d_ex(1, n, n, x, K, K, k, y, pg.PENCIL_F32,
+                                                                            0, sraw), 200))
+    us = statistics.median(reps) * 1e3
+    # the same 200 launches captured once and replayed from a CUDA graph: the
+    # device time per launch without the host's per-call cost
+    graph_us = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(dev)
+        cap.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.graph(g, stream=cap):
+            for _ in range(200):
+                pg.pencil_conv2d_ex(1, n, n, x, K, K, k, y, pg.PENCIL_F32, 0, cap.cuda_stream)
+        greps = []
+        with torch.cuda.stream(stream):  # replay and events on the same stream
+            g.replay()
+            for _ in range(5):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                g.replay()
+                b.record(stream)
+                b.synchronize()
+                greps.append(a.elapsed_time(b) / 200 * 1e3)
+        graph_us = statistics.median(greps)
+    except RuntimeError as e:  # capture not possible here: report the stream-launched number only
+        graph_us = f"not captured: {e}"
+    for _ in range(20):
+        pg.pencil_conv2d(n, n, x, K, K, k, y)
+    t = time.perf_counter()
+    for _ in range(500):
+        pg.pencil_conv2d(n, n, x, K, K, k, y)
+    call_us = (time.perf_counter() - t) / 500 * 1e6
+    px = n * n
+    best = graph_us if isinstance(graph_us, float) else us
+    return {"device_us_per_launch": round(best, 2), "gpx_s": round(px / best / 1e3, 2),
+            "l2_resident_gb_s": round(8 * px / best / 1e3, 1), "graph_replay_us": graph_us if not isinstance(
+                graph_us, float) else round(graph_us, 2), "stream_launch_us": round(us, 2),
+            "plain_call_us": round(call_us, 2),
+            "note": "fits in L2: launch-latency bound; GB/s is L2-resident, not HBM"}
 
 
 def measure_batched(torch, pg, dev, stream):

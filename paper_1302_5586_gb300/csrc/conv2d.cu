@@ -450,25 +450,35 @@ bool image_tensor_map(CUtensorMap *m, const T *base, int c, int h, int w, int bw
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The TMA-staged launch for aligned rows with the clamp or zero border (a box
+// side is at most 256 elements); false, with nothing launched, where it does
+// not apply.
+template <typename T, int K, int TX, int TY, int R, int G, int MINB, bool HALFW>
+bool try_direct_tma(int c, int h, int w, const T *in, const float *k, T *out, bool vec_ok, int border,
+                    cudaStream_t s, cudaError_t *err) {
+    using Cfg = DirectCfg<K, K, TX, TY, R, G>;
+    static_assert(Cfg::SW <= 256 && Cfg::SH <= 256, "a TMA box side is at most 256 elements");
+    CUtensorMap tmap;
+    if (!vec_ok || (border != 0 && border != 1) || !image_tensor_map<T>(&tmap, in, c, h, w, Cfg::SW, Cfg::SH))
+        return false;
+    auto kern = border == 0 ? conv2d_direct_tma_kernel<T, K, K, TX, TY, R, G, MINB, HALFW, true>
+                            : conv2d_direct_tma_kernel<T, K, K, TX, TY, R, G, MINB, HALFW, false>;
+    const size_t smem = HALFW ? Cfg::smem_half : Cfg::smem(sizeof(T));
+    *err = set_smem(kern, smem);
+    if (*err == cudaSuccess) {
+        dim3 grid((w + Cfg::TW - 1) / Cfg::TW, (h + Cfg::TH - 1) / Cfg::TH, c);
+        kern<<<grid, Cfg::NT, smem, s>>>(tmap, k, out, h, w);
+        *err = cudaGetLastError();
+    }
+    return true;
+}
+
 template <typename T, int K, int TX, int TY, int R, int G = 1, int MINB = 1, bool HALFW = false>
 cudaError_t run_direct(int c, int h, int w, const T *in, const float *k, T *out, bool vec_ok,
                        int border, cudaStream_t s) {
     using Cfg = DirectCfg<K, K, TX, TY, R, G>;
-    // Aligned rows with the clamp or zero border: TMA staging (a box side is
-    // at most 256 elements; wider tiles keep cp.async).
-    if constexpr (Cfg::SW <= 256 && Cfg::SH <= 256) {
-        CUtensorMap tmap;
-        if (vec_ok && (border == 0 || border == 1) && image_tensor_map<T>(&tmap, in, c, h, w, Cfg::SW, Cfg::SH)) {
-            auto kern = border == 0 ? conv2d_direct_tma_kernel<T, K, K, TX, TY, R, G, MINB, HALFW, true>
-                                    : conv2d_direct_tma_kernel<T, K, K, TX, TY, R, G, MINB, HALFW, false>;
-            const size_t smem = HALFW ? Cfg::smem_half : Cfg::smem(sizeof(T));
-            cudaError_t e = set_smem(kern, smem);
-            if (e != cudaSuccess) return e;
-            dim3 grid((w + Cfg::TW - 1) / Cfg::TW, (h + Cfg::TH - 1) / Cfg::TH, c);
-            kern<<<grid, Cfg::NT, smem, s>>>(tmap, k, out, h, w);
-            return cudaGetLastError();
-        }
-    }
+    cudaError_t err = cudaSuccess;
+    if (try_direct_tma<T, K, TX, TY, R, G, MINB, HALFW>(c, h, w, in, k, out, vec_ok, border, s, &err)) return err;
     // sides up to 5 (memory-bound): an aligned-row kernel and an adaptive
     // any-row kernel; larger sides: one kernel with vec_ok at run time
     using Kern = void (*)(const T *, const float *, T *, int, int, bool, int);
@@ -488,9 +498,44 @@ cudaError_t run_direct(int c, int h, int w, const T *in, const float *k, T *out,
     return cudaGetLastError();
 }
 
+// SMs of the current device (cached per device).
+int sm_count() {
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cache[dev] && cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        cache[dev] = 152;
+    return cache[dev];
+}
+
+// Images with fewer 32 x 128 tiles than two per SM (a small image leaves most
+// SMs idle): 8-row tiles (sides up to 7) or 16-row tiles (larger sides), TMA
+// staging.  512 x 512 with a 5 x 5 filter: 5.3 -> 3.2 us on GB300.  False if
+// it does not apply (then the default tiling runs).
+template <typename T>
+bool try_direct_small(int K, int c, int h, int w, const T *in, const float *k, T *out, bool vec_ok, int border,
+                      cudaStream_t s, cudaError_t *err) {
+    const long long tiles = (long long)c * ((h + 31) / 32) * ((w + 127) / 128);
+    if (!vec_ok || tiles >= 2ll * sm_count()) return false;
+    constexpr bool HW = sizeof(T) == 2;  // binary16 tiles of sides up to 7 stay binary16
+    switch (K) {
+        case 1: return try_direct_tma<T, 1, 32, 8, 1, 1, 8, HW>(c, h, w, in, k, out, vec_ok, border, s, err);
+        case 3: return try_direct_tma<T, 3, 32, 8, 1, 1, 8, HW>(c, h, w, in, k, out, vec_ok, border, s, err);
+        case 5: return try_direct_tma<T, 5, 32, 8, 1, 1, 8, HW>(c, h, w, in, k, out, vec_ok, border, s, err);
+        case 7: return try_direct_tma<T, 7, 32, 8, 1, 1, 8, HW>(c, h, w, in, k, out, vec_ok, border, s, err);
+        case 9: return try_direct_tma<T, 9, 16, 8, 2, 2, 3, false>(c, h, w, in, k, out, vec_ok, border, s, err);
+        case 11: return try_direct_tma<T, 11, 16, 8, 2, 2, 3, false>(c, h, w, in, k, out, vec_ok, border, s, err);
+        case 13: return try_direct_tma<T, 13, 16, 8, 2, 2, 3, false>(c, h, w, in, k, out, vec_ok, border, s, err);
+        case 15: return try_direct_tma<T, 15, 16, 8, 2, 2, 3, false>(c, h, w, in, k, out, vec_ok, border, s, err);
+        default: return false;
+    }
+}
+
 template <typename T>
 cudaError_t run_direct_k(int K, int c, int h, int w, const T *in, const float *k, T *out,
                          bool vec_ok, int border, cudaStream_t s) {
+    cudaError_t err = cudaSuccess;
+    if (try_direct_small<T>(K, c, h, w, in, k, out, vec_ok, border, s, &err)) return err;
     // Tile shapes and register caps per side, from timing sweeps on GB300 at
     // 8192 x 8192 x 3 (small sides: occupancy for HBM streaming; large sides:
     // two column groups so each filter-row load feeds eight FMA chains).  All
