@@ -25,6 +25,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "conv_tile.cuh"
 #include "tma.cuh"
@@ -498,14 +499,17 @@ cudaError_t run_direct(int c, int h, int w, const T *in, const float *k, T *out,
     return cudaGetLastError();
 }
 
-// SMs of the current device (cached per device).
+// SMs of the current device (cached per device; 152 if the query fails).
 int sm_count() {
-    static int cache[64] = {};
+    static std::atomic<int> cache[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-    if (!cache[dev] && cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        cache[dev] = 152;
-    return cache[dev];
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n == 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        cache[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
 }
 
 // Images with fewer 32 x 128 tiles than two per SM (a small image leaves most
