@@ -98,17 +98,34 @@ __global__ void __launch_bounds__(JT)
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 
     float hi = 0.f, lo = 0.f;
-    float4 up = (colok && i0 > 0) ? __ldg(U + (size_t)(i0 - 1) * w4 + q) : z4;
-    float4 cur = (colok && i0 < h) ? __ldg(U + (size_t)i0 * w4 + q) : z4;
+    // All JR + 2 rows of the strip are loaded before any is used, so a warp has
+    // them all in flight at once (the sweep is bound by memory latency, not by
+    // the few flops per point); row o + 1 of `x` is grid row i0 + o.
+    // Lanes 0 and 31 also load the column beyond the warp's edge for every row.
+    float4 x[JR + 2];
+    float edge[JR];
+#pragma unroll
+    for (int o = 0; o < JR + 2; ++o) {
+        const int i = i0 - 1 + o;
+        x[o] = (colok && i >= 0 && i < h) ? __ldg(U + (size_t)i * w4 + q) : z4;
+    }
+    const int ec = lane == 0 ? j0 - 1 : j0 + 4;  // edge column of lanes 0 and 31
+    const bool eok = colok && (lane == 0 || lane == 31) && ec >= 0 && ec < w;
+#pragma unroll
+    for (int o = 0; o < JR; ++o) {
+        const int i = i0 + o;
+        edge[o] = (eok && i < h) ? __ldg(u + (size_t)i * w + ec) : 0.f;
+    }
+    float4 up = x[0], cur = x[1];
 #pragma unroll
     for (int o = 0; o < JR; ++o) {
         const int i = i0 + o;
         if (i >= h) break;
-        const float4 dn = (colok && i + 1 < h) ? __ldg(U + (size_t)(i + 1) * w4 + q) : z4;
+        const float4 dn = x[o + 2];
         float lf = __shfl_up_sync(FULL, cur.w, 1);
         float rt = __shfl_down_sync(FULL, cur.x, 1);
-        if (lane == 0) lf = (colok && j0 > 0) ? __ldg(u + (size_t)i * w + j0 - 1) : 0.f;
-        if (lane == 31) rt = (colok && j0 + 4 < w) ? __ldg(u + (size_t)i * w + j0 + 4) : 0.f;
+        if (lane == 0) lf = edge[o];
+        if (lane == 31) rt = edge[o];
         if (i > 0 && i < h - 1) {
             const float sx = nsum(up.x, dn.x, lf, cur.y);
             const float sy = nsum(up.y, dn.y, cur.x, cur.z);
