@@ -596,7 +596,7 @@ def run_reference(args, rank, world):
     g = synth.gaussian_taps_f32(GAUSS_R, GAUSS_SIGMA)
     _oracle_band(oracle, img, ks, g, 8, 0)  # start the thread pool
     t_probe = _oracle_band(oracle, img, ks, g, 8, 4096)
-    per_step_budget = max(0.5, 150.0 / max(args.steps + args.warmup, 1))
+    per_step_budget = max(0.01, args.ref_seconds / max(args.steps + args.warmup, 1))
     rows = int(max(1, min(H, 8 * per_step_budget / max(t_probe, 1e-6))))
     for i in range(args.warmup):
         _oracle_band(oracle, img, ks, g, rows, (i * rows) % (H - rows + 1))
@@ -702,6 +702,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="approximate host time of a --impl reference run (warm-up and timed steps)")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
