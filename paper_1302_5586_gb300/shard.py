@@ -1,4 +1,16 @@
-"""Row-band decomposition of the Jacobi iteration over several ranks.
+"""Row-band decompositions over several ranks: one large image's conv2d
+(read-only halo rows, no exchange) and the Jacobi iteration (halo exchange).
+
+Convolution of one image (`BandConv2d`): rank q computes the output rows
+[r0, r1) of an even split of the image's rows.  It reads input rows
+[r0 - kh//2, r1 + kh - 1 - kh//2), clipped to the image: inside that
+sub-image every window of an owned output row reads the same rows as in the
+whole image (at the image's top and bottom edge the sub-image's edge row is
+the image's, so clamp-to-edge clamps to the same row), so the owned rows are
+the same bits as one undivided call.  Nothing is exchanged; gathering the
+bands (if wanted) is one all-gather.
+
+Jacobi:
 
 The grid's rows are split into contiguous bands, one per rank (rank 0 also
 owns the top boundary row, the last rank the bottom one).  A rank holds its
@@ -18,6 +30,44 @@ tensors (NCCL) or any host implementation on CPU tensors (gloo).
 from __future__ import annotations
 
 import math
+
+
+def conv_band_bounds(h: int, rank: int, world: int):
+    """Output rows [r0, r1) of `rank` in an even split of h rows."""
+    q, rem = divmod(h, world)
+    r0 = rank * q + min(rank, rem)
+    return r0, r0 + q + (1 if rank < rem else 0)
+
+
+class BandConv2d:
+    """One rank's share of a clamp-to-edge conv2d of one h-row image with a
+    kh-row filter: the input rows it reads and the output rows it owns."""
+
+    def __init__(self, h: int, kh: int, rank: int, world: int):
+        if kh < 1 or h < 1 or world < 1 or not 0 <= rank < world:
+            raise ValueError("need h >= 1, kh >= 1 and 0 <= rank < world")
+        self.h, self.kh, self.rank, self.world = h, kh, rank, world
+        self.r0, self.r1 = conv_band_bounds(h, rank, world)
+        ah = kh // 2
+        self.lo = max(0, self.r0 - ah) if self.r1 > self.r0 else self.r0
+        self.hi = min(h, self.r1 + kh - 1 - ah) if self.r1 > self.r0 else self.r0
+
+    def input_rows(self):
+        """Global input rows [lo, hi) the rank reads (its band plus halo rows)."""
+        return self.lo, self.hi
+
+    def owned(self, sub_out):
+        """The owned output rows inside the sub-image's output (rows of the
+        last axis but one)."""
+        return sub_out[..., self.r0 - self.lo:self.r1 - self.lo, :]
+
+    def run(self, img, conv):
+        """conv(sub_image) -> output of the same shape; returns the owned rows.
+        `img` holds all rows (e.g. a read-only mapping); only [lo, hi) are read."""
+        sub = img[..., self.lo:self.hi, :]
+        if self.r1 == self.r0:  # more ranks than rows: nothing to compute
+            return sub
+        return self.owned(conv(sub))
 
 
 def band_bounds(h: int, rank: int, world: int):

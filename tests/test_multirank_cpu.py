@@ -1,6 +1,8 @@
 """Multi-rank paths on CPU with gloo (world sizes 2 and 3): the row-band
-Jacobi decomposition equals the undivided grid bit for bit, and the
-benchmark's cross-rank timing takes the slowest rank."""
+Jacobi decomposition equals the undivided grid bit for bit, the row-band
+split of one image's conv2d (halo rows, no exchange) equals the undivided
+image bit for bit, and the benchmark's cross-rank timing takes the slowest
+rank."""
 import os
 import socket
 
@@ -113,3 +115,53 @@ def test_bench_takes_the_slowest_rank(world):
     for r in range(world):
         assert out[r][0] == slowest
         assert out[r][1] == pytest.approx(1e9 * world * 4 / (slowest * 1e-3) / 1e9)
+
+
+def _conv_worker(rank, world, port, c, h, w, kh, kw, out):
+    _init(rank, world, port)
+    try:
+        img = synth.image_f32(51, c, h, w)
+        k = synth.filter_f32(52, kh, kw)
+        bc = shard.BandConv2d(h, kh, rank, world)
+        mine = bc.run(img, lambda sub: oracle.conv2d(np.ascontiguousarray(sub), k, want_bound=False)[0])
+        # one all-gather of the owned bands (padded to the largest band)
+        rows = torch.tensor([bc.r1 - bc.r0])
+        sizes = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
+        dist.all_gather(sizes, rows)
+        m = max(int(t) for t in sizes)
+        pad = torch.zeros((c, m, w), dtype=torch.float64)
+        pad[:, :bc.r1 - bc.r0] = torch.from_numpy(np.ascontiguousarray(mine))
+        parts = [torch.zeros_like(pad) for _ in range(world)]
+        dist.all_gather(parts, pad)
+        full = np.concatenate([p[:, :int(n)].numpy() for p, n in zip(parts, sizes)], axis=1)
+        out[rank] = full
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,c,h,w,kh,kw", [(2, 2, 37, 23, 5, 3), (3, 1, 41, 19, 15, 15), (3, 1, 4, 9, 7, 7),
+                                                (2, 1, 1, 16, 3, 3)])
+def test_band_conv2d_equals_single_image(world, c, h, w, kh, kw):
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_conv_worker, args=(r, world, port, c, h, w, kh, kw, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    img = synth.image_f32(51, c, h, w)
+    ref = oracle.conv2d(img, synth.filter_f32(52, kh, kw), want_bound=False)[0]
+    for r in range(world):
+        np.testing.assert_array_equal(out[r].view(np.uint64), ref.view(np.uint64))
+
+
+def test_conv_band_bounds_cover_the_rows():
+    for h in (1, 2, 7, 64, 1001):
+        for world in (1, 2, 3, 8):
+            spans = [shard.conv_band_bounds(h, r, world) for r in range(world)]
+            assert spans[0][0] == 0 and spans[-1][1] == h
+            assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))
+            assert all(z - a in (h // world, h // world + 1) for a, z in spans)
