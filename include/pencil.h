@@ -55,7 +55,7 @@ typedef enum pencil_status {
     PENCIL_ERR_NOMEM = -5,       /* workspace too small or device allocation failed */
     PENCIL_ERR_CUDA = -6,        /* a CUDA call failed; see pencil_last_cuda_error() */
     PENCIL_ERR_TIMEOUT = -7,     /* a bounded wait expired */
-    PENCIL_ERR_UNSUPPORTED = -8  /* a valid request this build does not implement */
+    PENCIL_ERR_UNSUPPORTED = -8  /* a valid request the library does not implement */
 } pencil_status;
 
 /* Storage types of images (filters are always FP32; arithmetic is FP32). */

@@ -190,7 +190,7 @@ const char *pencil_strerror(int status) {
         case PENCIL_ERR_NOMEM: return "workspace too small or device allocation failed";
         case PENCIL_ERR_CUDA: return "CUDA error (see pencil_last_cuda_error)";
         case PENCIL_ERR_TIMEOUT: return "bounded wait expired";
-        case PENCIL_ERR_UNSUPPORTED: return "not supported by this build";
+        case PENCIL_ERR_UNSUPPORTED: return "valid request the library does not implement";
         default: return "unknown status";
     }
 }
