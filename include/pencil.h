@@ -203,6 +203,17 @@ int pencil_batch_run(pencil_batch *b, int n, const pencil_image *imgs, void *str
  * has finished.  NULL is accepted. */
 int pencil_batch_destroy(pencil_batch *b);
 
+/* The auto-tuning step of Sec. 2 for a batch plan: for every filter side
+ * present in the n images, run that side's images alone under each tile
+ * variant (one warm-up run, then `reps` timed runs between CUDA events on
+ * `stream`), keep the fastest on the plan and report it in chosen[ks / 2]
+ * (chosen has 8 entries for sides 1, 3, ..., 15; -1 for sides not present;
+ * may be NULL).  Every variant gives the same bits, so tuning changes only
+ * the time.  Synchronous (it reads the events); the images' outputs are
+ * overwritten.  Same requirements on the images as pencil_batch_run.
+ * Errors: NULL, ARG (bad size or side, reps < 1), ALIAS, NOMEM, CUDA. */
+int pencil_tune(pencil_batch *b, int n, const pencil_image *imgs, int reps, void *stream, int *chosen);
+
 /* ------------------------------------------------------------------- arena
  * Byte-offset bookkeeping for one device memory budget, used by the serving
  * loop to admit requests only while their buffers fit (the paper has no

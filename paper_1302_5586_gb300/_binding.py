@@ -93,6 +93,7 @@ def lib():
         "pencil_batch_tiles": (i, [vp, i, vp, ctypes.POINTER(ctypes.c_longlong)]),
         "pencil_batch_run": (i, [vp, i, vp, vp]),
         "pencil_batch_destroy": (i, [vp]),
+        "pencil_tune": (i, [vp, i, vp, i, vp, ctypes.POINTER(i)]),
         "pencil_device_info": (i, [ctypes.c_char_p, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
         "pencil_arena_create": (i, [sz, sz, ctypes.POINTER(ctypes.c_void_p)]),
         "pencil_arena_alloc": (i, [vp, sz, ctypes.POINTER(ctypes.c_size_t)]),
@@ -282,6 +283,14 @@ def pencil_batch_tiles(b, imgs) -> int:
 
 def pencil_batch_run(b, imgs, stream=None):
     _check(lib().pencil_batch_run(b, len(imgs), imgs, _stream(stream)), "pencil_batch_run")
+
+
+def pencil_tune(b, imgs, reps=5, stream=None):
+    """Measure every tile variant per filter side present in `imgs` (a
+    make_images array), keep the fastest on plan b.  Returns {ks: variant}."""
+    chosen = (ctypes.c_int * 8)()
+    _check(lib().pencil_tune(b, len(imgs), imgs, reps, _stream(stream), chosen), "pencil_tune")
+    return {2 * i + 1: chosen[i] for i in range(8) if chosen[i] >= 0}
 
 
 def pencil_batch_destroy(b):

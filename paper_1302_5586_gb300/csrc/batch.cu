@@ -476,6 +476,50 @@ int pencil_batch_run(pencil_batch *b, int n, const pencil_image *imgs, void *str
     return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
 }
 
+int pencil_tune(pencil_batch *b, int n, const pencil_image *imgs, int reps, void *stream, int *chosen) {
+    if (!b || (n > 0 && !imgs)) return PENCIL_ERR_NULL;
+    if (n < 0 || reps < 1) return PENCIL_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!image_ok(imgs[i])) return PENCIL_ERR_ARG;
+    if (chosen)
+        for (int i = 0; i < kSides; ++i) chosen[i] = -1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    int st = ce == cudaSuccess ? PENCIL_OK : cuda_fail(ce);
+    std::vector<pencil_image> sub;
+    for (int ks = 1; ks <= 15 && st == PENCIL_OK; ks += 2) {
+        sub.clear();
+        for (int i = 0; i < n; ++i)
+            if (imgs[i].ks == ks) sub.push_back(imgs[i]);
+        if (sub.empty()) continue;
+        float best = 0.0f;
+        int best_v = 0;
+        for (int v = 0; v < PENCIL_BATCH_VARIANTS && st == PENCIL_OK; ++v) {
+            st = pencil_batch_set_variant(b, ks, v);
+            if (st == PENCIL_OK) st = pencil_batch_run(b, (int)sub.size(), sub.data(), stream);  // warm-up
+            if (st != PENCIL_OK) break;
+            ce = cudaEventRecord(e0, (cudaStream_t)stream);
+            for (int r = 0; r < reps && ce == cudaSuccess && st == PENCIL_OK; ++r)
+                st = pencil_batch_run(b, (int)sub.size(), sub.data(), stream);
+            if (ce == cudaSuccess && st == PENCIL_OK) ce = cudaEventRecord(e1, (cudaStream_t)stream);
+            if (ce == cudaSuccess && st == PENCIL_OK) ce = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (ce == cudaSuccess && st == PENCIL_OK) ce = cudaEventElapsedTime(&ms, e0, e1);
+            if (ce != cudaSuccess) st = cuda_fail(ce);
+            if (st == PENCIL_OK && (v == 0 || ms < best)) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        if (st == PENCIL_OK) st = pencil_batch_set_variant(b, ks, best_v);
+        if (st == PENCIL_OK && chosen) chosen[ks / 2] = best_v;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return st;
+}
+
 int pencil_batch_destroy(pencil_batch *b) {
     if (!b) return PENCIL_OK;
     cudaError_t e = cudaSuccess;

@@ -3,8 +3,9 @@ chosen by measurement on the GPU it will run on (the profile-driven tuning
 step of the paper's flow, Sec. 2).
 
 For each filter side present in a batch, the images with that side are run
-alone under every tile variant the kernel offers; the fastest variant (median
-of `reps` timed runs after a warm-up) is set on the plan.  Results are cached
+alone under every tile variant the kernel offers; the fastest variant (CUDA
+events around `reps` runs after a warm-up, measured in the library by
+pencil_tune) is set on the plan.  Results are cached
 in a JSON file keyed by GPU name, SM count, CUDA driver version, storage
 dtype and filter side, so later processes on the same kind of GPU skip the
 search.  The cache path is $PENCIL_TUNE_CACHE, else
@@ -14,7 +15,6 @@ from __future__ import annotations
 
 import json
 import os
-import statistics
 
 from . import _binding as b
 
@@ -37,17 +37,6 @@ def _key(dtype: int, ks: int) -> str:
     return f"{name}|sm{sms}|drv{drv}|{'f16' if dtype == b.PENCIL_F16 else 'f32'}|k{ks}"
 
 
-def _time_batch(torch, plan, imgs, stream, reps):
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-    b.pencil_batch_run(plan, imgs, stream)
-    for a, z in ev:
-        a.record(stream)
-        b.pencil_batch_run(plan, imgs, stream)
-        z.record(stream)
-    stream.synchronize()
-    return statistics.median(a.elapsed_time(z) for a, z in ev)
-
-
 def autotune(plan, dtype: int, items, reps: int = 5, use_cache: bool = True, path: str | None = None):
     """Choose and set the tile variant for every filter side in `items`
     ((in, out, k, h, w, ks) tuples, device tensors).  Returns {ks: (variant, source)}."""
@@ -57,22 +46,22 @@ def autotune(plan, dtype: int, items, reps: int = 5, use_cache: bool = True, pat
     cache = _load(path) if use_cache else {}
     stream = torch.cuda.current_stream()
     chosen = {}
+    todo = []
     for ks in sorted({it[5] for it in items}):
         key = _key(dtype, ks)
         if key in cache:
             v = int(cache[key]["variant"])
             b.pencil_batch_set_variant(plan, ks, v)
             chosen[ks] = (v, "cache")
-            continue
-        sub = b.make_images([it for it in items if it[5] == ks])
-        times = {}
-        for v in range(b.PENCIL_BATCH_VARIANTS):
-            b.pencil_batch_set_variant(plan, ks, v)
-            times[v] = _time_batch(torch, plan, sub, stream, reps)
-        v = min(times, key=times.get)
-        b.pencil_batch_set_variant(plan, ks, v)
-        chosen[ks] = (v, "measured")
-        cache[key] = {"variant": v, "ms": {str(k): round(t, 5) for k, t in times.items()}}
+        else:
+            todo.append(ks)
+    if todo:
+        # the search itself runs in the library (pencil_tune: CUDA events per
+        # variant and side, the fastest kept on the plan)
+        sub = b.make_images([it for it in items if it[5] in todo])
+        for ks, v in b.pencil_tune(plan, sub, reps, stream).items():
+            chosen[ks] = (v, "measured")
+            cache[_key(dtype, ks)] = {"variant": v, "reps": reps}
     if use_cache and any(src == "measured" for _, src in chosen.values()):
         os.makedirs(os.path.dirname(path), exist_ok=True)
         tmp = path + ".tmp"

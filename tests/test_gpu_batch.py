@@ -153,3 +153,26 @@ def test_full_size_512_images(dtype):
             assert np.all(np.abs(got.double().cpu().numpy() - o) <= tol * bound)
     finally:
         pg.pencil_batch_destroy(plan)
+
+
+def test_native_tune_reports_present_sides_and_keeps_bits():
+    """pencil_tune through the C ABI: a variant for every side present (and
+    only those), the plan keeps it, and the batch is still the standalone bits."""
+    items, _ = make_batch(33, 20, 80, 500, pg.PENCIL_F32)
+    plan = pg.pencil_batch_create(pg.PENCIL_F32, 32, 1 << 16)
+    try:
+        imgs = pg.make_images(items)
+        chosen = pg.pencil_tune(plan, imgs, reps=2)
+        assert set(chosen) == {it[5] for it in items}
+        assert all(0 <= v < pg.PENCIL_BATCH_VARIANTS for v in chosen.values())
+        with pytest.raises(pg.PencilError) as e:
+            pg.pencil_tune(plan, imgs, reps=0)
+        assert e.value.name == "PENCIL_ERR_ARG"
+        for it in items:
+            it[1].zero_()
+        pg.pencil_batch_run(plan, imgs)
+        torch.cuda.synchronize()
+        for it in items:
+            assert torch.equal(it[1], standalone(it, pg.PENCIL_F32))
+    finally:
+        pg.pencil_batch_destroy(plan)
