@@ -107,3 +107,14 @@ def test_binding_constants_match_the_header():
         m = re.search(r"#define\s+%s\s+(\d+)" % name, text) or re.search(r"\b%s\s*=\s*(\d+)" % name, text)
         assert m, name
         assert getattr(pg, name) == int(m.group(1)), name
+
+
+def test_status_and_tune_argument_errors_before_cuda(lib):
+    done = ctypes.c_int(-1)
+    assert lib.pencil_selftest_wait_timeout(0, ctypes.byref(done)) == -1        # limit below 1 us
+    assert lib.pencil_selftest_wait_timeout(2000000, ctypes.byref(done)) == -1  # above 1 s
+    assert lib.pencil_selftest_wait_timeout(1000, None) == -2
+    chosen = (ctypes.c_int * 8)()
+    assert lib.pencil_tune(None, 0, None, 1, None, chosen) == -2
+    imgs = pg.make_images([(0x1000, 0x2000, 0x3000, 8, 8, 3)])
+    assert lib.pencil_tune(None, 1, imgs, 1, None, chosen) == -2
