@@ -113,7 +113,11 @@ int pencil_conv2d(int h, int w, PENCIL_ARR2(const float, in, h, w), int kh, int 
  * (binary16 images; FP32 accumulation; binary16 results rounded to nearest
  * even).  in, out: c*h*w elements of dtype, device memory; k: kh*kw FP32,
  * device memory.  flags: PENCIL_CONV_GENERIC and/or one PENCIL_BORDER(m).
- * Errors: ARG, NULL, ALIAS, PTR, CUDA. */
+ * Speed, not results, depends on alignment: images whose rows are 16-byte
+ * aligned (w a multiple of 4 for FP32, of 8 for binary16, and in and out
+ * 16-byte aligned) with the clamp or zero border load their tiles with the
+ * tensor memory accelerator; others use cp.async copies.  The call may be
+ * captured in a CUDA graph.  Errors: ARG, NULL, ALIAS, PTR, CUDA. */
 int pencil_conv2d_ex(int c, int h, int w, const void *in, int kh, int kw, const float *k,
                      void *out, int dtype, int flags, void *stream);
 
