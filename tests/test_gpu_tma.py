@@ -113,3 +113,25 @@ def test_tma_separable_matches_oracle(dtype, border):
                 slack = np.abs(k2 - k2.astype(np.float32).astype(np.float64)).sum() * np.abs(img.astype(np.float64)).max()
             assert np.all(np.abs(out - ref) <= tol * bound + slack), f"K={K} shape={shape}"
     assert pg.pencil_device_status() == pg.PENCIL_OK
+
+
+@pytest.mark.parametrize("w", [264, 262])
+def test_conv2d_ex_in_a_cuda_graph(w):
+    """pencil_conv2d_ex captured in a CUDA graph (TMA-staged for aligned rows,
+    cp.async otherwise) replays to the bits of a plain stream launch."""
+    img = synth.image_f32(970, 2, 45, w)
+    k = to_dev(synth.filter_f32(971, 15, 15))
+    d_in = to_dev(img)
+    ref = torch.empty_like(d_in)
+    pg.pencil_conv2d_ex(2, 45, w, d_in, 15, 15, k, ref, pg.PENCIL_F32)
+    out = torch.full_like(d_in, float("nan"))
+    g = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    cap.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(g, stream=cap):
+        pg.pencil_conv2d_ex(2, 45, w, d_in, 15, 15, k, out, pg.PENCIL_F32, 0, cap.cuda_stream)
+    assert torch.isnan(out).all()  # captured, not run
+    g.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), ref.cpu().numpy().view(np.uint32))
+    assert pg.pencil_device_status() == pg.PENCIL_OK
