@@ -15,8 +15,11 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "oracle.c")
-_BUILD = os.path.join(_HERE, "_build")
+# ORACLE_SRC, when set, names another copy of oracle.c to build (into a _build
+# folder beside it) and load instead: the mutation tests plant one mistake in
+# such a copy and check that the pin tests catch it.
+_SRC = os.path.abspath(os.environ.get("ORACLE_SRC") or os.path.join(_HERE, "oracle.c"))
+_BUILD = os.path.join(os.path.dirname(_SRC), "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
 DT_F32 = 0
@@ -26,7 +29,7 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into oracle/_build/liboracle.so (OpenMP when available).
+    """Compile oracle.c into _build/liboracle.so beside it (OpenMP when available).
 
     FP contraction is switched off so that every multiply and add rounds as
     written, on x86-64 and aarch64 alike.
