@@ -6,7 +6,8 @@ a Poisson trace.  The scheduler loop:
 * admits arrived requests in arrival order while a slot is free
   (`max_inflight`) and the arena (one device buffer of `budget_bytes`, offsets
   kept by the native pencil_arena) has room for the request's input and
-  output; a request that does not fit waits until completions free memory;
+  output; a request that does not fit waits until completions free memory,
+  and one that could not fit even an empty arena is rejected on arrival;
 * packs every request admitted in one pass into a wave and issues it on the
   next of `streams` CUDA streams: host-to-device copies of the inputs (from
   pinned host memory into the arena), ONE batched persistent conv2d launch
@@ -79,6 +80,18 @@ def make_trace(seed: int, rate: float, duration: float, lo: int = 128, hi: int =
     return Trace(reqs, pool_elems, bank)
 
 
+ARENA_ALIGN = 256  # bytes; the arena rounds blocks up and its capacity down to this
+
+
+def fits_alone(h: int, w: int, esz: int, budget: int, align: int = ARENA_ALIGN) -> bool:
+    """Whether a request's input and output blocks fit an empty arena of
+    `budget` bytes (each block rounded up to `align`, the capacity rounded
+    down); a request that does not is rejected on arrival instead of waiting
+    for memory that can never be freed."""
+    need = -(-h * w * esz // align) * align
+    return 2 * need <= budget // align * align
+
+
 @dataclasses.dataclass
 class Stats:
     mode: str
@@ -121,7 +134,7 @@ class Server:
         self.esz = 2 if dtype == b.PENCIL_F16 else 4
         self.budget = budget_bytes
         self.pool = torch.empty(budget_bytes, dtype=torch.uint8, device=self.dev)
-        self.arena = b.pencil_arena_create(budget_bytes, 256)
+        self.arena = b.pencil_arena_create(budget_bytes, ARENA_ALIGN)
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(streams)]
         self.plans = [b.pencil_batch_create(dtype, max_wave, max_tiles) for _ in range(streams)]
         self.max_wave = max_wave
@@ -169,7 +182,9 @@ class Server:
         n = len(reqs)
         lat = np.full(n, np.nan)
         outputs = [None] * n if keep_outputs else None
-        sink = None if keep_outputs else torch.empty(sink_bytes // self.esz, dtype=self.tdtype, pin_memory=True)
+        largest = max((r.h * r.w for r in reqs), default=1)
+        sink = None if keep_outputs else torch.empty(max(sink_bytes // self.esz, largest), dtype=self.tdtype,
+                                                     pin_memory=True)
         sink_pos = 0
         pending = collections.deque()
         inflight = [collections.deque() for _ in self.streams]
@@ -189,7 +204,7 @@ class Server:
             now = time.perf_counter() - t0
             while nxt < n and reqs[nxt].arrival <= now:
                 r = reqs[nxt]
-                if 2 * r.h * r.w * self.esz > self.budget:  # can never fit
+                if not fits_alone(r.h, r.w, self.esz, self.budget):
                     rejected += 1
                 else:
                     pending.append(r)
@@ -290,4 +305,4 @@ def percentile_summary(stats_list):
     return {s.mode: s.summary() for s in stats_list}
 
 
-__all__ = ["Request", "Trace", "Stats", "Server", "make_trace", "host_pool", "percentile_summary"]
+__all__ = ["Request", "Trace", "Stats", "Server", "make_trace", "fits_alone", "host_pool", "percentile_summary"]
