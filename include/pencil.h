@@ -38,7 +38,9 @@
 
 /* PENCIL_ARR2(T, name, n, m): a [n][m] array parameter.  C99 sees the
  * PENCIL form `T name[restrict const static n][m]`; C++/CUDA see `T *name`,
- * which has the same ABI. */
+ * which has the same ABI.  C before C2X converts no `float[n][m]` to a
+ * `const float` parameter of this form: declare the input array const, or
+ * cast it. */
 #ifdef __cplusplus
 extern "C" {
 #define PENCIL_ARR2(T, name, n, m) T *name

@@ -37,6 +37,54 @@ def test_header_compiles_as_c99_and_cxx(tmp_path):
                     str(tmp_path / "b.o")], check=True)
 
 
+C_CLIENT = r"""
+#include <stdio.h>
+#include <string.h>
+#include "pencil.h"
+
+int main(int argc, char **argv)
+{
+    (void)argv;
+    const int h0 = argc - 1; /* 0 at run time, unknown to the compiler */
+    if (pencil_version() < 100) return 10;
+    if (strcmp(pencil_strerror(PENCIL_OK), "ok") != 0) return 11;
+    pencil_arena *a = NULL;
+    if (pencil_arena_create(4096, 256, &a) != PENCIL_OK || !a) return 12;
+    size_t x = 1, y = 1;
+    if (pencil_arena_alloc(a, 1, &x) != PENCIL_OK || x != 0) return 13;
+    if (pencil_arena_alloc(a, 300, &y) != PENCIL_OK || y != 256) return 14;
+    if (pencil_arena_free_bytes(a) != 4096 - 768) return 15;
+    if (pencil_arena_alloc(a, 4096, &x) != PENCIL_ERR_NOMEM) return 16;
+    if (pencil_arena_free(a, 256) != PENCIL_OK || pencil_arena_free(a, 0) != PENCIL_OK) return 17;
+    if (pencil_arena_largest_free(a) != 4096) return 18;
+    pencil_arena_destroy(a);
+    /* const inputs: C before C2X converts no T[n][m] to const T (*)[m] */
+    static const float img[4][4], k[3][3];
+    float out[4][4];
+    if (pencil_conv2d(4, h0, img, 3, 3, k, out) != PENCIL_ERR_ARG) return 19;
+    if (pencil_jacobi2d_workspace_size(100, 100) == 0) return 20;
+    printf("c client ok\n");
+    return 0;
+}
+"""
+
+
+def test_a_c_program_links_and_calls_the_library(lib, tmp_path):
+    """The boundary from C itself: a C99 program includes pencil.h, links the
+    built library and runs its host-only calls (version, status text, the
+    arena, an argument check, a workspace size)."""
+    import os
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    libdir = os.path.dirname(pg.LIB_PATH)
+    exe = str(tmp_path / "client")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-pedantic", "-I" + os.path.dirname(pg.HEADER),
+                    str(src), "-o", exe, "-L" + libdir, "-l:" + os.path.basename(pg.LIB_PATH),
+                    "-Wl,-rpath," + libdir], check=True, capture_output=True, text=True)
+    p = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert p.returncode == 0 and p.stdout.strip() == "c client ok", (p.returncode, p.stdout, p.stderr)
+
+
 def test_utility_calls(lib):
     assert pg.pencil_version() >= 100
     assert pg.pencil_strerror(0) == "ok"
