@@ -92,6 +92,85 @@ def fits_alone(h: int, w: int, esz: int, budget: int, align: int = ARENA_ALIGN) 
     return 2 * need <= budget // align * align
 
 
+class Admission:
+    """The serving loop's host-side admission (no CUDA calls).
+
+    Arrived requests queue in arrival order.  `wave` takes requests from the
+    head of the queue while fewer than `max_inflight` are in flight and the
+    arena takes the head's input block and then its output block; when either
+    allocation fails the head waits (the input block is given back), so a
+    request is never reordered past an earlier one.  A request that could
+    never fit even an empty arena is rejected on arrival; a cancelled request
+    and one whose deadline (seconds after its arrival) has passed are dropped
+    when they reach the head, before any memory is taken.  `release` gives a
+    finished request's blocks back.  `alloc(nbytes) -> offset | None` and
+    `free(offset)` are the arena's calls (a test may pass failing ones)."""
+
+    def __init__(self, alloc, free, budget: int, esz: int, max_inflight: int, deadline_s: float | None = None):
+        self.alloc, self.free = alloc, free
+        self.budget, self.esz, self.max_inflight = budget, esz, max_inflight
+        self.deadline_s = deadline_s
+        self.pending = collections.deque()
+        self.cancelled_ids = set()
+        self.inflight = 0
+        self.rejected = self.cancelled = self.expired = 0
+
+    @property
+    def dropped(self) -> int:
+        """Requests that will never run: rejected, cancelled or expired."""
+        return self.rejected + self.cancelled + self.expired
+
+    def arrive(self, r) -> bool:
+        """Queue an arrived request; False if it is rejected or was cancelled."""
+        if r.rid in self.cancelled_ids:
+            self.cancelled_ids.discard(r.rid)
+            self.cancelled += 1
+            return False
+        if not fits_alone(r.h, r.w, self.esz, self.budget):
+            self.rejected += 1
+            return False
+        self.pending.append(r)
+        return True
+
+    def cancel(self, rid: int) -> None:
+        """Cancel a request that has not been admitted (no effect afterwards)."""
+        self.cancelled_ids.add(rid)
+
+    def wave(self, limit: int, now: float) -> list:
+        """Admit up to `limit` requests at time `now`: [(request, in_offset, out_offset)]."""
+        out = []
+        while self.pending and len(out) < limit and self.inflight + len(out) < self.max_inflight:
+            r = self.pending[0]
+            if r.rid in self.cancelled_ids:
+                self.pending.popleft()
+                self.cancelled_ids.discard(r.rid)
+                self.cancelled += 1
+                continue
+            if self.deadline_s is not None and now - r.arrival > self.deadline_s:
+                self.pending.popleft()
+                self.expired += 1
+                continue
+            nb = r.h * r.w * self.esz
+            oi = self.alloc(nb)
+            if oi is None:
+                break
+            oo = self.alloc(nb)
+            if oo is None:
+                self.free(oi)
+                break
+            self.pending.popleft()
+            out.append((r, oi, oo))
+        self.inflight += len(out)
+        return out
+
+    def release(self, items) -> None:
+        """A wave's requests finished: give their blocks back."""
+        for _, oi, oo in items:
+            self.free(oi)
+            self.free(oo)
+        self.inflight -= len(items)
+
+
 @dataclasses.dataclass
 class Stats:
     mode: str
@@ -103,12 +182,15 @@ class Stats:
     waves: int
     peak_inflight: int
     peak_arena_bytes: int
+    cancelled: int = 0
+    expired: int = 0
 
     def summary(self) -> dict:
         lat = self.latency_ms
         ok = lat[np.isfinite(lat)]
         return {
             "mode": self.mode, "requests": self.requests, "rejected": self.rejected,
+            "cancelled": self.cancelled, "expired": self.expired,
             "p50_ms": round(float(np.percentile(ok, 50)), 3) if ok.size else None,
             "p99_ms": round(float(np.percentile(ok, 99)), 3) if ok.size else None,
             "mean_ms": round(float(ok.mean()), 3) if ok.size else None,
@@ -173,10 +255,12 @@ class Server:
         return self.pool[off:off + n * self.esz].view(self.tdtype)
 
     def run(self, trace: Trace, host_pool, filters_dev, mode: str = "served", keep_outputs: bool = False,
-            sink_bytes: int = 1 << 29) -> tuple:
+            sink_bytes: int = 1 << 29, deadline_ms: float | None = None, cancel=()) -> tuple:
         """Replay `trace` open-loop.  host_pool: pinned host tensor of the
         storage dtype (trace.pool_elems elements); filters_dev: device FP32
-        tensor holding trace.filters.  Returns (Stats, outputs or None)."""
+        tensor holding trace.filters.  Requests still queued `deadline_ms`
+        after their arrival, and those whose ids are in `cancel`, are dropped
+        unrun (latency NaN).  Returns (Stats, outputs or None)."""
         torch = self.torch
         reqs = trace.requests
         n = len(reqs)
@@ -186,12 +270,14 @@ class Server:
         sink = None if keep_outputs else torch.empty(max(sink_bytes // self.esz, largest), dtype=self.tdtype,
                                                      pin_memory=True)
         sink_pos = 0
-        pending = collections.deque()
+        adm = Admission(lambda nb: b.pencil_arena_alloc(self.arena, nb),
+                        lambda off: b.pencil_arena_free(self.arena, off), self.budget, self.esz,
+                        self.max_inflight, None if deadline_ms is None else deadline_ms * 1e-3)
+        for rid in cancel:
+            adm.cancel(int(rid))
         inflight = [collections.deque() for _ in self.streams]
-        n_inflight = 0
         peak_inflight = 0
         peak_arena = 0
-        rejected = 0
         waves = 0
         done = 0
         pix = 0
@@ -200,14 +286,10 @@ class Server:
         kbase = filters_dev.data_ptr()
         t0 = time.perf_counter()
         last_done = t0
-        while done + rejected < n:
+        while done + adm.dropped < n:
             now = time.perf_counter() - t0
             while nxt < n and reqs[nxt].arrival <= now:
-                r = reqs[nxt]
-                if not fits_alone(r.h, r.w, self.esz, self.budget):
-                    rejected += 1
-                else:
-                    pending.append(r)
+                adm.arrive(reqs[nxt])
                 nxt += 1
             progressed = False
             # completions
@@ -215,30 +297,17 @@ class Server:
                 while q and q[0][0].query():
                     ev, items = q.popleft()
                     tdone = time.perf_counter()
-                    for r, oi, oo in items:
+                    for r, _, _ in items:
                         lat[r.rid] = (tdone - t0 - r.arrival) * 1e3
-                        b.pencil_arena_free(self.arena, oi)
-                        b.pencil_arena_free(self.arena, oo)
                         pix += r.h * r.w
-                    n_inflight -= len(items)
+                    adm.release(items)
                     done += len(items)
                     last_done = tdone
                     progressed = True
             # admission: arrival order, while a slot and arena memory are free
-            wave = []
-            limit = self.max_wave if mode == "served" else 1
-            while pending and len(wave) < limit and n_inflight + len(wave) < self.max_inflight:
-                r = pending[0]
-                nb = r.h * r.w * self.esz
-                oi = b.pencil_arena_alloc(self.arena, nb)
-                if oi is None:
-                    break
-                oo = b.pencil_arena_alloc(self.arena, nb)
-                if oo is None:
-                    b.pencil_arena_free(self.arena, oi)
-                    break
-                pending.popleft()
-                wave.append((r, oi, oo))
+            dropped = adm.dropped
+            wave = adm.wave(self.max_wave if mode == "served" else 1, time.perf_counter() - t0)
+            progressed = progressed or adm.dropped != dropped
             if wave:
                 s = self.streams[rr % len(self.streams)]
                 plan = self.plans[rr % len(self.plans)]
@@ -272,8 +341,7 @@ class Server:
                     ev.record(s)
                 q.append((ev, wave))
                 waves += 1
-                n_inflight += len(wave)
-                peak_inflight = max(peak_inflight, n_inflight)
+                peak_inflight = max(peak_inflight, adm.inflight)
                 peak_arena = max(peak_arena, self.budget - b.pencil_arena_free_bytes(self.arena))
                 progressed = True
             if not progressed:
@@ -284,7 +352,8 @@ class Server:
         torch.cuda.synchronize(self.dev)
         first = reqs[0].arrival if n else 0.0
         wall = (last_done - t0) - first
-        st = Stats(mode, n, rejected, pix, wall, lat, waves, peak_inflight, peak_arena)
+        st = Stats(mode, n, adm.rejected, pix, wall, lat, waves, peak_inflight, peak_arena, adm.cancelled,
+                   adm.expired)
         if keep_outputs:
             outputs = [o.view(r.h, r.w) if o is not None else None for o, r in zip(outputs, reqs)]
         return st, outputs
@@ -305,4 +374,5 @@ def percentile_summary(stats_list):
     return {s.mode: s.summary() for s in stats_list}
 
 
-__all__ = ["Request", "Trace", "Stats", "Server", "make_trace", "fits_alone", "host_pool", "percentile_summary"]
+__all__ = ["Request", "Trace", "Stats", "Server", "Admission", "make_trace", "fits_alone", "host_pool",
+           "percentile_summary"]
