@@ -1,8 +1,9 @@
 """Multi-rank paths on CPU with gloo (world sizes 2 and 3): the row-band
 Jacobi decomposition equals the undivided grid bit for bit, the row-band
 split of one image's conv2d (halo rows, no exchange) equals the undivided
-image bit for bit, and the benchmark's cross-rank timing takes the slowest
-rank."""
+image bit for bit, the benchmark's cross-rank timing takes the slowest
+rank, and a rank that dies between steps makes its neighbour's next halo
+exchange fail with an error instead of hanging."""
 import os
 import socket
 
@@ -165,3 +166,63 @@ def test_conv_band_bounds_cover_the_rows():
             assert spans[0][0] == 0 and spans[-1][1] == h
             assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))
             assert all(z - a in (h // world, h // world + 1) for a, z in spans)
+
+
+def _dying_worker(rank, world, port, die_after, out):
+    """Rank 1 raises between steps (after `die_after` sweeps, with nothing of
+    its own in flight); rank 0 keeps iterating and must get an error from its
+    next halo exchange, within the process group's timeout, not hang."""
+    import datetime
+    import time
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    h, w = 40, 16
+    u0 = synth.jacobi_init_f32(43, h, w).astype(np.float64)
+    bj = shard.BandJacobi(h, w, rank, world, 1, dist)
+    lo, hi = bj.local_slice()
+    local = torch.from_numpy(u0[lo:hi].copy())
+    sweeps = {"n": 0}
+
+    def sweep(loc, n):
+        if rank == 1 and sweeps["n"] >= die_after:
+            raise RuntimeError("injected rank failure")
+        arr = loc.numpy()
+        arr[...] = oracle.jacobi2d(arr, n)[0]
+        sweeps["n"] += n
+
+    t0 = time.monotonic()
+    try:
+        bj.run(local, 1000, 0, sweep, lambda sub: 0.0)
+        out[rank] = ("finished", sweeps["n"], time.monotonic() - t0)
+    except Exception as e:  # the failure, as each rank sees it
+        out[rank] = (type(e).__name__, sweeps["n"], time.monotonic() - t0)
+    finally:
+        try:
+            dist.destroy_process_group()
+        except Exception:
+            pass
+
+
+def test_a_rank_that_dies_is_detected_by_the_others():
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_dying_worker, args=(r, 2, port, 3, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        for p in procs:
+            p.join(120)
+            assert p.exitcode is not None, "a rank hung after its peer died"
+    finally:
+        for p in procs:
+            if p.exitcode is None:
+                p.kill()
+    what1, n1, _ = out[1]
+    assert what1 == "RuntimeError" and n1 == 3           # the injected failure, between steps
+    what0, n0, t0 = out[0]
+    assert what0 != "finished" and n0 <= 4              # the survivor stopped at the next exchange ...
+    assert t0 < 60                                       # ... with an error, not a hang
