@@ -26,6 +26,10 @@
  *   - Ownership: the caller owns every array; the library never frees them.
  *     Scratch for plain calls comes from a library pool released by
  *     pencil_shutdown(); _ex calls take caller-provided workspace.
+ *   - Devices: the library works on the calling thread's current CUDA device.
+ *     The plain calls' scratch lives on the device that was current when it
+ *     was allocated, so a process that moves plain calls to another device
+ *     calls pencil_shutdown() first (one process per GPU needs nothing).
  *   - Errors: every call returns 0 (PENCIL_OK) or a negative pencil_status.
  *     Nothing aborts or traps.  After PENCIL_ERR_CUDA the CUDA error code is
  *     kept per thread and readable with pencil_last_cuda_error().
@@ -406,8 +410,9 @@ int pencil_device_status(void);
 int pencil_selftest_wait_timeout(unsigned limit_us, int *completed);
 
 /* Release the library's device pools (plain calls' scratch, the temporaries
- * of pencil_conv2d_chain).  Call when no library work is in flight.  Safe to
- * call more than once; later calls allocate again. */
+ * of pencil_conv2d_chain).  Call when no library work is in flight, and
+ * before moving plain calls to another device.  Safe to call more than once;
+ * later calls allocate again. */
 void pencil_shutdown(void);
 
 #ifdef __cplusplus
