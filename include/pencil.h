@@ -284,7 +284,8 @@ int pencil_jacobi2d_ex(int h, int w, float *u, int iters, int check_every, doubl
                        void *workspace, size_t ws_bytes, int temporal_t, void *stream);
 
 /* Stream-ordered residual of one grid (device memory) into *res_out (device).
- * workspace as for pencil_jacobi2d_ex.  Errors: ARG, NULL, PTR, NOMEM, CUDA. */
+ * workspace as for pencil_jacobi2d_ex (not overlapping u or res_out).
+ * Errors: ARG, NULL, ALIAS, PTR, NOMEM, CUDA. */
 int pencil_residual2d(int h, int w, const float *u, double *res_out, void *workspace,
                       size_t ws_bytes, void *stream);
 

@@ -511,6 +511,10 @@ int pencil_residual2d(int h, int w, const float *u, double *res_out, void *works
     if (!u || !res_out || !workspace) return PENCIL_ERR_NULL;
     if (ws_bytes < jacobi_workspace_bytes(h, w)) return PENCIL_ERR_NOMEM;
     if ((uintptr_t)workspace % 256 != 0) return PENCIL_ERR_ARG;
+    const size_t ub = sizeof(float) * (size_t)h * w;
+    if (overlaps(workspace, ws_bytes, u, ub) || overlaps(res_out, sizeof(double), u, ub) ||
+        overlaps(res_out, sizeof(double), workspace, ws_bytes))
+        return PENCIL_ERR_ALIAS;
     if (kind_of(u) != Mem::Device || kind_of(res_out) != Mem::Device ||
         kind_of(workspace) != Mem::Device)
         return PENCIL_ERR_PTR;

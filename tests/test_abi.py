@@ -166,3 +166,15 @@ def test_status_and_tune_argument_errors_before_cuda(lib):
     assert lib.pencil_tune(None, 0, None, 1, None, chosen) == -2
     imgs = pg.make_images([(0x1000, 0x2000, 0x3000, 8, 8, 3)])
     assert lib.pencil_tune(None, 1, imgs, 1, None, chosen) == -2
+
+
+def test_residual_alias_checks_before_cuda(lib):
+    """The residual's workspace and result may not overlap the grid or each
+    other (checked on the addresses alone, before any CUDA call)."""
+    ws = pg.pencil_jacobi2d_workspace_size(4, 4)
+    u, res, wsp = 1 << 20, 2 << 20, 3 << 20          # disjoint, 256-byte aligned
+    assert lib.pencil_residual2d(4, 4, u, u + 8, wsp, ws, None) == -3       # result inside the grid
+    assert lib.pencil_residual2d(4, 4, u, res, u, ws, None) == -3           # workspace over the grid
+    assert lib.pencil_residual2d(4, 4, u, wsp + 16, wsp, ws, None) == -3    # result inside the workspace
+    assert lib.pencil_residual2d(4, 4, u, res, wsp + 8, ws, None) == -1     # workspace not 256-aligned
+    assert lib.pencil_residual2d(4, 4, u, res, wsp, ws - 1, None) == -5     # workspace too small
