@@ -248,6 +248,8 @@ def test_server_loop_on_a_fake_device(fake_server, mode):
     srv, fake = fake_server
     tr = serve.make_trace(11, rate=20000.0, duration=0.01, lo=8, hi=200, klo=3, khi=7, pool_elems=1 << 18)
     n = len(tr.requests)
+    for r in tr.requests:  # all at once: the fake device is instant, so only a burst is sure to batch
+        r.arrival = 0.0
     pool = torch.arange(tr.pool_elems, dtype=torch.float32)
     cancel = {3, 17, n - 1}
     st, outs = srv.run(tr, pool, torch.zeros(1), mode=mode, keep_outputs=True, cancel=cancel)
