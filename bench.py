@@ -38,27 +38,50 @@ GAUSS_R, GAUSS_SIGMA = 7, 3.0
 PX_PER_PASS = C * H * W
 PASSES = len(DIRECT_K) + 1
 PX_PER_STEP = PX_PER_PASS * PASSES
-SM_COUNT = 152
+SM_COUNT = 152            # GB300; the run reads the device's own count
 FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+SM_MAX_MHZ = 2070.0       # GB300; the run reads nvidia-smi's clocks.max.sm
+TOL_F32 = 1e-6            # |gpu - oracle| <= TOL_F32 * sum|k||x| per pixel
+TOL_F16 = 2.0 ** -10      # the same against the oracle on the binary16 input
+TOL_JACOBI = 1e-5         # max |u_gpu - u_oracle| after 100 sweeps
 SERVE_SECONDS = 60.0
 WORKLOAD = ("conv2d clamp-to-edge, 3 planar channels of 8192x8192 FP32, filters 3x3/7x7/15x15 "
             "direct (normalised U[0,1) weights) + 15x15 Gaussian sigma=3 separable")
 
 
-def config(extra=None):
-    cfg = {"workload": WORKLOAD, "channels": C, "h": H, "w": W,
-           "filters": ["3x3", "7x7", "15x15", "gauss15x15-separable"],
-           "seed": synth.SEEDS["conv8192x3"],
-           "l2": "inputs larger than L2 (768 MiB image vs 129 MB L2); no flush between steps"}
-    if extra:
-        cfg.update(extra)
-    return cfg
+def config():
+    """The workload both arms measure (the same dict for either)."""
+    return {"workload": WORKLOAD, "channels": C, "h": H, "w": W,
+            "filters": ["3x3", "7x7", "15x15", "gauss15x15-separable"],
+            "seed": synth.SEEDS["conv8192x3"],
+            "l2": "inputs larger than L2 (768 MiB image vs 129 MB L2); no flush between steps",
+            "parallelism": "one image set per process (independent images: replicas, no collective)"}
 
 
-def fp32_peak_tflops():
-    """FP32 (non-tensor) FMA peak from unit counts and the maximum SM clock."""
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+_PEAK = {"sms": SM_COUNT, "mhz": SM_MAX_MHZ, "source": "nominal GB300 counts"}
+
+
+def fp32_peak_tflops(sms=None, mhz=None):
+    """FP32 (non-tensor) FMA peak from unit counts and the maximum SM clock:
+    SMs x 128 FP32 lanes x 2 flops per FMA x MHz (the device's own SM count and
+    maximum clock once set_fp32_peak has read them)."""
+    sms = _PEAK["sms"] if sms is None else sms
+    mhz = _PEAK["mhz"] if mhz is None else mhz
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def set_fp32_peak(sms, mhz, source):
+    _PEAK.update(sms=int(sms), mhz=float(mhz), source=source)
+
+
+def max_sm_mhz(index):
+    """clocks.max.sm of a GPU from nvidia-smi, or None."""
+    try:
+        r = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=clocks.max.sm",
+                            "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=30)
+        return float(r.stdout.strip().splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        return None
 
 
 def measured_peaks():
@@ -170,6 +193,10 @@ def run_ours(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
+    _, sms, _ = pg.pencil_device_info()
+    mhz = max_sm_mhz(local_rank) or measured_peaks().get("sm_max_mhz") or SM_MAX_MHZ
+    set_fp32_peak(sms, mhz, f"derived: {sms} SMs (device count) x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz "
+                            "(clocks.max.sm)")
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -231,32 +258,48 @@ def run_ours(args, rank, world, local_rank):
     roofline = {"bound": "alu", "kernel": "conv2d_direct_tma_kernel<float,15,15,16,8,4,2,3,false,true>",
                 "achieved": round(achieved, 3),
                 "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "peak_source": _PEAK["source"],
                 "launch_ms": round(k15_ms, 4), "algorithmic_bytes": 8 * PX_PER_PASS, "traffic": traffic}
     clk = clocks.summary()
 
-    extras = {}
+    extras, keep = {}, {}
     if rank == 0 and not args.no_extras:
-        extras = measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g, args.serve_seconds)
+        extras, keep = measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g, args.serve_seconds)
     e2e = measure_e2e(torch, pg, img, ks, g, max(2, min(args.steps // 50, 5))) if not args.no_e2e else None
 
-    del d_out, d_img
     if dist is not None:
         dist.barrier()
     if rank == 0:
-        cpu = None if (world > 1 or args.no_cpu) else cpu_baseline(img, ks, g, budget_s=args.cpu_seconds)
+        cpu, precision = None, None
+        if world == 1 and not args.no_cpu:
+            cpu, precision = cpu_baseline(torch, img, ks, g, d_out, keep, budget_s=args.cpu_seconds)
+        del d_out, d_img, keep
         launches = PASSES * args.steps
         line = {"metric": METRIC, "value": round(value, 3), "unit": "Gpixel/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded SplitMix64 U[0,1) images; normalised U[0,1) and Gaussian filters)",
-                "config": config({"parallelism": f"replicas x{world} (independent images per GPU)"}),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "hbm_peak_gbs": measured_peaks().get("hbm_gbs")}
-        line.update(extras)
+                "config": config(), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk, "hbm_peak_gbs": measured_peaks().get("hbm_gbs")}
+        line.update(ordered_extras(extras, precision))
         print(json.dumps(line))
+    else:
+        del d_out, d_img
     if dist is not None:
         dist.destroy_process_group()
+
+
+# Keys printed last, in this order: the per-config summary the reader needs
+# most sits at the end of the line, where a truncated log keeps it.
+SUMMARY_KEYS = ("batched_512", "serving_2000_req_s", "passes_f16", "passes_f32", "jacobi_8192x8192_100sweeps")
+
+
+def ordered_extras(extras, precision):
+    out = {k: v for k, v in extras.items() if k not in SUMMARY_KEYS}
+    out.update({k: extras[k] for k in SUMMARY_KEYS if k in extras})
+    if precision is not None:
+        out["precision"] = precision
+    return out
 
 
 def _time_stream(torch, stream, fn, reps):
@@ -272,44 +315,56 @@ def _time_stream(torch, stream, fn, reps):
     return a.elapsed_time(b) / reps
 
 
+def _pass_entry(ms, bytes_per_px, flop_per_px, hbm):
+    e = {"ms": round(ms, 4), "gpx_s": round(PX_PER_PASS / ms / 1e6, 1),
+         "hbm": round(bytes_per_px * PX_PER_PASS / (ms * 1e-3) / 1e9 / hbm, 3)}
+    if flop_per_px:
+        e["fp32"] = round(flop_per_px * PX_PER_PASS / (ms * 1e-3) / 1e12 / fp32_peak_tflops(), 3)
+    return e
+
+
 def measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g, serve_seconds=SERVE_SECONDS):
-    """Per-pass kernel times of the workload, the FP16-storage variant, and
-    the 8192^2 x 100-sweep Jacobi run (residual every 10 sweeps)."""
+    """Per-pass kernel times of the workload (FP32 and binary16 storage), the
+    8192^2 x 100-sweep Jacobi run (residual every 10 sweeps) and the other
+    workloads.  Returns (results, keep): keep holds the outputs the CPU leg
+    compares with the oracle (binary16 outputs per filter, the Jacobi iterate,
+    sampled batch and served results)."""
     sraw = stream.cuda_stream
     hbm = measured_peaks().get("hbm_gbs") or 6800.0
-    out = {}
+    out, keep = {}, {}
     per = {}
     d_ks = [torch.from_numpy(k).to(dev) for k in ks]
     d_g = torch.from_numpy(g).to(dev)
     for K, dk in zip(DIRECT_K, d_ks):
         ms = _time_stream(torch, stream, lambda: pg.pencil_conv2d_ex(C, H, W, d_img, K, K, dk, d_out[0],
                                                                      pg.PENCIL_F32, 0, sraw), 10)
-        per[f"{K}x{K}"] = {"ms": round(ms, 4), "gpx_s": round(PX_PER_PASS / ms / 1e6, 2),
-                           "hbm_frac": round(8 * PX_PER_PASS / (ms * 1e-3) / 1e9 / hbm, 4),
-                           "fp32_frac": round(2 * K * K * PX_PER_PASS / (ms * 1e-3) / 1e12 / fp32_peak_tflops(), 4)}
+        per[f"{K}x{K}"] = _pass_entry(ms, 8, 2 * K * K, hbm)
     ms = _time_stream(torch, stream, lambda: pg.pencil_conv2d_sep_ex(C, H, W, d_img, 15, d_g, 15, d_g, d_out[0],
                                                                      pg.PENCIL_F32, 0, sraw), 10)
-    per["gauss15-sep"] = {"ms": round(ms, 4), "gpx_s": round(PX_PER_PASS / ms / 1e6, 2),
-                          "hbm_frac": round(8 * PX_PER_PASS / (ms * 1e-3) / 1e9 / hbm, 4)}
+    per["gauss15-sep"] = _pass_entry(ms, 8, 0, hbm)
+    # d_out[0] holds the 3x3 result again, as the timed steps left it
+    pg.pencil_conv2d_ex(C, H, W, d_img, 3, 3, d_ks[0], d_out[0], pg.PENCIL_F32, 0, sraw)
     out["passes_f32"] = per
-    # FP16 storage, same filters
+    # binary16 storage, same filters; each output kept for the precision check
     d16 = d_img.half()
-    o16 = torch.empty_like(d16)
-    per16 = {}
+    per16, o16s = {}, []
     for K, dk in zip(DIRECT_K, d_ks):
+        o16 = torch.empty_like(d16)
         ms = _time_stream(torch, stream, lambda: pg.pencil_conv2d_ex(C, H, W, d16, K, K, dk, o16,
                                                                      pg.PENCIL_F16, 0, sraw), 10)
-        per16[f"{K}x{K}"] = {"ms": round(ms, 4), "gpx_s": round(PX_PER_PASS / ms / 1e6, 2),
-                             "hbm_frac": round(4 * PX_PER_PASS / (ms * 1e-3) / 1e9 / hbm, 4)}
+        per16[f"{K}x{K}"] = _pass_entry(ms, 4, 2 * K * K, hbm)
+        o16s.append(o16)
+    o16 = torch.empty_like(d16)
     ms = _time_stream(torch, stream, lambda: pg.pencil_conv2d_sep_ex(C, H, W, d16, 15, d_g, 15, d_g, o16,
                                                                      pg.PENCIL_F16, 0, sraw), 10)
-    per16["gauss15-sep"] = {"ms": round(ms, 4), "gpx_s": round(PX_PER_PASS / ms / 1e6, 2),
-                            "hbm_frac": round(4 * PX_PER_PASS / (ms * 1e-3) / 1e9 / hbm, 4)}
+    per16["gauss15-sep"] = _pass_entry(ms, 4, 0, hbm)
+    o16s.append(o16)
     out["passes_f16"] = per16
-    del d16, o16
+    keep["f16"] = (d16, o16s)
     # Jacobi 8192^2, 100 sweeps, residual after every 10 sweeps
     n = 8192
-    u0 = torch.from_numpy(synth.jacobi_init_f32(synth.SEEDS["jacobi8192"], n, n)).to(dev)
+    u0h = synth.jacobi_init_f32(synth.SEEDS["jacobi8192"], n, n)
+    u0 = torch.from_numpy(u0h).to(dev)
     u = u0.clone()
     wsb = pg.pencil_jacobi2d_workspace_size(n, n)
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
@@ -322,59 +377,82 @@ def measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g, serve_seconds=SE
         ms_copy = _time_stream(torch, stream, lambda: u.copy_(u0), 3)
         ms = _time_stream(torch, stream, run, 3) - ms_copy
         pts = (n - 2) * (n - 2) * 100
-        jac[f"temporal_t={t or 'auto'}"] = {
-            "ms": round(ms, 3), "gpt_sweeps_s": round(pts / ms / 1e6, 2),
-            "effective_hbm_frac": round(8 * n * n * 100 / (ms * 1e-3) / 1e9 / hbm, 4)}
-    jac["residuals"] = [float(x) for x in res.cpu()]
+        jac[f"t{t}" if t else "auto"] = {
+            "ms": round(ms, 3), "gpt_sweeps_s": round(pts / ms / 1e6, 1),
+            "hbm_effective": round(8 * n * n * 100 / (ms * 1e-3) / 1e9 / hbm, 3)}
+    jac["note"] = "t1: one sweep per pass; auto: the library's temporal tiling; hbm on 8 B per point-sweep"
     out["jacobi_8192x8192_100sweeps"] = jac
+    keep["jacobi"] = (u0h, u, res)
     # red-black SOR, omega 1.9, in place: per sweep each point is read twice and
     # its float4 written twice (16 B per point-sweep)
+    u2 = torch.empty_like(u0)
+    res2 = torch.empty(10, dtype=torch.float64, device=dev)
     wsr = pg.pencil_rbsor2d_workspace_size(n, n)
+    if wsr > wsb:
+        ws = torch.empty(wsr, dtype=torch.uint8, device=dev)
 
     def sor():
-        u.copy_(u0)
-        pg.pencil_rbsor2d_ex(n, n, u, 100, 1.9, 10, res, ws, wsr, sraw)
-    ms_copy = _time_stream(torch, stream, lambda: u.copy_(u0), 3)
+        u2.copy_(u0)
+        pg.pencil_rbsor2d_ex(n, n, u2, 100, 1.9, 10, res2, ws, wsr, sraw)
+    ms_copy = _time_stream(torch, stream, lambda: u2.copy_(u0), 3)
     ms = _time_stream(torch, stream, sor, 3) - ms_copy
     out["rbsor_8192x8192_100sweeps"] = {
-        "ms": round(ms, 3), "gpt_sweeps_s": round((n - 2) * (n - 2) * 100 / ms / 1e6, 2),
-        "hbm_frac_16B_per_point_sweep": round(16 * n * n * 100 / (ms * 1e-3) / 1e9 / hbm, 4),
-        "residuals": [float(x) for x in res.cpu()]}
-    del u0, u, ws
-    out["plain_512x512_5x5"] = measure_small(torch, pg, dev, stream)
-    out["batched_512"] = measure_batched(torch, pg, dev, stream)
+        "ms": round(ms, 3), "gpt_sweeps_s": round((n - 2) * (n - 2) * 100 / ms / 1e6, 1),
+        "hbm_frac_16B_per_point_sweep": round(16 * n * n * 100 / (ms * 1e-3) / 1e9 / hbm, 3),
+        "residuals": [float(f"{x:.6g}") for x in res2.cpu()]}
+    del u0, u2, ws
+    out["plain_512x512_5x5"], keep["plain512"] = measure_small(torch, pg, dev, stream)
     out["op2_inc_2048x2048_cells"] = measure_op2(torch, pg, dev, stream)
     out["chain_8192x8192x3"] = measure_chain(torch, pg, dev, stream, d_img, d_out)
-    out["serving"] = measure_serving(torch, pg, dev, serve_seconds)
-    return out
+    # the chain runs overwrote d_out[0]: the 3x3 result again for the precision check
+    pg.pencil_conv2d_ex(C, H, W, d_img, 3, 3, d_ks[0], d_out[0], pg.PENCIL_F32, 0, sraw)
+    out["batched_512"], keep["batch"] = measure_batched(torch, pg, dev, stream)
+    serving, keep["served"] = measure_serving(torch, pg, dev, serve_seconds)
+    out["serving_saturation_40000_req_s"] = serving.pop("saturation_40000_req_s")
+    out["serving_2000_req_s"] = serving["2000_req_s"]
+    torch.cuda.synchronize(dev)
+    return out, keep
 
+
+SERVE_SAMPLE_EVERY = 97  # every 97th request of the 2000 req/s replay is kept and checked
+
+
+def _serve_brief(st):
+    d = st.summary()
+    return {k: d[k] for k in ("requests", "rejected", "p50_ms", "p99_ms", "max_ms", "gpx_s", "req_s", "mean_wave",
+                              "peak_inflight", "peak_arena_mib")}
 
 
 def measure_serving(torch, pg, dev, seconds):
     """Open-loop Poisson replay, FP16 storage, sides log-uniform [128, 4096],
     odd filter sides 3..15, 8 GiB arena budget: continuous batching against
     one launch per request, at 2000 req/s (latency) and at a saturating rate
-    (throughput)."""
+    (throughput).  Returns (results, kept): the served results of every 97th
+    request of the 2000 req/s replay, with what the CPU leg needs to check
+    them (their pinned buffers are allocated before the replay starts)."""
     from paper_1302_5586_gb300 import serve, tune
 
-    res = {}
+    res, kept = {}, None
     seed = synth.SEEDS["serve"]
     for label, rate, dur in (("2000_req_s", 2000.0, seconds), ("saturation_40000_req_s", 40000.0, 0.5)):
         tr = serve.make_trace(seed, rate, dur)
         pool = serve.host_pool(tr, pg.PENCIL_F16, seed + 1)
         bank = torch.from_numpy(tr.filters).to(dev)
         srv = serve.Server(dtype=pg.PENCIL_F16, budget_bytes=8 << 30, streams=4, max_wave=64, max_inflight=256)
+        sample = range(0, len(tr.requests), SERVE_SAMPLE_EVERY) if label == "2000_req_s" else ()
         try:
             srv.set_variants(tune.cached_variants(pg.PENCIL_F16))
-            served, _ = srv.run(tr, pool, bank, mode="served")
+            served, outs = srv.run(tr, pool, bank, mode="served", keep_ids=sample)
             plain, _ = srv.run(tr, pool, bank, mode="plain")
         finally:
             srv.close()
         res[label] = {"offered_req_s": rate, "seconds": dur,
                       "offered_gpx_s": round(sum(r.h * r.w for r in tr.requests) / dur / 1e9, 3),
-                      "served": served.summary(), "plain": plain.summary()}
-        del pool, bank
-    return res
+                      "served": _serve_brief(served), "plain": _serve_brief(plain)}
+        if sample:
+            kept = {"trace": tr, "pool": pool, "outputs": {i: outs[i] for i in sample if outs[i] is not None}}
+        del bank
+    return res, kept
 
 
 def measure_chain(torch, pg, dev, stream, d_img, d_out):
@@ -439,8 +517,10 @@ def measure_small(torch, pg, dev, stream):
     around 200 back-to-back launches, median of 5) and host wall time of the
     synchronous plain call on device pointers."""
     n, K = 512, 5
-    x = torch.from_numpy(synth.image_f32(synth.SEEDS["conv512"], 1, n, n)).to(dev)
-    k = torch.from_numpy(synth.filter_f32(synth.SEEDS["conv512"] + 1, K, K)).to(dev)
+    xh = synth.image_f32(synth.SEEDS["conv512"], 1, n, n)
+    kh = synth.filter_f32(synth.SEEDS["conv512"] + 1, K, K)
+    x = torch.from_numpy(xh).to(dev)
+    k = torch.from_numpy(kh).to(dev)
     y = torch.empty_like(x)
     sraw = stream.cuda_stream
     reps = []
@@ -479,11 +559,12 @@ def measure_small(torch, pg, dev, stream):
     call_us = (time.perf_counter() - t) / 500 * 1e6
     px = n * n
     best = graph_us if isinstance(graph_us, float) else us
-    return {"device_us_per_launch": round(best, 2), "gpx_s": round(px / best / 1e3, 2),
-            "l2_resident_gb_s": round(8 * px / best / 1e3, 1), "graph_replay_us": graph_us if not isinstance(
-                graph_us, float) else round(graph_us, 2), "stream_launch_us": round(us, 2),
-            "plain_call_us": round(call_us, 2),
-            "note": "fits in L2: launch-latency bound; GB/s is L2-resident, not HBM"}
+    return ({"device_us_per_launch": round(best, 2), "gpx_s": round(px / best / 1e3, 2),
+             "l2_resident_gb_s": round(8 * px / best / 1e3, 1), "graph_replay_us": graph_us if not isinstance(
+                 graph_us, float) else round(graph_us, 2), "stream_launch_us": round(us, 2),
+             "plain_call_us": round(call_us, 2),
+             "note": "fits in L2: launch-latency bound; GB/s is L2-resident, not HBM"},
+            (xh, kh, y))
 
 
 def measure_batched(torch, pg, dev, stream):
@@ -498,6 +579,7 @@ def measure_batched(torch, pg, dev, stream):
     fp32 = fp32_peak_tflops() * 1e12
     px = int(np.sum(h.astype(np.int64) * w))
     res = {"images": 512, "pixels": px, "mean_flop_per_px": round(float(np.sum(2.0 * k * k * h * w) / px), 1)}
+    keep = {}
     for dtype, name, esz in ((pg.PENCIL_F32, "f32", 4), (pg.PENCIL_F16, "f16", 2)):
         items = []
         for i in range(512):
@@ -512,6 +594,9 @@ def measure_batched(torch, pg, dev, stream):
             chosen = tune.autotune(plan, dtype, items, reps=3)
             imgs = pg.make_images(items)
             ms_b = _time_stream(torch, stream, lambda: pg.pencil_batch_run(plan, imgs, stream.cuda_stream), 5)
+            # the batched results of every 8th image, for the precision check
+            keep[name] = [(i, items[i][0].cpu().numpy(), items[i][2].cpu().numpy().reshape(items[i][5], items[i][5]),
+                           items[i][1].cpu().numpy()) for i in range(0, 512, 8)]
 
             def per_image():
                 for it in items:
@@ -526,7 +611,7 @@ def measure_batched(torch, pg, dev, stream):
                      "roofline_ms": round(roof, 3), "frac_of_roofline": round(roof / ms_b, 4),
                      "variants": {str(a): v for a, (v, _) in chosen.items()}}
         del items
-    return res
+    return res, keep
 
 
 def measure_e2e(torch, pg, img, ks, g, steps):
@@ -558,30 +643,159 @@ def measure_e2e(torch, pg, img, ks, g, steps):
 
 
 # ------------------------------------------------------------- CPU oracle
-def _oracle_band(oracle, img, ks, g, rows, r0):
-    """Oracle over rows [r0, r0+rows) of all channels for every pass of the step."""
+def _oracle_band(oracle, img, ks, g, rows, r0, keep=False):
+    """Oracle over rows [r0, r0+rows) of all channels for every pass of the
+    step: each pass reads its halo rows too (cut at the image edges, where the
+    sub-image's clamp is the image's), so the band rows are exact.  Returns the
+    seconds taken and, with keep, each pass's band rows."""
+    outs = []
     t = time.perf_counter()
     for K, k in zip(DIRECT_K, ks):
         a = K // 2
         lo, hi = max(0, r0 - a), min(H, r0 + rows + a)
-        oracle.conv2d(img[:, lo:hi, :], k, want_bound=False)
+        o, _ = oracle.conv2d(img[:, lo:hi, :], k, want_bound=False)
+        if keep:
+            outs.append(o[:, r0 - lo:r0 - lo + rows, :])
     lo, hi = max(0, r0 - GAUSS_R), min(H, r0 + rows + GAUSS_R)
-    oracle.conv2d_sep(img[:, lo:hi, :], g, g, want_bound=False)
-    return time.perf_counter() - t
+    o, _ = oracle.conv2d_sep(img[:, lo:hi, :], g, g, want_bound=False)
+    if keep:
+        outs.append(o[:, r0 - lo:r0 - lo + rows, :])
+    dt = time.perf_counter() - t
+    return (dt, outs) if keep else dt
 
 
-def cpu_baseline(img, ks, g, budget_s=15.0):
+def _ratio_max(got, want, bound):
+    """max |got - want| / bound over the elements (0 where both are 0)."""
+    got = np.asarray(got, dtype=np.float64)
+    err = np.abs(got - want)
+    return float(np.max(np.where(err == 0, 0.0, err / np.maximum(bound, 1e-300)))) if err.size else 0.0
+
+
+def _edge_and_random_points(seed, c, h, w, n):
+    """n random (ch, i, j) points plus every pixel of the outer rows and
+    columns of channel 0 (where the clamp acts)."""
+    r = np.random.default_rng(seed)
+    pts = [np.stack([r.integers(0, c, n), r.integers(0, h, n), r.integers(0, w, n)], axis=1)]
+    for i in (0, h - 1):
+        pts.append(np.stack([np.zeros(w, np.int64), np.full(w, i), np.arange(w)], axis=1))
+    for j in (0, w - 1):
+        pts.append(np.stack([np.zeros(h, np.int64), np.arange(h), np.full(h, j)], axis=1))
+    return np.concatenate(pts).astype(np.int64)
+
+
+def _gather(t, pts):
+    import torch
+    p = torch.from_numpy(pts).to(t.device)
+    return t[p[:, 0], p[:, 1], p[:, 2]].double().cpu().numpy()
+
+
+def cpu_baseline(torch, img, ks, g, d_out=None, keep=None, budget_s=15.0):
+    """The CPU leg: the FP64 oracle as it stands, on all host cores.
+
+    (1) Timed: all four passes over a band of rows of the benchmark image,
+        sized to about budget_s seconds -- the cpu_baseline value.
+    (2) Each result's error: that band's oracle rows and the oracle at every
+        edge pixel of channel 0 plus 4096 random pixels, against the GPU
+        outputs of this run; then the oracle on bounded samples of the other
+        workloads (a band of the binary16 image, the whole Jacobi grid after
+        100 sweeps, every 8th batched image, every 97th served request, the
+        512 x 512 case), each against the GPU's result.
+    Returns (cpu_baseline, precision)."""
     import oracle
 
     probe = 32
     _oracle_band(oracle, img, ks, g, 8, 0)  # start the thread pool
-    t_probe = _oracle_band(oracle, img, ks, g, probe, 4096)
+    t_probe = _oracle_band(oracle, img, ks, g, probe, H // 2)
     rows = int(max(probe, min(H, probe * budget_s / max(t_probe, 1e-6))))
-    dt = _oracle_band(oracle, img, ks, g, rows, 4096 - rows // 2 if rows < H else 0)
+    r0 = H // 2 - rows // 2 if rows < H else 0
+    got_band = _oracle_band(oracle, img, ks, g, rows, r0, keep=d_out is not None)
+    dt, bands = got_band if d_out is not None else (got_band, None)
     px = rows * W * C * PASSES
-    return {"value": round(px / dt / 1e9, 6), "unit": "Gpixel/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"FP64 oracle, all 4 passes over rows {rows} of 8192 (x3 channels) of the same image, {dt:.1f} s"}
+    cpu = {"value": round(px / dt / 1e9, 6), "unit": "Gpixel/s", "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"FP64 oracle, all 4 passes over rows {rows} of 8192 (x3 channels) of the same image, "
+                     f"{dt:.1f} s"}
+    if d_out is None:
+        return cpu, None
+    keep = keep or {}
+    t0 = time.perf_counter()
+    # every pixel and weight of the benchmark is >= 0, so sum |k||x| is the value itself
+    assert img.min() >= 0 and all(k.min() >= 0 for k in ks) and g.min() >= 0
+    names = [f"{K}x{K}" for K in DIRECT_K] + ["gauss15-sep"]
+    pts = _edge_and_random_points(5, C, H, W, 4096)
+    f32 = {}
+    for n, name in enumerate(names):
+        got = d_out[n][:, r0:r0 + rows, :].cpu().numpy()
+        r = max(_ratio_max(got[:, i:i + 512], bands[n][:, i:i + 512], bands[n][:, i:i + 512])
+                for i in range(0, rows, 512))
+        if n < len(DIRECT_K):
+            want, bound = oracle.conv2d_points(img, ks[n], pts)
+        else:
+            want, bound = oracle.conv2d_sep_points(img, g, g, pts)
+        f32[name] = max(r, _ratio_max(_gather(d_out[n], pts), want, bound))
+    prec = {"tol": {"f32": TOL_F32, "f16": TOL_F16, "jacobi_abs": TOL_JACOBI},
+            "conv_f32_err_over_bound": {k: float(f"{v:.3g}") for k, v in f32.items()}}
+    worst = max(f32.values()) / TOL_F32
+    if keep.get("f16"):
+        d16, o16s = keep["f16"]
+        x16 = d16.cpu().numpy()
+        rows16 = min(256, H // 2)
+        r16 = H // 2 - rows16 // 2
+        f16 = {}
+        for n, (name, o16) in enumerate(zip(names, o16s)):
+            a = GAUSS_R if n == len(DIRECT_K) else DIRECT_K[n] // 2
+            sub = x16[:, r16 - a:r16 + rows16 + a, :]
+            if n < len(DIRECT_K):
+                want, bound = oracle.conv2d(sub, ks[n])
+                pw, pb = oracle.conv2d_points(x16, ks[n], pts)
+            else:
+                want, bound = oracle.conv2d_sep(sub, g, g)
+                pw, pb = oracle.conv2d_sep_points(x16, g, g, pts)
+            got = o16[:, r16:r16 + rows16, :].cpu().numpy()
+            f16[name] = max(_ratio_max(got, want[:, a:a + rows16], bound[:, a:a + rows16]),
+                            _ratio_max(_gather(o16, pts), pw, pb))
+        prec["conv_f16_err_over_bound"] = {k: float(f"{v:.3g}") for k, v in f16.items()}
+        worst = max(worst, max(f16.values()) / TOL_F16)
+    if keep.get("plain512"):
+        xh, kh, y = keep["plain512"]
+        want, bound = oracle.conv2d(xh, kh)
+        r = _ratio_max(y.cpu().numpy().reshape(want.shape), want, bound)
+        prec["plain_512x512_5x5_err_over_bound"] = float(f"{r:.3g}")
+        worst = max(worst, r / TOL_F32)
+    if keep.get("batch"):
+        for name, tol in (("f32", TOL_F32), ("f16", TOL_F16)):
+            r = 0.0
+            for i, x, k, y in keep["batch"].get(name, []):
+                hh, ww = x.shape[-2:]
+                x, y = x.reshape(hh, ww), y.reshape(hh, ww)
+                p = _edge_and_random_points(i, 1, hh, ww, 1024)
+                want, bound = oracle.conv2d_points(x, k, p)
+                r = max(r, _ratio_max(y[p[:, 1], p[:, 2]], want, bound))
+            prec[f"batched_{name}_err_over_bound"] = float(f"{r:.3g}")
+            worst = max(worst, r / tol)
+    if keep.get("served"):
+        sv = keep["served"]
+        tr, pool, r = sv["trace"], sv["pool"], 0.0
+        for rid, y in sv["outputs"].items():
+            q = tr.requests[rid]
+            x = pool[q.src:q.src + q.h * q.w].numpy().reshape(1, q.h, q.w)
+            k = tr.filters[q.filt:q.filt + q.ks * q.ks].reshape(q.ks, q.ks)
+            p = _edge_and_random_points(rid, 1, q.h, q.w, 256)
+            want, bound = oracle.conv2d_points(x, k, p)
+            r = max(r, _ratio_max(y.numpy()[p[:, 1], p[:, 2]], want, bound))
+        prec["served_f16_err_over_bound"] = float(f"{r:.3g}")
+        prec["served_checked"] = len(sv["outputs"])
+        worst = max(worst, r / TOL_F16)
+    if keep.get("jacobi"):
+        u0h, u, res = keep["jacobi"]
+        u_ref, res_ref = oracle.jacobi2d(u0h, 100, 10)
+        du = float(np.max(np.abs(u.cpu().numpy().astype(np.float64) - u_ref)))
+        rr = float(np.max(np.abs(res.cpu().numpy() - res_ref) / res_ref))
+        prec["jacobi_max_abs_du"] = float(f"{du:.3g}")
+        prec["jacobi_residual_rel_err"] = float(f"{rr:.3g}")
+        worst = max(worst, du / TOL_JACOBI)
+    prec["worst_err_over_tol"] = float(f"{worst:.3g}")
+    prec["oracle_check_s"] = round(time.perf_counter() - t0, 1)
+    return cpu, prec
 
 
 def run_reference(args, rank, world):
@@ -611,7 +825,7 @@ def run_reference(args, rank, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total / args.steps * 1e3, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config({"parallelism": "host cores (OpenMP)"}),
+            "config": config(),
             "cpu_baseline": {"value": round(value, 6), "unit": "Gpixel/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 6), "unit": "Gpixel/s", "h2d_bytes_per_step": 0,

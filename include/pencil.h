@@ -305,14 +305,17 @@ int pencil_residual2d(int h, int w, const float *u, double *res_out, void *works
  * Same sweeps, residuals and results as pencil_jacobi2d_ex.  u and res_out
  * are caller-owned device memory.  The first call on each device looks up
  * the array's device address (with that device current) and caches it, so
- * make that first call before any stream capture.  All calls on a device share
+ * make that first call before any stream capture; after a device reset the
+ * next call finds a new context and looks the address up again, so that
+ * call too belongs before any capture.  All calls on a device share
  * the one array, which keeps the previous call's contents (every element a
  * call reads it has first written, so nothing needs clearing): calls whose
  * work overlaps on the GPU -- on different streams or from different host
  * threads without ordering -- race and corrupt each other.
- * Errors: ARG, NULL, PTR, NOMEM (the grid needs more scratch than
- * PENCIL_NOALLOC_SCRATCH_BYTES: h*w above about 4.4 million points; every grid
- * up to 2048 x 2048 fits), CUDA. */
+ * Errors: ARG, UNSUPPORTED (h above PENCIL_MAX_ROWS, as for every _ex call),
+ * NULL, PTR, ALIAS (res_out overlaps u), NOMEM (the grid needs more scratch
+ * than PENCIL_NOALLOC_SCRATCH_BYTES: h*w above about 4.4 million points; every
+ * grid up to 2048 x 2048 fits), CUDA. */
 int pencil_jacobi2d_noalloc(int h, int w, float *u, int iters, int check_every, double *res_out,
                             int temporal_t, void *stream);
 

@@ -27,6 +27,9 @@
 #include <mutex>
 #include <utility>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "internal.cuh"
 
 namespace pencil {
@@ -779,20 +782,50 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[kMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kMaxDevices] = {};
+
+// Unique id of the calling thread's current context (0 if none is current or
+// the driver does not offer the query).  Ids are never reused, so a primary
+// context torn down and created again (cudaDeviceReset) gets a new one.
+unsigned long long current_context_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_ctx = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_ctx = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+        cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_ctx || !get_id || get_ctx(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 // Device address of the static scratch on the current device, or the failing
-// CUDA status.
+// CUDA status.  Looked up once per device and context: after a device reset
+// the module is loaded again and the array may sit elsewhere, so a changed
+// context id makes the next call look it up again.
 cudaError_t noalloc_scratch(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_noalloc_ptr[dev] || ctx == 0 || ctx != g_noalloc_ctx[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_noalloc_ptr[dev] = p;
+        g_noalloc_ctx[dev] = current_context_id();  // the lookup made the primary context current
     }
     *out = g_noalloc_ptr[dev];
     return cudaSuccess;
@@ -812,6 +845,7 @@ extern "C" int pencil_jacobi2d_noalloc(int h, int w, float *u, int iters, int ch
                                        double *res_out, int temporal_t, void *stream) {
     if (h <= 0 || w <= 0 || iters < 0 || check_every < 0 || temporal_t < 0) return PENCIL_ERR_ARG;
     if ((int64_t)h * (int64_t)w > ((int64_t)1 << 40)) return PENCIL_ERR_ARG;
+    if (h > PENCIL_MAX_ROWS) return PENCIL_ERR_UNSUPPORTED;  // the row limit of every _ex call
     if (!u) return PENCIL_ERR_NULL;
     const int nres = check_every > 0 ? iters / check_every : 0;
     if (nres > 0 && !res_out) return PENCIL_ERR_NULL;

@@ -255,17 +255,24 @@ class Server:
         return self.pool[off:off + n * self.esz].view(self.tdtype)
 
     def run(self, trace: Trace, host_pool, filters_dev, mode: str = "served", keep_outputs: bool = False,
-            sink_bytes: int = 1 << 29, deadline_ms: float | None = None, cancel=()) -> tuple:
+            sink_bytes: int = 1 << 29, deadline_ms: float | None = None, cancel=(), keep_ids=()) -> tuple:
         """Replay `trace` open-loop.  host_pool: pinned host tensor of the
         storage dtype (trace.pool_elems elements); filters_dev: device FP32
         tensor holding trace.filters.  Requests still queued `deadline_ms`
         after their arrival, and those whose ids are in `cancel`, are dropped
-        unrun (latency NaN).  Returns (Stats, outputs or None)."""
+        unrun (latency NaN).  keep_outputs keeps every result; keep_ids keeps
+        only those requests' results, in pinned buffers allocated before the
+        replay starts (so checking a sample costs the replay no allocation).
+        Returns (Stats, outputs: a list with None for results not kept, or
+        None when nothing is kept)."""
         torch = self.torch
         reqs = trace.requests
         n = len(reqs)
         lat = np.full(n, np.nan)
-        outputs = [None] * n if keep_outputs else None
+        outputs = [None] * n if (keep_outputs or keep_ids) else None
+        for rid in keep_ids if not keep_outputs else ():
+            r = reqs[int(rid)]
+            outputs[r.rid] = torch.empty(r.h * r.w, dtype=self.tdtype, pin_memory=True)
         largest = max((r.h * r.w for r in reqs), default=1)
         sink = None if keep_outputs else torch.empty(max(sink_bytes // self.esz, largest), dtype=self.tdtype,
                                                      pin_memory=True)
@@ -332,6 +339,8 @@ class Server:
                         if keep_outputs:
                             outputs[r.rid] = torch.empty(hw, dtype=self.tdtype, pin_memory=True)
                             outputs[r.rid].copy_(src, non_blocking=True)
+                        elif outputs is not None and outputs[r.rid] is not None:
+                            outputs[r.rid].copy_(src, non_blocking=True)
                         else:
                             if sink_pos + hw > sink.numel():
                                 sink_pos = 0
@@ -354,7 +363,7 @@ class Server:
         wall = (last_done - t0) - first
         st = Stats(mode, n, adm.rejected, pix, wall, lat, waves, peak_inflight, peak_arena, adm.cancelled,
                    adm.expired)
-        if keep_outputs:
+        if outputs is not None:
             outputs = [o.view(r.h, r.w) if o is not None else None for o, r in zip(outputs, reqs)]
         return st, outputs
 

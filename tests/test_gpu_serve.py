@@ -63,3 +63,54 @@ def test_admission_waits_for_memory_and_rejects_what_never_fits():
     assert np.all(np.isfinite(st.latency_ms[:-1]))
     assert 0 < st.peak_arena_bytes <= budget
     assert st.peak_inflight < len(tr.requests) - 1  # memory, not the slot limit, held requests back
+
+
+def test_served_mix_at_full_request_sizes_against_alone_runs_and_the_oracle():
+    """The serving workload's request shapes (binary16 images, sides
+    log-uniform in [128, 4096], odd filter sides 3..15) arriving ten times
+    faster than the 2000 req/s stream, so that waves hold many requests: every
+    served result is the same bits as its request run alone through
+    pencil_conv2d_ex, in the served mix and in the plain replay, and every 97th
+    request is checked against the FP64 oracle (on its binary16 input) at 1024
+    sampled pixels plus the four corners, within 2^-10 * sum |k||x| (the
+    floating-point reproducibility point of Sec. 3.1)."""
+    import oracle
+    from gpu_util import sample_points
+
+    tr = serve.make_trace(2024, rate=20000.0, duration=0.016)
+    n = len(tr.requests)
+    assert 250 <= n <= 450
+    sides = np.array([(r.h, r.w) for r in tr.requests])
+    assert sides.min() >= 128 and sides.max() <= 4096 and sides.max() > 2048
+    assert {r.ks for r in tr.requests} == set(range(3, 16, 2))
+    pool = serve.host_pool(tr, pg.PENCIL_F16, 2025)
+    bank = torch.from_numpy(tr.filters).to(dev())
+    srv = serve.Server(dtype=pg.PENCIL_F16, budget_bytes=8 << 30, streams=4, max_wave=64, max_inflight=256)
+    try:
+        st, outs = srv.run(tr, pool, bank, mode="served", keep_outputs=True)
+        st2, outs2 = srv.run(tr, pool, bank, mode="plain", keep_outputs=True)
+        assert pg.pencil_arena_free_bytes(srv.arena) == 8 << 30
+    finally:
+        srv.close()
+    assert st.rejected == 0 and np.all(np.isfinite(st.latency_ms))
+    assert st.waves < n / 2                       # waves of many requests
+    assert st2.waves == n
+    worst = 0.0
+    for r in tr.requests:
+        ref = alone(r, pool, tr.filters, pg.PENCIL_F16)
+        assert torch.equal(outs[r.rid].view(torch.int16), ref.view(torch.int16)), r
+        assert torch.equal(outs2[r.rid].view(torch.int16), ref.view(torch.int16)), r
+        if r.rid % 97:
+            continue
+        hw = r.h * r.w
+        x = pool[r.src:r.src + hw].numpy().reshape(1, r.h, r.w)
+        k = tr.filters[r.filt:r.filt + r.ks * r.ks].reshape(r.ks, r.ks)
+        pts = sample_points(r.rid, 1, r.h, r.w, 1024, borders=False)
+        corners = np.array([[0, 0, 0], [0, 0, r.w - 1], [0, r.h - 1, 0], [0, r.h - 1, r.w - 1]])
+        pts = np.concatenate([pts, corners])
+        want, bound = oracle.conv2d_points(x, k, pts)
+        got = outs[r.rid].numpy().astype(np.float64)[pts[:, 1], pts[:, 2]]
+        ratio = np.abs(got - want) / np.maximum(bound, 1e-300)
+        assert np.all(ratio <= 2.0 ** -10), (r, float(ratio.max()))
+        worst = max(worst, float(ratio.max()))
+    assert 0.0 < worst <= 2.0 ** -10

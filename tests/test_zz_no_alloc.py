@@ -61,3 +61,24 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
     ok = torch.zeros(2048, 2048, device=dev())
     pg.pencil_jacobi2d_noalloc(2048, 2048, ok, 2, 0, None)
     torch.cuda.synchronize()
+
+
+def test_noalloc_applies_the_row_limit_of_the_workspace_entry_point():
+    # a tall, narrow grid fits the scratch but has more rows than a launch
+    # can cover: the same UNSUPPORTED as pencil_jacobi2d_ex, before any launch
+    h, w = pg.PENCIL_MAX_ROWS + 1, 3
+    assert pg.pencil_jacobi2d_workspace_size(h, w) <= pg.PENCIL_NOALLOC_SCRATCH_BYTES
+    u = torch.zeros(h, w, device=dev())
+    for call in (lambda: pg.pencil_jacobi2d_noalloc(h, w, u, 1, 0, None),
+                 lambda: pg.pencil_jacobi2d_ex(h, w, u, 1, 0, None, u, 1 << 30, 0)):
+        with pytest.raises(pg.PencilError) as e:
+            call()
+        assert e.value.name == "PENCIL_ERR_UNSUPPORTED"
+
+
+def test_noalloc_rejects_residuals_inside_the_grid():
+    u = torch.zeros(64 * 64 + 64, device=dev())
+    res = u[64 * 64 - 8:].view(torch.float64)  # overlaps the grid's last elements
+    with pytest.raises(pg.PencilError) as e:
+        pg.pencil_jacobi2d_noalloc(64, 64, u, 10, 5, res)
+    assert e.value.name == "PENCIL_ERR_ALIAS"
