@@ -75,6 +75,12 @@ def lib():
     L.oracle_conv2d_points.restype = i32
     L.oracle_conv2d_sep_points.argtypes = [i64, i64, i64, vp, i32, i32, vp, i32, vp, i64, vp, dp, dp]
     L.oracle_conv2d_sep_points.restype = i32
+    L.oracle_conv2d_hwc.argtypes = [i64, i64, i64, vp, i32, i32, i32, vp, dp, dp, i32]
+    L.oracle_conv2d_hwc.restype = i32
+    L.oracle_conv2d_sep_hwc.argtypes = [i64, i64, i64, vp, i32, i32, vp, i32, vp, dp, dp, i32]
+    L.oracle_conv2d_sep_hwc.restype = i32
+    L.oracle_conv2d_hwc_points.argtypes = [i64, i64, i64, vp, i32, i32, i32, vp, i64, vp, dp, dp]
+    L.oracle_conv2d_hwc_points.restype = i32
     L.oracle_residual2d_f64.argtypes = [i64, i64, vp]
     L.oracle_residual2d_f64.restype = ctypes.c_double
     L.oracle_residual2d_f32.argtypes = [i64, i64, vp]
@@ -198,6 +204,69 @@ def conv2d_sep_points(img: np.ndarray, gx: np.ndarray, gy: np.ndarray, pts: np.n
                                         p.shape[0], _ptr(p), _ptr(out), _ptr(bound))
     if rc != 0:
         raise ValueError("oracle_conv2d_sep_points rejected its arguments")
+    return out, bound
+
+
+def _image_hwc(x: np.ndarray):
+    """(array as [h][w][c] contiguous, dtype code)."""
+    if x.dtype == np.float16:
+        x = np.ascontiguousarray(x).view(np.uint16)
+        dt = DT_F16
+    elif x.dtype == np.uint16:
+        dt = DT_F16
+    else:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        dt = DT_F32
+    x = np.ascontiguousarray(x)
+    if x.ndim != 3:
+        raise ValueError("interleaved image must be [h][w][c]")
+    return x, dt
+
+
+def conv2d_hwc(img: np.ndarray, k: np.ndarray, want_bound: bool = True, border: str = "clamp"):
+    """Correlation of every channel of an interleaved [h][w][c] image with k
+    (FP64) under a border mode.  Returns (out, bound), both [h][w][c]."""
+    x, dt = _image_hwc(img)
+    kk = np.ascontiguousarray(k, dtype=np.float32)
+    h, w, c = x.shape
+    kh, kw = kk.shape
+    out = np.empty((h, w, c), dtype=np.float64)
+    bound = np.empty((h, w, c), dtype=np.float64) if want_bound else None
+    rc = lib().oracle_conv2d_hwc(c, h, w, _ptr(x), dt, kh, kw, _ptr(kk), _ptr(out), _ptr(bound), BORDER[border])
+    if rc != 0:
+        raise ValueError("oracle_conv2d_hwc rejected its arguments")
+    return out, bound
+
+
+def conv2d_sep_hwc(img: np.ndarray, gx: np.ndarray, gy: np.ndarray, want_bound: bool = True,
+                   border: str = "clamp"):
+    """Separable weights outer(gy, gx) on an interleaved [h][w][c] image (FP64)."""
+    x, dt = _image_hwc(img)
+    gx = np.ascontiguousarray(gx, dtype=np.float32).ravel()
+    gy = np.ascontiguousarray(gy, dtype=np.float32).ravel()
+    h, w, c = x.shape
+    out = np.empty((h, w, c), dtype=np.float64)
+    bound = np.empty((h, w, c), dtype=np.float64) if want_bound else None
+    rc = lib().oracle_conv2d_sep_hwc(c, h, w, _ptr(x), dt, gx.size, _ptr(gx), gy.size, _ptr(gy), _ptr(out),
+                                     _ptr(bound), BORDER[border])
+    if rc != 0:
+        raise ValueError("oracle_conv2d_sep_hwc rejected its arguments")
+    return out, bound
+
+
+def conv2d_hwc_points(img: np.ndarray, k: np.ndarray, pts: np.ndarray):
+    """The interleaved correlation (clamp-to-edge) at sampled (ch, i, j) points: (out, bound)."""
+    x, dt = _image_hwc(img)
+    kk = np.ascontiguousarray(k, dtype=np.float32)
+    p = np.ascontiguousarray(pts, dtype=np.int64).reshape(-1, 3)
+    h, w, c = x.shape
+    kh, kw = kk.shape
+    out = np.empty(p.shape[0], dtype=np.float64)
+    bound = np.empty(p.shape[0], dtype=np.float64)
+    rc = lib().oracle_conv2d_hwc_points(c, h, w, _ptr(x), dt, kh, kw, _ptr(kk), p.shape[0], _ptr(p),
+                                        _ptr(out), _ptr(bound))
+    if rc != 0:
+        raise ValueError("oracle_conv2d_hwc_points rejected its arguments")
     return out, bound
 
 

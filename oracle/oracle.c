@@ -280,6 +280,93 @@ int oracle_conv2d_sep_points(int64_t nc, int64_t h, int64_t w, const void *in, i
     return bad ? -1 : 0;
 }
 
+/* ------------------------------------------------- interleaved [h][w][c] */
+
+/* The interleaved layout image DSLs hand over (pixels of nc channels side by
+ * side, Sec. 1): channel ch of pixel (i, j) is element (i*w + j)*nc + ch.  The
+ * definition is the planar one with that address: each channel is correlated
+ * with k on its own, and the border mode acts on pixel rows and columns. */
+static void conv_pixel_hwc(int64_t nc, int64_t h, int64_t w, const void *in, int dtype, int64_t ch,
+                           int kh, int kw, const double *k, int64_t i, int64_t j,
+                           double *out, double *bound, int mode)
+{
+    const int ah = kh / 2, aw = kw / 2;
+    double s = 0.0, b = 0.0;
+    for (int a = 0; a < kh; ++a) {
+        const int64_t r = border_index(i + a - ah, h, mode);
+        for (int bb = 0; bb < kw; ++bb) {
+            const int64_t c = border_index(j + bb - aw, w, mode);
+            const double x = (r < 0 || c < 0) ? 0.0 : load_px(in, dtype, (r * w + c) * nc + ch);
+            const double wt = k[a * kw + bb];
+            s += wt * x;
+            b += fabs(wt) * fabs(x);
+        }
+    }
+    *out = s;
+    if (bound) *bound = b;
+}
+
+static void conv_hwc(int64_t nc, int64_t h, int64_t w, const void *in, int dtype,
+                     int kh, int kw, const double *k, double *out, double *bound, int mode)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < h; ++i)
+        for (int64_t j = 0; j < w; ++j)
+            for (int64_t ch = 0; ch < nc; ++ch) {
+                const int64_t o = (i * w + j) * nc + ch;
+                conv_pixel_hwc(nc, h, w, in, dtype, ch, kh, kw, k, i, j, out + o, bound ? bound + o : NULL,
+                               mode);
+            }
+}
+
+/* Direct correlation of an interleaved [h][w][nc] image (FP32 or binary16
+ * bits) under border mode `mode`; out/bound: h*w*nc doubles in the same
+ * layout (bound may be NULL).  Returns 0, or -1 on bad arguments. */
+int oracle_conv2d_hwc(int64_t nc, int64_t h, int64_t w, const void *in, int dtype,
+                      int kh, int kw, const float *k, double *out, double *bound, int mode)
+{
+    if (nc <= 0 || h <= 0 || w <= 0 || kh <= 0 || kw <= 0 || mode < 0 || mode > 4) return -1;
+    double *kd = widen_filter(kh, kw, k);
+    if (!kd) return -1;
+    conv_hwc(nc, h, w, in, dtype, kh, kw, kd, out, bound, mode);
+    free(kd);
+    return 0;
+}
+
+/* Separable weights gy[a] * gx[b] (FP64) on an interleaved image. */
+int oracle_conv2d_sep_hwc(int64_t nc, int64_t h, int64_t w, const void *in, int dtype,
+                          int kx, const float *gx, int ky, const float *gy,
+                          double *out, double *bound, int mode)
+{
+    if (nc <= 0 || h <= 0 || w <= 0 || kx <= 0 || ky <= 0 || mode < 0 || mode > 4) return -1;
+    double *kd = (double *)malloc(sizeof(double) * (size_t)kx * (size_t)ky);
+    if (!kd) return -1;
+    for (int a = 0; a < ky; ++a)
+        for (int b = 0; b < kx; ++b) kd[a * kx + b] = (double)gy[a] * (double)gx[b];
+    conv_hwc(nc, h, w, in, dtype, ky, kx, kd, out, bound, mode);
+    free(kd);
+    return 0;
+}
+
+/* The interleaved definition at sampled (ch, i, j) points. */
+int oracle_conv2d_hwc_points(int64_t nc, int64_t h, int64_t w, const void *in, int dtype,
+                             int kh, int kw, const float *k, int64_t npts, const int64_t *pts,
+                             double *out, double *bound)
+{
+    if (nc <= 0 || h <= 0 || w <= 0 || kh <= 0 || kw <= 0 || npts < 0) return -1;
+    double *kd = widen_filter(kh, kw, k);
+    if (!kd) return -1;
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (int64_t p = 0; p < npts; ++p) {
+        const int64_t ch = pts[3 * p], i = pts[3 * p + 1], j = pts[3 * p + 2];
+        if (ch < 0 || ch >= nc || i < 0 || i >= h || j < 0 || j >= w) { bad = 1; continue; }
+        conv_pixel_hwc(nc, h, w, in, dtype, ch, kh, kw, kd, i, j, out + p, bound ? bound + p : NULL, 0);
+    }
+    free(kd);
+    return bad ? -1 : 0;
+}
+
 /* ------------------------------------------------------- Jacobi + residual */
 
 /* sqrt(sum over interior points of (4u - up - down - left - right)^2), summed

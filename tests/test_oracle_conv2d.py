@@ -272,3 +272,75 @@ def test_border_modes_hand_row():
         want = [sum(k[0, b] * e[j + b] for b in range(5)) for j in range(3)]
         out, _ = oracle.conv2d(img, k, border=mode)
         np.testing.assert_array_equal(out[0, 0], want, err_msg=mode)
+
+
+# ------------------------------------------------ interleaved [h][w][c] layout
+
+@pytest.mark.parametrize("border", ["clamp", "zero", "reflect", "mirror", "wrap"])
+@pytest.mark.parametrize("seed", range(8))
+def test_interleaved_layout_matches_scipy_per_channel(border, seed):
+    """Channel ch of an interleaved image is scipy's correlation of the slice
+    x[:, :, ch] under the same border mode (channels never mix)."""
+    r = _rng(700 + seed)
+    h, w = r.integers(1, 9, size=2)
+    c = int(r.integers(1, 6))
+    kh, kw = r.integers(1, 10, size=2)
+    img = r.standard_normal((h, w, c)).astype(np.float32)
+    k = r.standard_normal((kh, kw)).astype(np.float32)
+    out, bound = oracle.conv2d_hwc(img, k, border=border)
+    assert out.shape == (h, w, c)
+    for ch in range(c):
+        ref = ndi.correlate(img[:, :, ch].astype(np.float64), k.astype(np.float64), mode=SCIPY_MODE[border],
+                            cval=0.0)
+        assert np.all(np.abs(out[:, :, ch] - ref) <= 1e-13 * bound[:, :, ch] + 1e-300), (border, ch)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_interleaved_layout_is_the_planar_definition_transposed(seed):
+    """The interleaved result is the planar result of the transposed image,
+    bit for bit (the same per-pixel sum), for FP32 and binary16 inputs."""
+    r = _rng(800 + seed)
+    h, w, c = int(r.integers(1, 12)), int(r.integers(1, 12)), int(r.integers(1, 5))
+    k = r.standard_normal((3, 5)).astype(np.float32)
+    for img in (r.standard_normal((h, w, c)).astype(np.float32),
+                r.standard_normal((h, w, c)).astype(np.float16)):
+        out, bound = oracle.conv2d_hwc(img, k)
+        pl, pb = oracle.conv2d(np.ascontiguousarray(np.moveaxis(img, 2, 0)), k)
+        np.testing.assert_array_equal(np.moveaxis(out, 2, 0), pl)
+        np.testing.assert_array_equal(np.moveaxis(bound, 2, 0), pb)
+
+
+def test_interleaved_impulse_stays_in_its_channel():
+    """One 1 at (p, q) of channel 1 of a 3-channel image: channel 1 shows the
+    filter (correlation orientation, anchor k/2), the other channels stay 0."""
+    img = np.zeros((9, 11, 3), dtype=np.float32)
+    img[4, 5, 1] = 1.0
+    k = np.arange(1, 16, dtype=np.float32).reshape(3, 5)
+    out, _ = oracle.conv2d_hwc(img, k)
+    assert not out[:, :, 0].any() and not out[:, :, 2].any()
+    for a in range(3):
+        for b in range(5):
+            assert out[4 - a + 1, 5 - b + 2, 1] == k[a, b]
+
+
+def test_interleaved_separable_equals_two_1d_passes():
+    r = _rng(901)
+    img = r.standard_normal((13, 10, 3)).astype(np.float32)
+    gx = r.standard_normal(5).astype(np.float32)
+    gy = r.standard_normal(7).astype(np.float32)
+    out, bound = oracle.conv2d_sep_hwc(img, gx, gy)
+    x = img.astype(np.float64)
+    ref = ndi.correlate1d(ndi.correlate1d(x, gx.astype(np.float64), axis=1, mode="nearest"),
+                          gy.astype(np.float64), axis=0, mode="nearest")
+    assert np.all(np.abs(out - ref) <= 1e-13 * bound + 1e-300)
+
+
+def test_interleaved_points_match_full_image():
+    r = _rng(902)
+    img = r.standard_normal((17, 9, 4)).astype(np.float32)
+    k = r.standard_normal((5, 3)).astype(np.float32)
+    full, fb = oracle.conv2d_hwc(img, k)
+    pts = np.array([[0, 0, 0], [3, 16, 8], [2, 7, 4], [1, 0, 8], [3, 16, 0]])
+    v, b = oracle.conv2d_hwc_points(img, k, pts)
+    np.testing.assert_array_equal(v, full[pts[:, 1], pts[:, 2], pts[:, 0]])
+    np.testing.assert_array_equal(b, fb[pts[:, 1], pts[:, 2], pts[:, 0]])

@@ -57,6 +57,12 @@ MUTANTS = [
      "const int64_t ch = pts[3 * p], j = pts[3 * p + 1], i = pts[3 * p + 2];"),
     ("separable sampled points with the filter sides swapped",
      "conv_pixel(h, w, in, dtype, ch * h * w, ky, kx, kd,", "conv_pixel(h, w, in, dtype, ch * h * w, kx, ky, kd,"),
+    ("interleaved pixels read without the channel stride",
+     "load_px(in, dtype, (r * w + c) * nc + ch)", "load_px(in, dtype, (r * w + c) + ch)"),
+    ("interleaved rows read with the planar pitch",
+     "load_px(in, dtype, (r * w + c) * nc + ch)", "load_px(in, dtype, r * w + c * nc + ch)"),
+    ("interleaved result written to the planar position",
+     "const int64_t o = (i * w + j) * nc + ch;", "const int64_t o = (ch * h + i) * w + j;"),
     ("binary16 pixels read as raw integers",
      "return oracle_f16_to_f64(((const uint16_t *)in)[idx]);", "return (double)((const uint16_t *)in)[idx];"),
     # binary16 codec
