@@ -22,123 +22,12 @@
 //     rows), with the filter row fetched by a broadcast LDS.128;
 //   * the output is written with one 16-byte (FP32) or 8-byte (FP16) store per
 //     thread and row.
-#include <cudaTypedefs.h>
-
-#include <algorithm>
-#include <atomic>
-
-#include "conv_tile.cuh"
-#include "tma.cuh"
+#include "conv_kernels.cuh"
 
 namespace pencil {
 namespace {
 
 using namespace tile;
-
-// Per-lane operations on a pair of FP32 values (fma.rn.f32x2, mul.rn.f32x2),
-// each lane rounded to nearest even exactly like the scalar operation.
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-
-// VMODE: how rows that are not 16-byte aligned are handled.  0: vec_ok at
-// run time, such rows staged in 4-byte copies and stored with scalar stores
-// (compute-bound sides: the least code around the FMA loop); 1: every row
-// aligned (compile-time); 2: rows not aligned, each chunk copied and stored
-// with the widest accesses its address allows (memory-bound sides).
-template <typename T, int KH, int KW, int TX, int TY, int R, int G, int MINB, bool ANYB, bool HALFW, int VMODE>
-__global__ void __launch_bounds__(TX *TY, MINB)
-    conv2d_direct_kernel(const T *__restrict__ in, const float *__restrict__ k, T *__restrict__ out,
-                         int h, int w, bool vec_ok, int border) {
-    using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
-    extern __shared__ __align__(128) float smem[];
-    const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
-    const bool vok = VMODE == 0 ? vec_ok : VMODE == 1;
-    direct_tile<T, KH, KW, TX, TY, R, G, ANYB, HALFW, VMODE == 2>(in + plane, k, out + plane, h, w, vok,
-                                               blockIdx.y * Cfg::TH, blockIdx.x * Cfg::TW, smem, border);
-}
-
-// ---------------------------------------------------------- TMA-staged kernel
-// Tile loads that did not complete within their bounded wait (each such CTA
-// skipped its tile); read and cleared by pencil_device_status.
-__device__ unsigned int g_wait_timeouts;
-
-// Clamp-to-edge on a staged tile that holds zeros outside the image (a TMA
-// load fills out-of-range elements with zeros): rows above or below the
-// image take the nearest edge row, then columns left or right of it the
-// nearest edge column, so corners get both clamps.  (gy0, gx0): global
-// position of t[0][0].  Block-uniform; ends with a barrier when it writes.
-template <typename S, int SH, int SW, int NT>
-__device__ __forceinline__ void clamp_fixup(S *__restrict__ t, int h, int w, int gy0, int gx0) {
-    const int top = -gy0, bot = h - gy0;  // staged rows [top, bot) are inside the image
-    if (top > 0 || bot < SH) {
-        for (int idx = threadIdx.x; idx < SH * SW; idx += NT) {
-            const int r = idx / SW, c = idx - r * SW;
-            const int src = r < top ? top : (r >= bot ? bot - 1 : r);
-            if (src != r) t[idx] = t[src * SW + c];
-        }
-        __syncthreads();
-    }
-    const int left = -gx0, right = w - gx0;  // staged columns [left, right) are inside
-    if (left > 0 || right < SW) {
-        for (int idx = threadIdx.x; idx < SH * SW; idx += NT) {
-            const int r = idx / SW, c = idx - r * SW;
-            const int src = c < left ? left : (c >= right ? right - 1 : c);
-            if (src != c) t[idx] = t[r * SW + src];
-        }
-        __syncthreads();
-    }
-}
-
-// The direct kernel with its halo tile loaded by the tensor memory
-// accelerator: one thread arms an mbarrier and issues a single
-// cp.async.bulk.tensor copy of the (TH+kh-1) x (TW+2P) box of plane
-// blockIdx.z (rows 16-byte aligned, which the tensor map requires); the other
-// threads stage the filter meanwhile.  Out-of-image elements arrive as zeros:
-// the zero border as it is, clamp-to-edge after clamp_fixup.  The compute is
-// the shared tile body, so the bits are those of the cp.async kernel.
-// Shared memory: the staged tile (type T, first, 128-byte aligned), the FP32
-// copy of a binary16 tile unless HALFW, the filter rows.
-template <typename T, int KH, int KW, int TX, int TY, int R, int G, int MINB, bool HALFW, bool CLAMP>
-__global__ void __launch_bounds__(TX *TY, MINB)
-    conv2d_direct_tma_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ k,
-                             T *__restrict__ out, int h, int w) {
-    using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
-    constexpr int SW = Cfg::SW, SH = Cfg::SH, KWP = Cfg::KWP, NT = Cfg::NT;
-    constexpr bool F16 = sizeof(T) == 2;
-    extern __shared__ __align__(128) float smem[];
-    __shared__ __align__(8) uint64_t bar;
-    T *s_t = reinterpret_cast<T *>(smem);                                           // the TMA box
-    float *s_in = F16 ? reinterpret_cast<float *>(s_t + SH * SW) : smem;            // FP32 tile
-    float *s_k = F16 && HALFW ? s_in : s_in + SH * SW;                              // filter rows
-    const int y0 = blockIdx.y * Cfg::TH, x0 = blockIdx.x * Cfg::TW;
-    const int gy0 = y0 - Cfg::AH, gx0 = x0 - Cfg::P;
-    if ((tma::smem_addr(s_t) & 127u) != 0) {  // a TMA box needs a 128-byte aligned destination
-        if (threadIdx.x == 0) atomicAdd(&g_wait_timeouts, 1u);
-        return;
-    }
-
-    if (threadIdx.x == 0) tma::mbar_init(&bar, 1);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        tma::mbar_arrive_expect_tx(&bar, (unsigned)(sizeof(T) * SH * SW));
-        tma::load_3d(s_t, &tmap, gx0, gy0, (int)blockIdx.z, &bar);
-    }
-    stage_filter<KH, KW, KWP, NT>(k, s_k);
-    const bool ok = __syncthreads_and(tma::mbar_wait(&bar, 0, tma::kLoadWaitNs));
-    if (!ok) {  // the copy did not complete in time: report, let it land, skip the tile
-        if (threadIdx.x == 0) atomicAdd(&g_wait_timeouts, 1u);
-        tma::mbar_wait(&bar, 0, tma::kLoadWaitNs);
-        return;
-    }
-    if (CLAMP) clamp_fixup<T, SH, SW, NT>(s_t, h, w, gy0, gx0);
-    T *dst = out + (size_t)h * (size_t)w * blockIdx.z;
-    if constexpr (F16 && HALFW) {
-        direct_compute<T, KH, KW, TX, TY, R, G, T, false>(s_t, s_k, dst, h, w, true, y0, x0);
-    } else {
-        stage_widen<T, SH, SW, NT>(s_in, s_t);
-        direct_compute<T, KH, KW, TX, TY, R, G, float, false>(s_in, s_k, dst, h, w, true, y0, x0);
-    }
-}
 
 // The bounded wait on its own: an mbarrier that expects 16 bytes no copy
 // delivers, waited on for limit_ns; a wait that runs out is counted like a
@@ -153,350 +42,6 @@ __global__ void wait_selftest_kernel(uint64_t limit_ns, int *result) {
         if (!ok) atomicAdd(&g_wait_timeouts, 1u);
         *result = ok ? 1 : 0;
     }
-}
-
-// ------------------------------------------------------------ generic kernel
-// Any kh, kw: one output per thread, reads straight from global memory with
-// clamped indices (L1/L2 serve the reuse).  Same per-pixel order as above.
-template <typename T>
-__global__ void __launch_bounds__(256)
-    conv2d_generic_kernel(const T *__restrict__ in, const float *__restrict__ k, T *__restrict__ out,
-                          int h, int w, int kh, int kw, int border) {
-    const int j = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
-    if (i >= h || j >= w) return;
-    const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
-    const T *src = in + plane;
-    const int ah = kh / 2, aw = kw / 2;
-    float acc = 0.0f;
-    for (int a = 0; a < kh; ++a) {
-        const int r = border_index(i + a - ah, h, border);
-        const T *row = src + (size_t)max(r, 0) * (size_t)w;
-        const float *kr = k + (size_t)a * kw;
-        auto px = [&](int b) {
-            const int c = border_index(j + b - aw, w, border);
-            return (r < 0 || c < 0) ? 0.0f : Io<T>::ld(row + c);
-        };
-        float s = __fmul_rn(__ldg(kr), px(0));
-        for (int b = 1; b < kw; ++b) s = __fmaf_rn(__ldg(kr + b), px(b), s);
-        acc = __fadd_rn(acc, s);
-    }
-    Io<T>::st(out + plane + (size_t)i * w + j, acc);
-}
-
-// --------------------------------------------------------- separable kernel
-// Row pass (kx taps) of the staged halo tile into shared memory, then the
-// column pass (ky taps) from it; nothing intermediate goes to HBM.  PAIR bit 1
-// runs the row pass, bit 2 the column pass, on packed FP32 pairs (two adjacent
-// columns per instruction, the same bits as the scalar form; on GB300 a pair
-// instruction costs the issue slots of two scalar ones, so it pays only where
-// it shortens the schedule: measured per side, see sep_pair).
-template <int KX, int KY, int TX, int TY, int R, bool INPLACE = false>
-struct SepCfg {
-    static constexpr int C = 4;
-    static constexpr int AX = KX / 2, AY = KY / 2;
-    static constexpr int NT = TX * TY;
-    static constexpr int TW = TX * C, TH = TY * R;
-    static constexpr int P = round_up(AX, 8);
-    static constexpr int SW = TW + 2 * P;
-    static constexpr int SH = TH + KY - 1;
-    static constexpr int M0 = (P - AX) & ~3;  // first 16-byte chunk a row pass reads
-    static constexpr int NX = round_up(P - AX - M0 + C + KX - 1, 4);
-    // in place: the row-pass results overwrite the staged tile (row stride SW)
-    static constexpr size_t smem_f32 = sizeof(float) * (size_t)(SH * SW + (INPLACE ? 0 : SH * TW));
-    // the binary16 staging area follows, 128-byte aligned (a TMA box destination)
-    static constexpr size_t off16 = (smem_f32 + 127) / 128 * 128;
-    static constexpr size_t smem(size_t esz) { return esz == 2 ? off16 + 2 * (size_t)SH * SW : smem_f32; }
-};
-
-// VMODE 0-2 as for the direct kernel (cp.async staging); 3: rows 16-byte
-// aligned, clamp (border 0) or zero (border 1) border, the halo tile loaded
-// as one TMA box of `tmap` (unused by the other modes), as the direct TMA
-// kernel does.
-template <typename T, int KX, int KY, int TX, int TY, int R, int MINB, bool INPLACE, bool ANYB, int PAIR,
-          int VMODE>
-__global__ void __launch_bounds__(TX *TY, MINB)
-    conv2d_sep_kernel(const __grid_constant__ CUtensorMap tmap, const T *__restrict__ in,
-                      const float *__restrict__ gx, const float *__restrict__ gy, T *__restrict__ out, int h,
-                      int w, bool vec_ok_, int border) {
-    constexpr bool ADAPT = VMODE == 2, TMA = VMODE == 3;
-    const bool vec_ok = VMODE == 0 ? vec_ok_ : VMODE != 2;
-    using Cfg = SepCfg<KX, KY, TX, TY, R, INPLACE>;
-    constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, SH = Cfg::SH, TW = Cfg::TW,
-                  NX = Cfg::NX, AX = Cfg::AX, AY = Cfg::AY, NT = Cfg::NT;
-    constexpr int TS = INPLACE ? SW : TW;  // row stride of the row-pass results
-    extern __shared__ __align__(128) float smem[];
-    float *s_in = smem;
-    float *s_t = INPLACE ? smem : smem + SH * SW;
-    T *s16 = reinterpret_cast<T *>(smem + Cfg::off16 / sizeof(float));
-
-    const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
-    const T *src = in + plane;
-    T *dst = out + plane;
-    const int x0 = blockIdx.x * TW;
-    const int y0 = blockIdx.y * Cfg::TH;
-    if constexpr (TMA) {
-        __shared__ __align__(8) uint64_t bar;
-        T *s_box = sizeof(T) == 2 ? s16 : reinterpret_cast<T *>(s_in);
-        if ((tma::smem_addr(s_box) & 127u) != 0) {  // a TMA box needs a 128-byte aligned destination
-            if (threadIdx.x == 0) atomicAdd(&g_wait_timeouts, 1u);
-            return;
-        }
-        if (threadIdx.x == 0) tma::mbar_init(&bar, 1);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            tma::mbar_arrive_expect_tx(&bar, (unsigned)(sizeof(T) * SH * SW));
-            tma::load_3d(s_box, &tmap, x0 - P, y0 - AY, (int)blockIdx.z, &bar);
-        }
-        if (!__syncthreads_and(tma::mbar_wait(&bar, 0, tma::kLoadWaitNs))) {
-            if (threadIdx.x == 0) atomicAdd(&g_wait_timeouts, 1u);
-            tma::mbar_wait(&bar, 0, tma::kLoadWaitNs);
-            return;
-        }
-        if (border == 0) clamp_fixup<T, SH, SW, NT>(s_box, h, w, y0 - AY, x0 - P);
-        stage_widen<T, SH, SW, NT>(s_in, s16);
-    } else {
-        stage_tile<T, SH, SW, NT, ANYB, ADAPT>(src, h, w, y0 - AY, x0 - P, vec_ok, s_in, s16, border);
-    }
-
-    // row pass: t[r][q*C + c] = sum_b gx[b] * in[r][q*C + c + b - AX]
-    {
-        float fx[KX];
-#pragma unroll
-        for (int b = 0; b < KX; ++b) fx[b] = __ldg(gx + b);
-        constexpr int X0 = P - AX - Cfg::M0;  // window index of tap 0 of column 0
-        constexpr int QPR = TW / C;
-        constexpr int ITEMS = SH * QPR;
-        constexpr int PER = (ITEMS + NT - 1) / NT;  // items per thread
-        float4 res[INPLACE ? PER : 1];
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int idx = threadIdx.x + k * NT;
-            if (idx < ITEMS) {
-                const int r = idx / QPR, q = idx - r * QPR;
-                const float *sp = s_in + r * SW + q * C + Cfg::M0;
-                float x[NX];
-#pragma unroll
-                for (int m = 0; m < NX; m += 4) {
-                    const float4 v = *reinterpret_cast<const float4 *>(sp + m);
-                    x[m] = v.x; x[m + 1] = v.y; x[m + 2] = v.z; x[m + 3] = v.w;
-                }
-                float tv[C];
-                if constexpr ((PAIR & 1) != 0) {
-#pragma unroll
-                    for (int c = 0; c < C; c += 2) {
-                        float2 sum = mul2(make_float2(fx[0], fx[0]), make_float2(x[X0 + c], x[X0 + c + 1]));
-#pragma unroll
-                        for (int b = 1; b < KX; ++b)
-                            sum = fma2(make_float2(fx[b], fx[b]), make_float2(x[X0 + c + b], x[X0 + c + b + 1]), sum);
-                        tv[c] = sum.x;
-                        tv[c + 1] = sum.y;
-                    }
-                } else {
-#pragma unroll
-                    for (int c = 0; c < C; ++c) {
-                        float sum = __fmul_rn(fx[0], x[X0 + c]);
-#pragma unroll
-                        for (int b = 1; b < KX; ++b) sum = __fmaf_rn(fx[b], x[X0 + c + b], sum);
-                        tv[c] = sum;
-                    }
-                }
-                const float4 t4 = make_float4(tv[0], tv[1], tv[2], tv[3]);
-                if (INPLACE)
-                    res[k] = t4;
-                else
-                    *reinterpret_cast<float4 *>(s_t + r * TS + q * C) = t4;
-            }
-        }
-        if (INPLACE) {
-            __syncthreads();  // every read of the staged tile is done
-#pragma unroll
-            for (int k = 0; k < PER; ++k) {
-                const int idx = threadIdx.x + k * NT;
-                if (idx < ITEMS) {
-                    const int r = idx / QPR, q = idx - r * QPR;
-                    *reinterpret_cast<float4 *>(s_t + r * TS + q * C) = res[k];
-                }
-            }
-        }
-    }
-    __syncthreads();
-
-    // column pass: out[o][c] = sum_a gy[a] * t[o + a][c]
-    float fy[KY];
-#pragma unroll
-    for (int a = 0; a < KY; ++a) fy[a] = __ldg(gy + a);
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    float acc[R][C];
-    if constexpr ((PAIR & 2) != 0) {
-        float2 acc2[R][C / 2];
-#pragma unroll
-        for (int r = 0; r < R + KY - 1; ++r) {
-            const float4 v = *reinterpret_cast<const float4 *>(s_t + (ty * R + r) * TS + tx * C);
-            const float2 tv[C / 2] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
-#pragma unroll
-            for (int o = 0; o < R; ++o) {
-                const int a = r - o;
-                if (a == 0) {
-#pragma unroll
-                    for (int q = 0; q < C / 2; ++q) acc2[o][q] = mul2(make_float2(fy[0], fy[0]), tv[q]);
-                } else if (a > 0 && a < KY) {
-#pragma unroll
-                    for (int q = 0; q < C / 2; ++q) acc2[o][q] = fma2(make_float2(fy[a], fy[a]), tv[q], acc2[o][q]);
-                }
-            }
-        }
-#pragma unroll
-        for (int o = 0; o < R; ++o)
-#pragma unroll
-            for (int q = 0; q < C / 2; ++q) {
-                acc[o][2 * q] = acc2[o][q].x;
-                acc[o][2 * q + 1] = acc2[o][q].y;
-            }
-    } else {
-#pragma unroll
-        for (int r = 0; r < R + KY - 1; ++r) {
-            const float4 v = *reinterpret_cast<const float4 *>(s_t + (ty * R + r) * TS + tx * C);
-            const float tv[C] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int o = 0; o < R; ++o) {
-                const int a = r - o;
-                if (a == 0) {
-#pragma unroll
-                    for (int c = 0; c < C; ++c) acc[o][c] = __fmul_rn(fy[0], tv[c]);
-                } else if (a > 0 && a < KY) {
-#pragma unroll
-                    for (int c = 0; c < C; ++c) acc[o][c] = __fmaf_rn(fy[a], tv[c], acc[o][c]);
-                }
-            }
-        }
-    }
-    store_block<T, R, ADAPT>(dst, h, w, y0 + ty * R, x0 + tx * C, vec_ok, acc);
-}
-
-// Separable with runtime tap counts (fallback for sides without a
-// specialisation): same order, taps read from shared memory.
-template <typename T>
-__global__ void __launch_bounds__(256)
-    conv2d_sep_generic_kernel(const T *__restrict__ in, const float *__restrict__ gx,
-                              const float *__restrict__ gy, T *__restrict__ out, int h, int w,
-                              int kx, int ky, int border) {
-    // tile 32 x 32 outputs, 256 threads
-    extern __shared__ __align__(128) float smem[];
-    const int SH = 32 + ky - 1;
-    float *s_t = smem;                  // SH x 32
-    const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
-    const T *src = in + plane;
-    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
-    const int ax = kx / 2, ay = ky / 2;
-    for (int idx = threadIdx.x; idx < SH * 32; idx += 256) {
-        const int r = idx / 32, c = idx % 32;
-        const int gr = border_index(y0 + r - ay, h, border);
-        const T *row = src + (size_t)max(gr, 0) * (size_t)w;
-        const int j = x0 + c;
-        auto px = [&](int b) {
-            const int gc = border_index(j + b - ax, w, border);
-            return (gr < 0 || gc < 0) ? 0.0f : Io<T>::ld(row + gc);
-        };
-        float s = __fmul_rn(__ldg(gx), px(0));
-        for (int b = 1; b < kx; ++b) s = __fmaf_rn(__ldg(gx + b), px(b), s);
-        s_t[idx] = s;
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < 32 * 32; idx += 256) {
-        const int r = idx / 32, c = idx % 32;
-        const int i = y0 + r, j = x0 + c;
-        if (i >= h || j >= w) continue;
-        float acc = __fmul_rn(__ldg(gy), s_t[r * 32 + c]);
-        for (int a = 1; a < ky; ++a) acc = __fmaf_rn(__ldg(gy + a), s_t[(r + a) * 32 + c], acc);
-        Io<T>::st(out + plane + (size_t)i * w + j, acc);
-    }
-}
-
-// ------------------------------------------------------------------ launch
-template <typename Kern>
-cudaError_t set_smem(Kern kern, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-// cuTensorMapEncodeTiled from the driver (no link-time dependency on it),
-// or null where the driver does not offer it.
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            p = nullptr;
-        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }();
-    return fn;
-}
-
-// Tensor map of a [c][h][w] image with rows 16-byte aligned, box (bw, bh, 1);
-// false if it cannot be made (the caller then stages with cp.async).
-template <typename T>
-bool image_tensor_map(CUtensorMap *m, const T *base, int c, int h, int w, int bw, int bh) {
-    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)c};
-    const cuuint64_t strides[2] = {(cuuint64_t)w * sizeof(T), (cuuint64_t)h * (cuuint64_t)w * sizeof(T)};
-    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1u};
-    const cuuint32_t elem[3] = {1u, 1u, 1u};
-    return enc(m, sizeof(T) == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-               const_cast<T *>(base), dims, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// The TMA-staged launch for aligned rows with the clamp or zero border (a box
-// side is at most 256 elements); false, with nothing launched, where it does
-// not apply.
-template <typename T, int K, int TX, int TY, int R, int G, int MINB, bool HALFW>
-bool try_direct_tma(int c, int h, int w, const T *in, const float *k, T *out, bool vec_ok, int border,
-                    cudaStream_t s, cudaError_t *err) {
-    using Cfg = DirectCfg<K, K, TX, TY, R, G>;
-    static_assert(Cfg::SW <= 256 && Cfg::SH <= 256, "a TMA box side is at most 256 elements");
-    CUtensorMap tmap;
-    if (!vec_ok || (border != 0 && border != 1) || !image_tensor_map<T>(&tmap, in, c, h, w, Cfg::SW, Cfg::SH))
-        return false;
-    auto kern = border == 0 ? conv2d_direct_tma_kernel<T, K, K, TX, TY, R, G, MINB, HALFW, true>
-                            : conv2d_direct_tma_kernel<T, K, K, TX, TY, R, G, MINB, HALFW, false>;
-    const size_t smem = HALFW ? Cfg::smem_half : Cfg::smem(sizeof(T));
-    *err = set_smem(kern, smem);
-    if (*err == cudaSuccess) {
-        dim3 grid((w + Cfg::TW - 1) / Cfg::TW, (h + Cfg::TH - 1) / Cfg::TH, c);
-        kern<<<grid, Cfg::NT, smem, s>>>(tmap, k, out, h, w);
-        *err = cudaGetLastError();
-    }
-    return true;
-}
-
-template <typename T, int K, int TX, int TY, int R, int G = 1, int MINB = 1, bool HALFW = false>
-cudaError_t run_direct(int c, int h, int w, const T *in, const float *k, T *out, bool vec_ok,
-                       int border, cudaStream_t s) {
-    using Cfg = DirectCfg<K, K, TX, TY, R, G>;
-    cudaError_t err = cudaSuccess;
-    if (try_direct_tma<T, K, TX, TY, R, G, MINB, HALFW>(c, h, w, in, k, out, vec_ok, border, s, &err)) return err;
-    // sides up to 5 (memory-bound): an aligned-row kernel and an adaptive
-    // any-row kernel; larger sides: one kernel with vec_ok at run time
-    using Kern = void (*)(const T *, const float *, T *, int, int, bool, int);
-    Kern kern;
-    if constexpr (K <= 5)
-        kern = border != 0 ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, true, HALFW, 2>
-               : vec_ok    ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 1>
-                           : conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 2>;
-    else
-        kern = border != 0 ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, true, HALFW, 0>
-                           : conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 0>;
-    const size_t smem = HALFW ? Cfg::smem_half : Cfg::smem(sizeof(T));
-    cudaError_t e = set_smem(kern, smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((w + Cfg::TW - 1) / Cfg::TW, (h + Cfg::TH - 1) / Cfg::TH, c);
-    kern<<<grid, Cfg::NT, smem, s>>>(in, k, out, h, w, vec_ok, border);
-    return cudaGetLastError();
 }
 
 // SMs of the current device (cached per device; 152 if the query fails).
@@ -576,48 +121,6 @@ cudaError_t run_direct_k(int K, int c, int h, int w, const T *in, const float *k
 }
 
 template <typename T>
-cudaError_t run_generic(int c, int h, int w, const T *in, int kh, int kw, const float *k, T *out,
-                        int border, cudaStream_t s) {
-    dim3 grid((w + 31) / 32, (h + 7) / 8, c);
-    conv2d_generic_kernel<T><<<grid, 256, 0, s>>>(in, k, out, h, w, kh, kw, border);
-    return cudaGetLastError();
-}
-
-template <typename T, int K, int TX, int TY, int R, int MINB = 1, bool INPLACE = false, int PAIR = 0>
-cudaError_t run_sep(int c, int h, int w, const T *in, const float *gx, const float *gy, T *out,
-                    bool vec_ok, int border, cudaStream_t s) {
-    using Cfg = SepCfg<K, K, TX, TY, R, INPLACE>;
-    using Kern = void (*)(const CUtensorMap, const T *, const float *, const float *, T *, int, int, bool, int);
-    Kern kern;
-    CUtensorMap tmap = {};
-    static_assert(Cfg::SW <= 256 && Cfg::SH <= 256, "a TMA box side is at most 256 elements");
-    if (vec_ok && (border == 0 || border == 1) && image_tensor_map<T>(&tmap, in, c, h, w, Cfg::SW, Cfg::SH)) {
-        kern = conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 3>;  // TMA staging
-    } else if constexpr (K <= 5) {  // as for the direct kernels
-        kern = border != 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 2>
-               : vec_ok    ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 1>
-                           : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 2>;
-    } else {
-        kern = border != 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 0>
-                           : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 0>;
-    }
-    const size_t smem = Cfg::smem(sizeof(T));
-    cudaError_t e = set_smem(kern, smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((w + Cfg::TW - 1) / Cfg::TW, (h + Cfg::TH - 1) / Cfg::TH, c);
-    kern<<<grid, Cfg::NT, smem, s>>>(tmap, in, gx, gy, out, h, w, vec_ok, border);
-    return cudaGetLastError();
-}
-
-// Packed pair arithmetic in the separable passes (bit 1: row pass, bit 2:
-// column pass), where it measured faster on GB300 at 8192 x 8192 x 3.
-template <typename T>
-constexpr int sep_pair(int k) {
-    if (sizeof(T) == 4) return k == 15 ? 2 : 0;
-    return k == 5 || k == 9 ? 3 : (k >= 7 ? 2 : 0);
-}
-
-template <typename T>
 cudaError_t run_sep_any(int c, int h, int w, const T *in, int kx, const float *gx, int ky,
                         const float *gy, T *out, bool vec_ok, int border, cudaStream_t s) {
     // Tiles from timing sweeps at 8192 x 8192 x 3; the 15-tap tiles are 128
@@ -634,10 +137,7 @@ cudaError_t run_sep_any(int c, int h, int w, const T *in, int kx, const float *g
             default: break;
         }
     }
-    const size_t smem = sizeof(float) * (size_t)(32 + ky - 1) * 32;
-    dim3 grid((w + 31) / 32, (h + 31) / 32, c);
-    conv2d_sep_generic_kernel<T><<<grid, 256, smem, s>>>(in, gx, gy, out, h, w, kx, ky, border);
-    return cudaGetLastError();
+    return run_sep_generic<T>(c, h, w, in, kx, gx, ky, gy, out, border, s);
 }
 
 }  // namespace
@@ -653,14 +153,7 @@ cudaError_t wait_selftest(uint64_t limit_ns, int *completed) {
     return e;
 }
 
-cudaError_t wait_timeouts(unsigned *n, bool clear) {
-    cudaError_t e = cudaMemcpyFromSymbol(n, g_wait_timeouts, sizeof(unsigned));
-    if (e == cudaSuccess && clear && *n) {
-        const unsigned zero = 0;
-        e = cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof(unsigned));
-    }
-    return e;
-}
+cudaError_t wait_timeouts(unsigned *n, bool clear) { return read_wait_counter(n, clear); }
 
 namespace {
 
@@ -688,12 +181,21 @@ cudaError_t launch_conv2d(int dtype, int c, int h, int w, const void *in, int kh
 }
 
 cudaError_t launch_conv2d_generic(int dtype, int c, int h, int w, const void *in, int kh, int kw,
-                                  const float *k, void *out, cudaStream_t s, int border) {
+                                  const float *k, void *out, cudaStream_t s, int border, int cs) {
     if (dtype == PENCIL_F32)
         return run_generic<float>(c, h, w, static_cast<const float *>(in), kh, kw, k,
-                                  static_cast<float *>(out), border, s);
+                                  static_cast<float *>(out), border, s, cs);
     return run_generic<__half>(c, h, w, static_cast<const __half *>(in), kh, kw, k,
-                               static_cast<__half *>(out), border, s);
+                               static_cast<__half *>(out), border, s, cs);
+}
+
+cudaError_t launch_conv2d_sep_generic(int dtype, int c, int h, int w, const void *in, int kx, const float *gx,
+                                      int ky, const float *gy, void *out, cudaStream_t s, int border, int cs) {
+    if (dtype == PENCIL_F32)
+        return run_sep_generic<float>(c, h, w, static_cast<const float *>(in), kx, gx, ky, gy,
+                                      static_cast<float *>(out), border, s, cs);
+    return run_sep_generic<__half>(c, h, w, static_cast<const __half *>(in), kx, gx, ky, gy,
+                                   static_cast<__half *>(out), border, s, cs);
 }
 
 cudaError_t launch_conv2d_sep(int dtype, int c, int h, int w, const void *in, int kx,

@@ -131,13 +131,30 @@ __device__ __forceinline__ int border_index(int i, int n, int mode) {
 // tests (rows that are not 16-byte aligned then move in 4-byte copies): for
 // compute-bound kernels, where staging is a small part of the time and the
 // extra code costs registers; those kernels pass vec_ok at run time.
-template <typename T, int SH, int SW, int NT, bool ANYB = false, bool ADAPT = true>
+// CS > 1: an interleaved image of CS channels, staged as one plane of rows of
+// w = pixels * CS elements; element q is channel q mod CS of pixel q / CS, and
+// the border mode maps the pixel, keeping the channel.
+template <typename T, int SH, int SW, int NT, bool ANYB = false, bool ADAPT = true, int CS = 1>
 __device__ __forceinline__ void stage_issue(const T *__restrict__ src, int h, int w, int y0, int x0,
                                             bool vec_ok, float *__restrict__ s, T *__restrict__ s16,
                                             int border = 0) {
     constexpr int V = Io<T>::VEC;
     constexpr int CPR = SW / V;
     constexpr bool F16 = sizeof(T) == 2;
+    // element column of staged element q under the border mode, or -1 for a zero
+    auto col = [&](int q) -> int {
+        if constexpr (CS == 1) {
+            if constexpr (ANYB) return border_index(q, w, border);
+            return clampi(q, 0, w - 1);
+        } else {
+            const int p = q >= 0 ? q / CS : -((CS - 1 - q) / CS);  // floor(q / CS)
+            const int ch = q - p * CS;
+            int pc;
+            if constexpr (ANYB) pc = border_index(p, w / CS, border);
+            else pc = clampi(p, 0, w / CS - 1);
+            return pc < 0 ? -1 : pc * CS + ch;
+        }
+    };
     // chunk q of staged row r
     auto chunk = [&](int r, int q) {
         const int gc = x0 + q * V;
@@ -178,15 +195,11 @@ __device__ __forceinline__ void stage_issue(const T *__restrict__ src, int h, in
             float *d = s + r * SW + q * V;
 #pragma unroll
             for (int e = 0; e < V; ++e) {
-                if constexpr (ANYB) {
-                    const int c = border_index(gc + e, w, border);
-                    if (c < 0)
-                        d[e] = 0.0f;
-                    else
-                        cp_async4(d + e, row + c);
-                } else {
-                    cp_async4(d + e, row + clampi(gc + e, 0, w - 1));
-                }
+                const int c = col(gc + e);
+                if (c < 0)
+                    d[e] = 0.0f;
+                else
+                    cp_async4(d + e, row + c);
             }
         } else if (inside && (mis & 3u) == 0) {
             // binary16 row that is only 4-byte aligned: pairs of elements
@@ -197,12 +210,8 @@ __device__ __forceinline__ void stage_issue(const T *__restrict__ src, int h, in
             T *d16 = s16 + r * SW + q * V;  // raw binary16 values, widened below
 #pragma unroll
             for (int e = 0; e < V; ++e) {
-                if constexpr (ANYB) {
-                    const int c = border_index(gc + e, w, border);
-                    d16[e] = c < 0 ? static_cast<T>(0.0f) : row[c];
-                } else {
-                    d16[e] = row[clampi(gc + e, 0, w - 1)];
-                }
+                const int c = col(gc + e);
+                d16[e] = c < 0 ? static_cast<T>(0.0f) : row[c];
             }
         }
     };
@@ -262,11 +271,11 @@ __device__ __forceinline__ void stage_finish(float *__restrict__ s, const T *__r
 
 // stage_issue followed by stage_finish: the staged tile in s (as FP32), ready
 // after the closing barrier.
-template <typename T, int SH, int SW, int NT, bool ANYB = false, bool ADAPT = true>
+template <typename T, int SH, int SW, int NT, bool ANYB = false, bool ADAPT = true, int CS = 1>
 __device__ __forceinline__ void stage_tile(const T *__restrict__ src, int h, int w, int y0, int x0,
                                            bool vec_ok, float *__restrict__ s, T *__restrict__ s16,
                                            int border = 0) {
-    stage_issue<T, SH, SW, NT, ANYB, ADAPT>(src, h, w, y0, x0, vec_ok, s, s16, border);
+    stage_issue<T, SH, SW, NT, ANYB, ADAPT, CS>(src, h, w, y0, x0, vec_ok, s, s16, border);
     stage_finish<T, SH, SW, NT>(s, s16);
 }
 
@@ -297,14 +306,18 @@ __device__ __forceinline__ void store_block(T *__restrict__ dst, int h, int w, i
 // Tile: TH = TY*R output rows by TW = G*TX*4 columns.  A thread owns R rows and
 // G groups of 4 adjacent columns; group g starts TX*4*g columns after group 0,
 // so the loads of a warp stay contiguous (conflict-free LDS.128) in every group.
-template <int KH, int KW, int TX, int TY, int R, int G>
+// CS > 1: columns are elements of an interleaved image of CS channels; tap b
+// of an element lies b*CS elements further, so the halo is AW*CS elements.
+template <int KH, int KW, int TX, int TY, int R, int G, int CS_ = 1>
 struct DirectCfg {
     static constexpr int C = 4;
+    static constexpr int CS = CS_;
     static constexpr int AH = KH / 2, AW = KW / 2;
+    static constexpr int AWE = AW * CS;             // left halo in elements
     static constexpr int NT = TX * TY;
     static constexpr int GS = TX * C;               // column stride between groups
     static constexpr int TW = G * GS, TH = TY * R;
-    static constexpr int P = round_up(AW, 8);       // left halo, 16-byte aligned for f32 and f16
+    static constexpr int P = round_up(AWE, 8);      // left halo, 16-byte aligned for f32 and f16
     static constexpr int SW = TW + 2 * P;
     static constexpr int SH = TH + KH - 1;
     static constexpr int KWP = round_up(KW, 4);     // filter row padded to LDS.128
@@ -334,7 +347,7 @@ __device__ __forceinline__ void ld4s(const __half *p, float *d) {
 // One staged input row r applied to every output row o that uses it (filter
 // row a = r - o).  CHECK tests a against [0, KH); for a compile-time r the test
 // folds away.
-template <bool CHECK, int R, int G, int GS, int KH, int KW, int KWP, int NX, int B0, typename S>
+template <bool CHECK, int R, int G, int GS, int KH, int KW, int KWP, int NX, int B0, typename S, int CS = 1>
 __device__ __forceinline__ void direct_row(int r, const S *__restrict__ xrow,
                                            const float *__restrict__ s_k, float (&acc)[R][G * 4]) {
     float x[G][NX];
@@ -358,7 +371,7 @@ __device__ __forceinline__ void direct_row(int r, const S *__restrict__ xrow,
                 for (int c = 0; c < 4; ++c) {
                     float sum = __fmul_rn(kr[0], x[g][B0 + c]);
 #pragma unroll
-                    for (int b = 1; b < KW; ++b) sum = __fmaf_rn(kr[b], x[g][B0 + c + b], sum);
+                    for (int b = 1; b < KW; ++b) sum = __fmaf_rn(kr[b], x[g][B0 + c + b * CS], sum);
                     acc[o][g * 4 + c] = __fadd_rn(acc[o][g * 4 + c], sum);
                 }
         }
@@ -370,12 +383,13 @@ __device__ __forceinline__ void direct_row(int r, const S *__restrict__ xrow,
 // from zero, in the documented order.  Each staged row is read from the
 // aligned group of four values that holds tap 0 of column 0 onwards, only as
 // far as the taps of column 3 reach.  S: the staged type (FP32, or binary16
-// widened as it is read).
-template <int KH, int KW, int R, int G, int GS, int SW, int KWP, int B0_, typename S = float>
+// widened as it is read).  CS: element distance between taps (the channels
+// of an interleaved image).
+template <int KH, int KW, int R, int G, int GS, int SW, int KWP, int B0_, typename S = float, int CS = 1>
 __device__ __forceinline__ void direct_accumulate(const S *__restrict__ srow_,
                                                   const float *__restrict__ s_k, float (&acc)[R][G * 4]) {
     constexpr int M0 = B0_ & ~3, B0 = B0_ - M0;
-    constexpr int NX = round_up(B0 + 4 + KW - 1, 4);
+    constexpr int NX = round_up(B0 + 4 + (KW - 1) * CS, 4);
     const S *srow = srow_ + M0;
 #pragma unroll
     for (int o = 0; o < R; ++o)
@@ -390,28 +404,29 @@ __device__ __forceinline__ void direct_accumulate(const S *__restrict__ srow_,
     constexpr int EPI = (KH > PRO) ? KH : PRO;
 #pragma unroll
     for (int r = 0; r < PRO; ++r)
-        direct_row<true, R, G, GS, KH, KW, KWP, NX, B0, S>(r, srow + r * SW, s_k, acc);
+        direct_row<true, R, G, GS, KH, KW, KWP, NX, B0, S, CS>(r, srow + r * SW, s_k, acc);
 #pragma unroll 1
     for (int r = PRO; r < EPI; ++r)
-        direct_row<false, R, G, GS, KH, KW, KWP, NX, B0, S>(r, srow + r * SW, s_k, acc);
+        direct_row<false, R, G, GS, KH, KW, KWP, NX, B0, S, CS>(r, srow + r * SW, s_k, acc);
 #pragma unroll
     for (int r = EPI; r < NR; ++r)
-        direct_row<true, R, G, GS, KH, KW, KWP, NX, B0, S>(r, srow + r * SW, s_k, acc);
+        direct_row<true, R, G, GS, KH, KW, KWP, NX, B0, S, CS>(r, srow + r * SW, s_k, acc);
 }
 
 // Compute and store one TH x TW output tile with origin (y0, x0) from a
 // staged tile s_in (see stage_tile; FP32, or the binary16 staging area read
 // directly) and staged filter rows s_k.
-template <typename T, int KH, int KW, int TX, int TY, int R, int G, typename S = float, bool ADAPT = true>
+template <typename T, int KH, int KW, int TX, int TY, int R, int G, typename S = float, bool ADAPT = true,
+          int CS = 1>
 __device__ __forceinline__ void direct_compute(const S *__restrict__ s_in,
                                                const float *__restrict__ s_k, T *__restrict__ dst,
                                                int h, int w, bool vec_ok, int y0, int x0) {
-    using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
-    constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, KWP = Cfg::KWP, AW = Cfg::AW, GS = Cfg::GS;
-    constexpr int B0 = P - AW;  // x index of tap 0 for column 0
+    using Cfg = DirectCfg<KH, KW, TX, TY, R, G, CS>;
+    constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, KWP = Cfg::KWP, GS = Cfg::GS;
+    constexpr int B0 = P - Cfg::AWE;  // x index of tap 0 for column 0
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     float acc[R][G * 4];
-    direct_accumulate<KH, KW, R, G, GS, SW, KWP, B0, S>(s_in + (ty * R) * SW + tx * C, s_k, acc);
+    direct_accumulate<KH, KW, R, G, GS, SW, KWP, B0, S, CS>(s_in + (ty * R) * SW + tx * C, s_k, acc);
 
 #pragma unroll
     for (int g = 0; g < G; ++g) {
@@ -453,28 +468,28 @@ __device__ __forceinline__ void stage_filter(const float *__restrict__ k, float 
 // memory and is widened as the windows are read -- half the shared-memory
 // traffic of an FP32 copy, for sides where that traffic is the limit.
 template <typename T, int KH, int KW, int TX, int TY, int R, int G, bool ANYB = false, bool HALFW = false,
-          bool ADAPT = true>
+          bool ADAPT = true, int CS = 1>
 __device__ __forceinline__ void direct_tile(const T *__restrict__ src, const float *__restrict__ k,
                                             T *__restrict__ dst, int h, int w, bool vec_ok, int y0,
                                             int x0, float *__restrict__ smem, int border = 0) {
-    using Cfg = DirectCfg<KH, KW, TX, TY, R, G>;
+    using Cfg = DirectCfg<KH, KW, TX, TY, R, G, CS>;
     constexpr int SW = Cfg::SW, SH = Cfg::SH, KWP = Cfg::KWP, AH = Cfg::AH, P = Cfg::P;
     if constexpr (HALFW) {
         static_assert(sizeof(T) == 2, "HALFW reads a binary16 tile");
         float *s_k = smem;
         T *s16 = reinterpret_cast<T *>(smem + KH * KWP);
         stage_filter<KH, KW, KWP, Cfg::NT>(k, s_k);
-        stage_issue<T, SH, SW, Cfg::NT, ANYB, ADAPT>(src, h, w, y0 - AH, x0 - P, vec_ok, nullptr, s16, border);
+        stage_issue<T, SH, SW, Cfg::NT, ANYB, ADAPT, CS>(src, h, w, y0 - AH, x0 - P, vec_ok, nullptr, s16, border);
         cp_async_wait_all();
         __syncthreads();
-        direct_compute<T, KH, KW, TX, TY, R, G, T, ADAPT>(s16, s_k, dst, h, w, vec_ok, y0, x0);
+        direct_compute<T, KH, KW, TX, TY, R, G, T, ADAPT, CS>(s16, s_k, dst, h, w, vec_ok, y0, x0);
     } else {
         float *s_in = smem;
         float *s_k = smem + SH * SW;
         T *s16 = reinterpret_cast<T *>(smem + SH * SW + KH * KWP);
         stage_filter<KH, KW, KWP, Cfg::NT>(k, s_k);
-        stage_tile<T, SH, SW, Cfg::NT, ANYB, ADAPT>(src, h, w, y0 - AH, x0 - P, vec_ok, s_in, s16, border);
-        direct_compute<T, KH, KW, TX, TY, R, G, float, ADAPT>(s_in, s_k, dst, h, w, vec_ok, y0, x0);
+        stage_tile<T, SH, SW, Cfg::NT, ANYB, ADAPT, CS>(src, h, w, y0 - AH, x0 - P, vec_ok, s_in, s16, border);
+        direct_compute<T, KH, KW, TX, TY, R, G, float, ADAPT, CS>(s_in, s_k, dst, h, w, vec_ok, y0, x0);
     }
 }
 
