@@ -92,8 +92,9 @@ def measured_peaks():
         return {}
 
 
-KERNEL_SOURCES = ["paper_1302_5586_gb300/csrc/conv2d.cu", "paper_1302_5586_gb300/csrc/conv_tile.cuh",
-                  "paper_1302_5586_gb300/csrc/internal.cuh", "paper_1302_5586_gb300/csrc/tma.cuh"]
+KERNEL_SOURCES = ["paper_1302_5586_gb300/csrc/conv2d.cu", "paper_1302_5586_gb300/csrc/conv_kernels.cuh",
+                  "paper_1302_5586_gb300/csrc/conv_tile.cuh", "paper_1302_5586_gb300/csrc/internal.cuh",
+                  "paper_1302_5586_gb300/csrc/tma.cuh"]
 
 
 def sources_sha(paths=KERNEL_SOURCES):
@@ -404,6 +405,7 @@ def measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g, serve_seconds=SE
     out["plain_512x512_5x5"], keep["plain512"] = measure_small(torch, pg, dev, stream)
     out["op2_inc_2048x2048_cells"] = measure_op2(torch, pg, dev, stream)
     out["chain_8192x8192x3"] = measure_chain(torch, pg, dev, stream, d_img, d_out)
+    out["conv_jacobi_8192x8192x3"] = measure_conv_jacobi(torch, pg, dev, stream, d_img, d_out)
     # the chain runs overwrote d_out[0]: the 3x3 result again for the precision check
     pg.pencil_conv2d_ex(C, H, W, d_img, 3, 3, d_ks[0], d_out[0], pg.PENCIL_F32, 0, sraw)
     out["batched_512"], keep["batch"] = measure_batched(torch, pg, dev, stream)
@@ -484,6 +486,35 @@ def measure_chain(torch, pg, dev, stream, d_img, d_out):
             "fused_hbm_frac": round(8 * PX_PER_PASS / (ms_f * 1e-3) / 1e9 / hbm, 4),
             "fused_fp32_frac": round(flop / (ms_f * 1e-3) / 1e12 / fp32_peak_tflops(), 4)}
     del tmp
+    return res
+
+
+def measure_conv_jacobi(torch, pg, dev, stream, d_img, d_out):
+    """A filter pass then 10 Jacobi smoothing sweeps on every channel of the
+    3 x 8192^2 FP32 image: the fused kernel (the filtered window goes straight
+    into the register sweeps) against a conv2d pass followed by the library's
+    tiled sweeps (same bits).  HBM basis: 8 B per pixel fused."""
+    hbm = measured_peaks().get("hbm_gbs") or 6800.0
+    sraw = stream.cuda_stream
+    n = 10
+    wsb = pg.pencil_jacobi2d_workspace_size(H, W)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    res = {}
+    for K in (3, 5, 7):
+        k = torch.from_numpy(synth.gaussian_2d_f32(K // 2, 1.0)).to(dev)
+        ms_f = _time_stream(torch, stream, lambda: pg.pencil_conv2d_jacobi(C, H, W, d_img, K, K, k, n, d_out[0],
+                                                                           pg.PENCIL_CHAIN_FUSED, sraw), 10)
+
+        def two():
+            pg.pencil_conv2d_ex(C, H, W, d_img, K, K, k, d_out[0], pg.PENCIL_F32, 0, sraw)
+            for ch in range(C):
+                pg.pencil_jacobi2d_ex(H, W, d_out[0][ch], n, 0, None, ws, wsb, 0, sraw)
+        ms_t = _time_stream(torch, stream, two, 10)
+        res[f"{K}x{K}+{n}sweeps"] = {"fused_ms": round(ms_f, 4), "two_pass_ms": round(ms_t, 4),
+                                     "speedup": round(ms_t / ms_f, 3),
+                                     "fused_gpx_s": round(PX_PER_PASS / ms_f / 1e6, 1),
+                                     "fused_hbm_frac": round(8 * PX_PER_PASS / (ms_f * 1e-3) / 1e9 / hbm, 4)}
+    del ws
     return res
 
 
@@ -853,13 +884,24 @@ def run_case(name, reps):
         out = torch.empty_like(img)
         for _ in range(reps):
             pg.pencil_conv2d_ex(c, h, w, img, K, K, k, out, pg.PENCIL_F16 if f16 else pg.PENCIL_F32)
-    elif name == "sep15":
-        c, h, w = 2, 4096, 4096
+    elif name in ("sep15", "sep15h"):
+        f16 = name.endswith("h")
+        c, h, w = (4 if f16 else 2), 4096, 4096  # binary16: twice the pixels, still larger than L2
         img = torch.from_numpy(synth.image_f32(1, c, h, w)).to(dev)
+        if f16:
+            img = img.half()
         g = torch.from_numpy(synth.gaussian_taps_f32(7, 3.0)).to(dev)
         out = torch.empty_like(img)
         for _ in range(reps):
-            pg.pencil_conv2d_sep_ex(c, h, w, img, 15, g, 15, g, out, pg.PENCIL_F32)
+            pg.pencil_conv2d_sep_ex(c, h, w, img, 15, g, 15, g, out, pg.PENCIL_F16 if f16 else pg.PENCIL_F32)
+    elif name.startswith("cj"):
+        K = int(name[2:])
+        c, h, w = 2, 4096, 4096
+        img = torch.from_numpy(synth.image_f32(1, c, h, w)).to(dev)
+        k = torch.from_numpy(synth.filter_f32(2, K, K)).to(dev)
+        out = torch.empty_like(img)
+        for _ in range(reps):
+            pg.pencil_conv2d_jacobi(c, h, w, img, K, K, k, 10, out, pg.PENCIL_CHAIN_FUSED)
     elif name == "batch":
         seed = synth.SEEDS["batch512"]
         h, w, k = synth.batch_spec(seed, 128, 64, 2048)
@@ -909,7 +951,9 @@ def run_case(name, reps):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default=None,
-                    help="profile one kernel on a reduced workload: conv3, conv7, conv15, conv3h (binary16), sep15, batch, jacobi, jacobi-tN (N sweeps per pass), op2-ordered, op2-atomic, chain3, chain5, chain7")
+                    help="profile one kernel on a reduced workload: conv3, conv7, conv15, conv3h (binary16), sep15, sep15h "
+                         "(binary16), batch, jacobi, jacobi-tN (N sweeps per pass), op2-ordered, op2-atomic, "
+                         "chain3, chain5, chain7, cj3, cj5, cj7 (filter then 10 Jacobi sweeps, fused)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=600)

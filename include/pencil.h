@@ -75,6 +75,15 @@ enum { PENCIL_F32 = 0, PENCIL_F16 = 1 };
 #define PENCIL_CONV_GENERIC 1
 /* pencil_conv2d_chain: run the fused kernel even where two passes are faster */
 #define PENCIL_CHAIN_FUSED 2
+/* pencil_conv2d_ex / pencil_conv2d_sep_ex flag: the c channels are
+ * interleaved [h][w][c] (channel ch of pixel (i, j) at element
+ * (i*w + j)*c + ch, the layout image DSLs hand over, Sec. 1) instead of
+ * planar [c][h][w].  Each channel is filtered on its own exactly as the planar
+ * layout filters it (the same bits per channel); the output has the input's
+ * layout.  3 and 4 channels run tiled kernels over the rows of w*c elements;
+ * other channel counts a generic kernel.  w*c must fit an int
+ * (PENCIL_ERR_UNSUPPORTED otherwise). */
+#define PENCIL_LAYOUT_HWC 4
 
 /* Border modes for the _ex conv2d calls, passed in flags as PENCIL_BORDER(m);
  * index i of an axis of length n reads (the plain calls always clamp):
@@ -118,7 +127,8 @@ int pencil_conv2d(int h, int w, PENCIL_ARR2(const float, in, h, w), int kh, int 
 /* Stream-ordered, c planar channels, storage dtype PENCIL_F32 or PENCIL_F16
  * (binary16 images; FP32 accumulation; binary16 results rounded to nearest
  * even).  in, out: c*h*w elements of dtype, device memory; k: kh*kw FP32,
- * device memory.  flags: PENCIL_CONV_GENERIC and/or one PENCIL_BORDER(m).
+ * device memory.  flags: PENCIL_CONV_GENERIC, PENCIL_LAYOUT_HWC and/or one
+ * PENCIL_BORDER(m).
  * Speed, not results, depends on alignment: images whose rows are 16-byte
  * aligned (w a multiple of 4 for FP32, of 8 for binary16, and in and out
  * 16-byte aligned) with the clamp or zero border load their tiles with the
@@ -138,8 +148,9 @@ int pencil_conv2d_sep(int h, int w, PENCIL_ARR2(const float, in, h, w), int kx, 
                       int ky, const float *gy, PENCIL_ARR2(float, out, h, w));
 
 /* Stream-ordered separable filter over c planar channels of dtype
- * PENCIL_F32 or PENCIL_F16; every array is device memory.  flags: 0 or one
- * PENCIL_BORDER(m).  Errors: ARG, NULL, ALIAS, PTR, UNSUPPORTED, CUDA. */
+ * PENCIL_F32 or PENCIL_F16; every array is device memory.  flags:
+ * PENCIL_LAYOUT_HWC and/or one PENCIL_BORDER(m).
+ * Errors: ARG, NULL, ALIAS, PTR, UNSUPPORTED, CUDA. */
 int pencil_conv2d_sep_ex(int c, int h, int w, const void *in, int kx, const float *gx, int ky,
                          const float *gy, void *out, int dtype, int flags, void *stream);
 
@@ -162,6 +173,25 @@ int pencil_conv2d_sep_ex(int c, int h, int w, const void *in, int kx, const floa
 int pencil_conv2d_chain(int c, int h, int w, const void *in, int kh1, int kw1, const float *k1,
                         int kh2, int kw2, const float *k2, void *out, int dtype, int flags,
                         void *stream);
+
+/* A filter pass followed by Jacobi smoothing, out = J^sweeps(conv(in, k)) on
+ * each of c planar FP32 channels: conv the clamp-to-edge correlation above,
+ * J the 5-point Jacobi sweep below (the image's outer ring fixed).  Where it
+ * can, one kernel computes a 128 x 128 window of the filtered image into
+ * registers and runs up to 10 sweeps on it before anything goes to HBM (the
+ * fusion of dependent stencils, Sec. 2.2.3); further sweeps run as
+ * pencil_jacobi2d_ex does.  Fused: square odd filters up to 7, w a multiple of
+ * 4, in and out 16-byte aligned; otherwise a conv2d pass into out and the
+ * sweeps in place.  Either way the result is the same bits as
+ * pencil_conv2d_ex followed by pencil_jacobi2d_ex on each channel.  Sweeps
+ * beyond the fused ones take a workspace from a library-owned stream-ordered
+ * pool (kept for reuse until pencil_shutdown).  flags: 0, or
+ * PENCIL_CHAIN_FUSED to require the fused kernel (UNSUPPORTED where it does
+ * not apply).  in, out: c*h*w floats; k: kh*kw floats; all device memory.
+ * Errors: ARG (sizes, sweeps < 0, flags), NULL, ALIAS (out overlaps in or k),
+ * PTR, UNSUPPORTED, NOMEM, CUDA. */
+int pencil_conv2d_jacobi(int c, int h, int w, const float *in, int kh, int kw, const float *k, int sweeps,
+                         float *out, int flags, void *stream);
 
 /* ------------------------------------------------------------------- batch
  * Many images, each with its own size and odd filter side 1..15, convolved in

@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "pencil.h")
 PENCIL_F32 = 0
 PENCIL_F16 = 1
 PENCIL_CONV_GENERIC = 1
+PENCIL_LAYOUT_HWC = 4  # channels interleaved [h][w][c] instead of planar [c][h][w]
 PENCIL_BORDER_CLAMP, PENCIL_BORDER_ZERO, PENCIL_BORDER_REFLECT, PENCIL_BORDER_MIRROR, PENCIL_BORDER_WRAP = range(5)
 BORDER_MODES = {"clamp": 0, "zero": 1, "reflect": 2, "mirror": 3, "wrap": 4}
 
@@ -80,6 +81,7 @@ def lib():
         "pencil_residual2d": (i, [i, i, vp, d, vp, sz, vp]),
         "pencil_jacobi2d_noalloc": (i, [i, i, vp, i, i, d, i, vp]),
         "pencil_conv2d_chain": (i, [i, i, i, vp, i, i, vp, i, i, vp, vp, i, i, vp]),
+        "pencil_conv2d_jacobi": (i, [i, i, i, vp, i, i, vp, i, vp, i, vp]),
         "pencil_op2_plan_create": (i, [i, i, vp, ctypes.POINTER(ctypes.c_void_p)]),
         "pencil_op2_inc": (i, [vp, vp, vp, i, vp]),
         "pencil_op2_plan_destroy": (i, [vp]),
@@ -191,6 +193,11 @@ def pencil_residual2d(h, w, u, res_out, workspace, ws_bytes, stream=None):
 def pencil_conv2d_chain(c, h, w, inp, kh1, kw1, k1, kh2, kw2, k2, out, dtype, flags=0, stream=None):
     _check(lib().pencil_conv2d_chain(c, h, w, _ptr(inp), kh1, kw1, _ptr(k1), kh2, kw2, _ptr(k2), _ptr(out),
                                      dtype, flags, _stream(stream)), "pencil_conv2d_chain")
+
+
+def pencil_conv2d_jacobi(c, h, w, inp, kh, kw, k, sweeps, out, flags=0, stream=None):
+    _check(lib().pencil_conv2d_jacobi(c, h, w, _ptr(inp), kh, kw, _ptr(k), sweeps, _ptr(out), flags,
+                                      _stream(stream)), "pencil_conv2d_jacobi")
 
 
 PENCIL_CHAIN_FUSED = 2

@@ -218,10 +218,13 @@ int pencil_device_info(char *name, int len, int *sm_count, int *driver_version) 
 int pencil_last_cuda_error(void) { return g_last_cuda; }
 
 int pencil_device_status(void) {
-    unsigned n = 0;
+    unsigned n = 0, m = 0;
+    unsigned q = 0;
     cudaError_t e = wait_timeouts(&n, true);
+    if (e == cudaSuccess) e = wait_timeouts_hwc(&m, true);
+    if (e == cudaSuccess) e = wait_timeouts_cj(&q, true);
     if (e != cudaSuccess) return cuda_fail(e);
-    return n ? PENCIL_ERR_TIMEOUT : PENCIL_OK;
+    return n + m + q ? PENCIL_ERR_TIMEOUT : PENCIL_OK;
 }
 
 int pencil_selftest_wait_timeout(unsigned limit_us, int *completed) {
@@ -236,37 +239,51 @@ void pencil_shutdown(void) {
     pool().release();
 }
 
+// Interleaved images: one row of w pixels is w*c elements, an int in the kernels.
+int check_layout(int c, int w, int flags) {
+    if ((flags & PENCIL_LAYOUT_HWC) && (int64_t)w * c > INT32_MAX) return PENCIL_ERR_UNSUPPORTED;
+    return PENCIL_OK;
+}
+
 int pencil_conv2d_ex(int c, int h, int w, const void *in, int kh, int kw, const float *k, void *out,
                      int dtype, int flags, void *stream) {
     const int border = (flags >> 8) & 0xF;
-    if (c <= 0 || kh <= 0 || kw <= 0 || (flags & ~(PENCIL_CONV_GENERIC | 0xF00)) != 0 ||
+    if (c <= 0 || kh <= 0 || kw <= 0 || (flags & ~(PENCIL_CONV_GENERIC | PENCIL_LAYOUT_HWC | 0xF00)) != 0 ||
         border > PENCIL_BORDER_WRAP)
         return PENCIL_ERR_ARG;
     if (dtype != PENCIL_F32 && dtype != PENCIL_F16) return PENCIL_ERR_ARG;
     int st = check_dims(h, w);
     if (st) return st;
     if (c > PENCIL_MAX_CHANNELS) return PENCIL_ERR_UNSUPPORTED;
+    if ((st = check_layout(c, w, flags))) return st;
     if (!in || !k || !out) return PENCIL_ERR_NULL;
     const size_t nb = (size_t)c * h * w * elem_size(dtype);
     if (overlaps(out, nb, in, nb) || overlaps(out, nb, k, sizeof(float) * (size_t)kh * kw))
         return PENCIL_ERR_ALIAS;
     if (kind_of(in) != Mem::Device || kind_of(out) != Mem::Device || kind_of(k) != Mem::Device)
         return PENCIL_ERR_PTR;
-    cudaError_t e = (flags & PENCIL_CONV_GENERIC)
-                        ? launch_conv2d_generic(dtype, c, h, w, in, kh, kw, k, out, (cudaStream_t)stream, border)
-                        : launch_conv2d(dtype, c, h, w, in, kh, kw, k, out, (cudaStream_t)stream, border);
+    const cudaStream_t s = (cudaStream_t)stream;
+    const bool generic = flags & PENCIL_CONV_GENERIC;
+    cudaError_t e;
+    if ((flags & PENCIL_LAYOUT_HWC) && c > 1)  // one channel interleaved is the planar layout
+        e = generic ? launch_conv2d_hwc_generic(dtype, c, h, w, in, kh, kw, k, out, s, border)
+                    : launch_conv2d_hwc(dtype, c, h, w, in, kh, kw, k, out, s, border);
+    else
+        e = generic ? launch_conv2d_generic(dtype, c, h, w, in, kh, kw, k, out, s, border)
+                    : launch_conv2d(dtype, c, h, w, in, kh, kw, k, out, s, border);
     return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
 }
 
 int pencil_conv2d_sep_ex(int c, int h, int w, const void *in, int kx, const float *gx, int ky,
                          const float *gy, void *out, int dtype, int flags, void *stream) {
     const int border = (flags >> 8) & 0xF;
-    if (c <= 0 || kx <= 0 || ky <= 0 || (flags & ~0xF00) != 0 || border > PENCIL_BORDER_WRAP)
+    if (c <= 0 || kx <= 0 || ky <= 0 || (flags & ~(PENCIL_LAYOUT_HWC | 0xF00)) != 0 || border > PENCIL_BORDER_WRAP)
         return PENCIL_ERR_ARG;
     if (dtype != PENCIL_F32 && dtype != PENCIL_F16) return PENCIL_ERR_ARG;
     int st = check_dims(h, w);
     if (st) return st;
     if (c > PENCIL_MAX_CHANNELS) return PENCIL_ERR_UNSUPPORTED;
+    if ((st = check_layout(c, w, flags))) return st;
     if (!in || !gx || !gy || !out) return PENCIL_ERR_NULL;
     if (kx > PENCIL_MAX_SPECIALISED_K || ky > PENCIL_MAX_SPECIALISED_K) return PENCIL_ERR_UNSUPPORTED;
     const size_t nb = (size_t)c * h * w * elem_size(dtype);
@@ -276,7 +293,55 @@ int pencil_conv2d_sep_ex(int c, int h, int w, const void *in, int kx, const floa
     if (kind_of(in) != Mem::Device || kind_of(out) != Mem::Device || kind_of(gx) != Mem::Device ||
         kind_of(gy) != Mem::Device)
         return PENCIL_ERR_PTR;
-    cudaError_t e = launch_conv2d_sep(dtype, c, h, w, in, kx, gx, ky, gy, out, (cudaStream_t)stream, border);
+    cudaError_t e = (flags & PENCIL_LAYOUT_HWC) && c > 1
+                        ? launch_conv2d_sep_hwc(dtype, c, h, w, in, kx, gx, ky, gy, out, (cudaStream_t)stream, border)
+                        : launch_conv2d_sep(dtype, c, h, w, in, kx, gx, ky, gy, out, (cudaStream_t)stream, border);
+    return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
+}
+
+int pencil_conv2d_jacobi(int c, int h, int w, const float *in, int kh, int kw, const float *k, int sweeps,
+                         float *out, int flags, void *stream) {
+    if (c <= 0 || kh <= 0 || kw <= 0 || sweeps < 0 || (flags & ~PENCIL_CHAIN_FUSED) != 0) return PENCIL_ERR_ARG;
+    int st = check_dims(h, w);
+    if (st) return st;
+    if (c > PENCIL_MAX_CHANNELS) return PENCIL_ERR_UNSUPPORTED;
+    if (!in || !k || !out) return PENCIL_ERR_NULL;
+    const size_t plane = (size_t)h * w, nb = sizeof(float) * (size_t)c * plane;
+    if (overlaps(out, nb, in, nb) || overlaps(out, nb, k, sizeof(float) * (size_t)kh * kw)) return PENCIL_ERR_ALIAS;
+    if (kind_of(in) != Mem::Device || kind_of(out) != Mem::Device || kind_of(k) != Mem::Device)
+        return PENCIL_ERR_PTR;
+    const bool fusable = sweeps > 0 && conv_jacobi_fusable(h, w, kh, kw, in, out);
+    if ((flags & PENCIL_CHAIN_FUSED) && !fusable) return PENCIL_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    int done = 0;  // sweeps already applied
+    if (fusable) {
+        done = std::min(sweeps, kConvJacobiMaxSweeps);
+        e = launch_conv_jacobi_fused(c, h, w, in, kh, k, done, out, s);
+    } else {
+        e = launch_conv2d(PENCIL_F32, c, h, w, in, kh, kw, k, out, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (done == sweeps || h < 3 || w < 3) return PENCIL_OK;
+    // the remaining sweeps, per channel, through a stream-ordered workspace
+    const size_t wsb = jacobi_workspace_bytes(h, w);
+    void *ws = nullptr;
+    cudaMemPool_t mp = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(pool().mu);
+        mp = pool().stream_pool();
+    }
+    if (!mp) return PENCIL_ERR_NOMEM;
+    e = cudaMallocFromPoolAsync(&ws, wsb, mp, s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return PENCIL_ERR_NOMEM;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int ch = 0; ch < c && e == cudaSuccess; ++ch)
+        e = jacobi_run(h, w, out + ch * plane, sweeps - done, 0, nullptr, ws, wsb, 0, s);
+    const cudaError_t ef = cudaFreeAsync(ws, s);
+    if (e == cudaSuccess) e = ef;
     return e == cudaSuccess ? PENCIL_OK : cuda_fail(e);
 }
 

@@ -51,15 +51,45 @@ __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wa
 cudaError_t launch_conv2d(int dtype, int c, int h, int w, const void *in, int kh, int kw,
                           const float *k, void *out, cudaStream_t s, int border = 0);
 // Force the generic (any-size) kernel; used by tests of the fixed-order rule.
+// cs = 0: c planar channels; cs = c > 1: one interleaved [h][w][c] image.
 cudaError_t launch_conv2d_generic(int dtype, int c, int h, int w, const void *in, int kh, int kw,
-                                  const float *k, void *out, cudaStream_t s, int border = 0);
+                                  const float *k, void *out, cudaStream_t s, int border = 0, int cs = 0);
+cudaError_t launch_conv2d_sep_generic(int dtype, int c, int h, int w, const void *in, int kx, const float *gx,
+                                      int ky, const float *gy, void *out, cudaStream_t s, int border = 0,
+                                      int cs = 0);
 cudaError_t launch_conv2d_sep(int dtype, int c, int h, int w, const void *in, int kx,
                               const float *gx, int ky, const float *gy, void *out,
                               cudaStream_t s, int border = 0);
 
+// Interleaved [h][w][c] images (c > 1): the same operations per channel.
+cudaError_t launch_conv2d_hwc(int dtype, int c, int h, int w, const void *in, int kh, int kw,
+                              const float *k, void *out, cudaStream_t s, int border = 0);
+cudaError_t launch_conv2d_hwc_generic(int dtype, int c, int h, int w, const void *in, int kh, int kw,
+                                      const float *k, void *out, cudaStream_t s, int border = 0);
+cudaError_t launch_conv2d_sep_hwc(int dtype, int c, int h, int w, const void *in, int kx,
+                                  const float *gx, int ky, const float *gy, void *out,
+                                  cudaStream_t s, int border = 0);
+
+// The tiled interleaved kernels, one translation unit per (channels, dtype);
+// we = w * channels elements per row.
+#define PENCIL_HWC_DECL(NAME)                                                                           \
+    cudaError_t hwc_direct_##NAME(int K, int h, int we, const void *in, const float *k, void *out,      \
+                                  bool vec_ok, int border, cudaStream_t s);                             \
+    cudaError_t hwc_sep_##NAME(int K, int h, int we, const void *in, const float *gx, const float *gy,  \
+                               void *out, bool vec_ok, int border, cudaStream_t s);                     \
+    cudaError_t wait_timeouts_##NAME(unsigned *n, bool clear);
+PENCIL_HWC_DECL(hwc3_f32)
+PENCIL_HWC_DECL(hwc3_f16)
+PENCIL_HWC_DECL(hwc4_f32)
+PENCIL_HWC_DECL(hwc4_f16)
+#undef PENCIL_HWC_DECL
+
 // Tile loads whose bounded wait ran out since the last clear (each skipped its
-// tile); clear resets the count.
+// tile); clear resets the count.  Each translation unit of kernels keeps its
+// own counter: wait_timeouts reads the planar unit's, wait_timeouts_hwc the sum
+// of the interleaved units'.
 cudaError_t wait_timeouts(unsigned *n, bool clear);
+cudaError_t wait_timeouts_hwc(unsigned *n, bool clear);
 // Run the bounded mbarrier wait against a barrier that never completes, for
 // limit_ns; *completed = 1 if it completed (it should not), 0 if it ran out.
 cudaError_t wait_selftest(uint64_t limit_ns, int *completed);
@@ -71,6 +101,16 @@ cudaError_t launch_conv2d_chain(int dtype, int c, int h, int w, const void *in, 
                                 bool generic, cudaStream_t s);
 // Shared memory the generic chain kernel needs for a second filter of kh2 x kw2.
 size_t chain_generic_smem(int kh2, int kw2);
+
+// conv -> Jacobi fused (conv_jacobi.cu): square odd filters up to
+// kConvJacobiMaxK, rows of w % 4 == 0 floats, 16-byte aligned buffers, at most
+// kConvJacobiMaxSweeps sweeps per launch.
+constexpr int kConvJacobiMaxK = 7;
+constexpr int kConvJacobiMaxSweeps = 10;
+bool conv_jacobi_fusable(int h, int w, int kh, int kw, const void *in, const void *out);
+cudaError_t launch_conv_jacobi_fused(int c, int h, int w, const float *in, int ks, const float *k, int n,
+                                     float *out, cudaStream_t s);
+cudaError_t wait_timeouts_cj(unsigned *n, bool clear);
 
 // ----------------------------------------------------------------- jacobi
 size_t jacobi_workspace_bytes(int h, int w);

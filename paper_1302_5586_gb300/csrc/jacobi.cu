@@ -30,29 +30,13 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
-#include "internal.cuh"
+#include "jacobi_tile.cuh"
 
 namespace pencil {
 namespace {
 
 constexpr int JT = 128;  // threads per block
 constexpr int JR = 16;   // rows per thread
-constexpr unsigned FULL = 0xffffffffu;
-
-__device__ __forceinline__ void acc_sq(float r, float &hi, float &lo) {
-    const float p = __fmul_rn(r, r);
-    const float e = __fmaf_rn(r, r, -p);  // p + e == r*r exactly
-    const float t = __fadd_rn(hi, p);
-    const float bp = __fsub_rn(t, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));
-    hi = t;
-    lo = __fadd_rn(lo, __fadd_rn(err, e));
-}
-
-__device__ __forceinline__ float nsum(float up, float dn, float lf, float rt) {
-    return __fadd_rn(__fadd_rn(up, dn), __fadd_rn(lf, rt));
-}
-
 // Sum one double per thread over the block in a fixed order; thread 0 writes it.
 __device__ __forceinline__ void block_sum_store(double d, double *dst) {
     __shared__ double wsum[JT / 32];
@@ -225,158 +209,25 @@ __global__ void __launch_bounds__(256) residual_finish_kernel(const double *__re
     }
 }
 
-// ------------------------------------------------------ temporal tiling
-// Up to T sweeps per HBM round trip with the tile held in registers.  A CTA
-// owns a window of NW*RS rows x 128 columns (lane l: columns 4l .. 4l+3; warp
-// k: rows k*RS .. k*RS+RS-1) and its core, rows [T, NW*RS-T) x columns
-// [P, 128-P) with P = T rounded up to 4.  It loads the window once, runs the
-// sweeps on registers -- each warp updates its rows top to bottom, taking
-// left/right neighbours from adjacent lanes (shuffles) and the rows just
-// outside its band from the neighbouring warps through shared memory (one
-// barrier per sweep) -- and writes the core back.  Window rows 0 and NW*RS-1
-// and columns 0 and 127 have no neighbours and take their own values in
-// their place; the wrong values this makes move inward one point per sweep,
-// like stale halo data, so after T sweeps the core is exact.  Grid boundary
-// points keep their values.  Per point the update is the same FP32
-// expression as the one-sweep kernel, so the iterate is the same bits for
-// every T.  Residuals of iterates inside the pass are accumulated, over core
-// points, during the sweep that updates them.
-template <int T>
-struct RegCfg {
-    static constexpr int NW = 8;              // warps
-    static constexpr int RS = 16;             // rows per warp
-    static constexpr int NT = 32 * NW;
-    static constexpr int W = 128;             // window columns: 32 lanes x 4
-    static constexpr int SH = NW * RS;        // window rows
-    static constexpr int P = round_up(T, 4);  // core starts at window column P (16-byte aligned)
-    static constexpr int BW = W - 2 * P;      // core columns
-    static constexpr int BH = SH - 2 * T;     // core rows
-};
-
-// One sweep over a warp's RS rows, row r held in y[OFF + r].  DOWN: rows
-// are updated top to bottom and new row r goes to y[OFF + r - 1] (the slot of
-// old row r-1, dead once row r is done); otherwise bottom to top into
-// y[OFF + r + 1].  A DOWN sweep from OFF = 1 and an up sweep from OFF = 0
-// bring the band back to its slots without a register copy.  above/below:
-// the rows just outside the band (old values).  EDGE: the window reaches the
-// grid boundary, so points there (and outside the grid) keep their values.
-template <int RS, bool DOWN, int OFF, bool EDGE, bool RESID>
-__device__ __forceinline__ void reg_sweep(float4 (&y)[RS + 1], const float4 above, const float4 below, int g_first,
-                                          int h, const bool (&cint)[4], bool core_cols, int core_lo, int core_hi,
-                                          float &hi, float &lo) {
-#pragma unroll
-    for (int k = 0; k < RS; ++k) {
-        const int r = DOWN ? k : RS - 1 - k;
-        const float4 cur = y[OFF + r];
-        const float4 upv = r > 0 ? y[OFF + r - 1] : above;
-        const float4 dn = r + 1 < RS ? y[OFF + r + 1] : below;
-        const float lf = __shfl_up_sync(FULL, cur.w, 1);    // lane 0: its own value (window column 0)
-        const float rt = __shfl_down_sync(FULL, cur.x, 1);  // lane 31: its own value (window column 127)
-        const float sx = nsum(upv.x, dn.x, lf, cur.y);
-        const float sy = nsum(upv.y, dn.y, cur.x, cur.z);
-        const float sz = nsum(upv.z, dn.z, cur.y, cur.w);
-        const float sw = nsum(upv.w, dn.w, cur.z, rt);
-        float4 nv = make_float4(__fmul_rn(0.25f, sx), __fmul_rn(0.25f, sy), __fmul_rn(0.25f, sz),
-                                __fmul_rn(0.25f, sw));
-        const int g = g_first + r;
-        if (EDGE) {
-            const bool rint = g >= 1 && g <= h - 2;
-            nv.x = (rint && cint[0]) ? nv.x : cur.x;
-            nv.y = (rint && cint[1]) ? nv.y : cur.y;
-            nv.z = (rint && cint[2]) ? nv.z : cur.z;
-            nv.w = (rint && cint[3]) ? nv.w : cur.w;
-        }
-        if (RESID && core_cols && g >= core_lo && g < core_hi && g >= 1 && g <= h - 2) {
-            if (cint[0]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.x), sx), hi, lo);
-            if (cint[1]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.y), sy), hi, lo);
-            if (cint[2]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.z), sz), hi, lo);
-            if (cint[3]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.w), sw), hi, lo);
-        }
-        y[DOWN ? OFF + r - 1 : OFF + r + 1] = nv;
-    }
-}
-
-// One sweep (DOWN from slots 1..RS, or up from slots 0..RS-1), with the band
-// edge rows exchanged first and, on checkpoint iterates, the residual partial
-// of the warp recorded in wres.
-template <int RS, int NW, bool DOWN, bool EDGE>
-__device__ __forceinline__ void reg_step(float4 (&y)[RS + 1], int t, int iter0, int check_every, float4 *xch,
-                                         double *wres, int &slot, int g_first, int h, const bool (&cint)[4],
-                                         bool core_cols, int core_lo, int core_hi) {
-    constexpr int OFF = DOWN ? 1 : 0;
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int it = iter0 + t;
-    const bool resid = check_every > 0 && it > 0 && it % check_every == 0;
-    // band edge rows to the neighbours (double-buffered by sweep parity)
-    float4 *xb = xch + (t & 1) * (NW * 2 * 32);
-    xb[(wp * 2 + 0) * 32 + lane] = y[OFF];
-    xb[(wp * 2 + 1) * 32 + lane] = y[OFF + RS - 1];
-    __syncthreads();
-    const float4 above = wp > 0 ? xb[((wp - 1) * 2 + 1) * 32 + lane] : y[OFF];
-    const float4 below = wp < NW - 1 ? xb[((wp + 1) * 2 + 0) * 32 + lane] : y[OFF + RS - 1];
-    if (resid) {
-        float hi = 0.f, lo = 0.f;
-        reg_sweep<RS, DOWN, OFF, EDGE, true>(y, above, below, g_first, h, cint, core_cols, core_lo, core_hi, hi, lo);
-        // this iterate's partial: fixed butterfly per warp, warps in order later
-        double d = (double)hi + (double)lo;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(FULL, d, off);
-        if (lane == 0) wres[slot * NW + wp] = d;
-        ++slot;
-    } else {
-        float hi = 0.f, lo = 0.f;
-        reg_sweep<RS, DOWN, OFF, EDGE, false>(y, above, below, g_first, h, cint, core_cols, core_lo, core_hi, hi,
-                                              lo);
-    }
-}
-
 template <int T, bool EDGE>
 __device__ __forceinline__ void jacobi_reg_body(const float *__restrict__ u, float *__restrict__ v, int h, int w,
                                                 int n, int gy0, int gx0, int iter0, int check_every,
                                                 float4 *xch, double *wres) {
     using Cfg = RegCfg<T>;
-    constexpr int RS = Cfg::RS, NW = Cfg::NW, P = Cfg::P, BW = Cfg::BW;
+    constexpr int RS = Cfg::RS;
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int gc0 = gx0 + 4 * lane;
-    const bool chunk_in = gc0 >= 0 && gc0 < w;  // w % 4 == 0: a chunk is wholly in or out
-    const bool core_cols = 4 * lane >= P && 4 * lane < P + BW && gc0 < w;
-    bool cint[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) cint[e] = gc0 + e >= 1 && gc0 + e <= w - 2;
-    const int g_first = gy0 + wp * RS;  // global row of this warp's first row
-    const int core_lo = gy0 + T, core_hi = min(h, gy0 + T + Cfg::BH);
-
+    const RegGeom<T> q(h, w, gy0, gx0);
+    const bool chunk_in = q.gc0 >= 0 && q.gc0 < w;  // w % 4 == 0: a chunk is wholly in or out
     float4 y[RS + 1];  // row r in y[1 + r] between pairs of sweeps
     y[0] = z4;
 #pragma unroll
     for (int r = 0; r < RS; ++r) {
-        const int g = g_first + r;
-        y[1 + r] = (g >= 0 && g < h && chunk_in) ? __ldg(reinterpret_cast<const float4 *>(u + (size_t)g * w + gc0))
-                                                 : z4;
+        const int g = q.g_first + r;
+        y[1 + r] = (g >= 0 && g < h && chunk_in)
+                       ? __ldg(reinterpret_cast<const float4 *>(u + (size_t)g * w + q.gc0))
+                       : z4;
     }
-    int slot = 0;
-    int t = 0;
-#pragma unroll 1
-    for (; t + 1 < n; t += 2) {
-        reg_step<RS, NW, true, EDGE>(y, t, iter0, check_every, xch, wres, slot, g_first, h, cint, core_cols,
-                                     core_lo, core_hi);
-        reg_step<RS, NW, false, EDGE>(y, t + 1, iter0, check_every, xch, wres, slot, g_first, h, cint, core_cols,
-                                      core_lo, core_hi);
-    }
-    const int base = (t < n) ? 0 : 1;  // an odd count ends with one more DOWN sweep
-    if (t < n)
-        reg_step<RS, NW, true, EDGE>(y, t, iter0, check_every, xch, wres, slot, g_first, h, cint, core_cols,
-                                     core_lo, core_hi);
-    // the core back to HBM
-    if (core_cols) {
-#pragma unroll
-        for (int r = 0; r < RS; ++r) {
-            const int g = g_first + r;
-            if (g >= core_lo && g < core_hi)
-                *reinterpret_cast<float4 *>(v + (size_t)g * w + gc0) = base ? y[1 + r] : y[r];
-        }
-    }
+    reg_sweeps_store<T, EDGE>(y, v, h, w, n, q, iter0, check_every, xch, wres);
 }
 
 template <int T>

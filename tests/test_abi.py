@@ -105,7 +105,11 @@ def test_conv2d_argument_errors_before_cuda(lib, args, status):
 
 def test_ex_argument_errors_before_cuda(lib):
     assert lib.pencil_conv2d_ex(1, 4, 4, 1, 3, 3, 2, 3, 7, 0, None) == -1   # bad dtype
-    assert lib.pencil_conv2d_ex(1, 4, 4, 1, 3, 3, 2, 3, 0, 4, None) == -1   # unknown flag
+    assert lib.pencil_conv2d_ex(1, 4, 4, 1, 3, 3, 2, 3, 0, 8, None) == -1   # unknown flag
+    # interleaved rows of w*c elements must fit an int
+    assert lib.pencil_conv2d_ex(3, 1, 1 << 30, 1, 3, 3, 2, 3, 0, pg.PENCIL_LAYOUT_HWC, None) == -8
+    assert lib.pencil_conv2d_sep_ex(3, 1, 1 << 30, 1, 3, 2, 3, 3, 5, 0, pg.PENCIL_LAYOUT_HWC, None) == -8
+    assert lib.pencil_conv2d_ex(3, 1, 1 << 30, 1, 3, 3, 2, 3, 0, 0, None) != -8  # planar rows are not limited
     assert lib.pencil_conv2d_sep_ex(1, 4, 4, 1, 17, 2, 3, 3, 5, 0, 0, None) == -8  # side > 15
     assert lib.pencil_conv2d_ex(1, 4, 4, 1, 3, 3, 2, 3, 0, 5 << 8, None) == -1   # border mode 5
     assert lib.pencil_conv2d_sep_ex(1, 4, 4, 1, 3, 2, 3, 3, 5, 0, 1, None) == -1  # generic flag not allowed
@@ -125,6 +129,11 @@ def test_ex_argument_errors_before_cuda(lib):
     assert lib.pencil_jacobi2d_ex(tall, 4, 1, 10, 0, None, 256, 1 << 40, 0, None) == -8
     assert lib.pencil_rbsor2d_ex(tall, 4, 1, 10, 1.5, 0, None, 256, 1 << 40, None) == -8
     assert lib.pencil_conv2d(tall, 4, 1, 3, 3, 2, 3) == -8
+    # conv -> Jacobi: sweeps < 0, unknown flags, NULL arrays, rows beyond the grid limit
+    assert lib.pencil_conv2d_jacobi(1, 8, 8, 1, 3, 3, 2, -1, 3, 0, None) == -1
+    assert lib.pencil_conv2d_jacobi(1, 8, 8, 1, 3, 3, 2, 5, 3, 1, None) == -1
+    assert lib.pencil_conv2d_jacobi(1, 8, 8, None, 3, 3, 2, 5, 3, 0, None) == -2
+    assert lib.pencil_conv2d_jacobi(1, tall, 8, 1, 3, 3, 2, 5, 3, 0, None) == -8
 
 
 def test_binding_refuses_missing_library(monkeypatch, tmp_path):
@@ -151,6 +160,7 @@ def test_binding_constants_match_the_header():
     import re
     text = open(pg.HEADER).read()
     for name in ("PENCIL_MAX_ROWS", "PENCIL_MAX_CHANNELS", "PENCIL_CHAIN_FUSED", "PENCIL_CONV_GENERIC",
+                 "PENCIL_LAYOUT_HWC",
                  "PENCIL_OP2_ORDERED", "PENCIL_OP2_ATOMIC", "PENCIL_F32", "PENCIL_F16"):
         m = re.search(r"#define\s+%s\s+(\d+)" % name, text) or re.search(r"\b%s\s*=\s*(\d+)" % name, text)
         assert m, name
