@@ -422,7 +422,7 @@ SERVE_SAMPLE_EVERY = 97  # every 97th request of the 2000 req/s replay is kept a
 def _serve_brief(st):
     d = st.summary()
     return {k: d[k] for k in ("requests", "rejected", "p50_ms", "p99_ms", "max_ms", "gpx_s", "req_s", "mean_wave",
-                              "peak_inflight", "peak_arena_mib")}
+                              "batched_waves", "peak_inflight", "peak_arena_mib")}
 
 
 def measure_serving(torch, pg, dev, seconds):

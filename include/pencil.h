@@ -432,7 +432,12 @@ int pencil_last_cuda_error(void);
  * arrive within its limit of about a second; that tile's outputs were not
  * written), else PENCIL_OK.  Clears the count.  Stream-ordered calls report
  * their waits here, so call it after synchronising the streams that ran
- * them.  The library's kernels never wait without a limit.  Errors: CUDA. */
+ * them.  The library's kernels never wait without a limit.  A CTA whose
+ * load timed out waits once more (same limit) for the copy to land before it
+ * exits; if even that runs out it exits all the same, and the late copy may
+ * then land in shared memory that a later CTA on that SM is using.  So after
+ * PENCIL_ERR_TIMEOUT treat every result computed since the previous check as
+ * suspect, not only the skipped tiles.  Errors: CUDA. */
 int pencil_device_status(void);
 
 /* Self-test of the bounded wait: one CTA waits up to limit_us microseconds

@@ -11,8 +11,10 @@ a Poisson trace.  The scheduler loop:
 * packs every request admitted in one pass into a wave and issues it on the
   next of `streams` CUDA streams: host-to-device copies of the inputs (from
   pinned host memory into the arena), ONE batched persistent conv2d launch
-  (pencil_batch_run, graph replay; one plan per stream), device-to-host copies
-  of the outputs, and an event;
+  (pencil_batch_run, graph replay; one plan per stream) -- or, for a wave of
+  a single request, its one standalone launch, which costs the host less
+  than building a batch table and gives the same bits -- device-to-host
+  copies of the outputs, and an event;
 * polls the events of the waves in flight; a finished wave's requests are
   timestamped (latency = completion - arrival) and their arena blocks freed.
 
@@ -184,6 +186,7 @@ class Stats:
     peak_arena_bytes: int
     cancelled: int = 0
     expired: int = 0
+    batched_waves: int = 0
 
     def summary(self) -> dict:
         lat = self.latency_ms
@@ -197,7 +200,8 @@ class Stats:
             "max_ms": round(float(ok.max()), 3) if ok.size else None,
             "gpx_s": round(self.pixels / self.wall_s / 1e9, 3) if self.wall_s > 0 else None,
             "req_s": round(ok.size / self.wall_s, 1) if self.wall_s > 0 else None,
-            "waves": self.waves, "mean_wave": round(ok.size / max(self.waves, 1), 2),
+            "waves": self.waves, "batched_waves": self.batched_waves,
+            "mean_wave": round(ok.size / max(self.waves, 1), 2),
             "peak_inflight": self.peak_inflight, "peak_arena_mib": round(self.peak_arena_bytes / 2**20, 1),
         }
 
@@ -286,6 +290,7 @@ class Server:
         peak_inflight = 0
         peak_arena = 0
         waves = 0
+        batched = 0
         done = 0
         pix = 0
         nxt = 0
@@ -324,10 +329,11 @@ class Server:
                     for r, oi, _ in wave:
                         hw = r.h * r.w
                         self._view(oi, hw).copy_(host_pool[r.src:r.src + hw], non_blocking=True)
-                    if mode == "served":
+                    if mode == "served" and len(wave) > 1:
                         imgs = b.make_images([(self.pool.data_ptr() + oi, self.pool.data_ptr() + oo,
                                                kbase + 4 * r.filt, r.h, r.w, r.ks) for r, oi, oo in wave])
                         b.pencil_batch_run(plan, imgs, s.cuda_stream)
+                        batched += 1
                     else:
                         for r, oi, oo in wave:
                             b.pencil_conv2d_ex(1, r.h, r.w, self.pool.data_ptr() + oi, r.ks, r.ks,
@@ -362,7 +368,7 @@ class Server:
         first = reqs[0].arrival if n else 0.0
         wall = (last_done - t0) - first
         st = Stats(mode, n, adm.rejected, pix, wall, lat, waves, peak_inflight, peak_arena, adm.cancelled,
-                   adm.expired)
+                   adm.expired, batched)
         if outputs is not None:
             outputs = [o.view(r.h, r.w) if o is not None else None for o, r in zip(outputs, reqs)]
         return st, outputs

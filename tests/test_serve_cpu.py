@@ -252,6 +252,7 @@ def test_server_loop_on_a_fake_device(fake_server, mode):
         r.arrival = 0.0
     pool = torch.arange(tr.pool_elems, dtype=torch.float32)
     cancel = {3, 17, n - 1}
+    runs0 = fake.batch_runs  # the server's warm-up runs
     st, outs = srv.run(tr, pool, torch.zeros(1), mode=mode, keep_outputs=True, cancel=cancel)
     assert st.cancelled == len(cancel) and st.rejected == 0 and st.expired == 0
     for r in tr.requests:
@@ -263,6 +264,9 @@ def test_server_loop_on_a_fake_device(fake_server, mode):
     assert pg.pencil_arena_free_bytes(srv.arena) == 1 << 20
     assert st.peak_inflight <= 24 and 0 < st.peak_arena_bytes <= 1 << 20
     assert (st.waves < n - len(cancel)) if mode == "served" else (st.waves == n - len(cancel))
+    # waves of several requests take one batched launch, single requests their own launch
+    assert fake.batch_runs - runs0 == st.batched_waves and (0 < st.batched_waves <= st.waves if mode == "served"
+                                                    else st.batched_waves == 0)
     # without kept outputs the results go through the wrapping host sink; a
     # zero deadline drops every request that was not admitted the moment it arrived
     st2, none = srv.run(tr, pool, torch.zeros(1), mode=mode, sink_bytes=4096, deadline_ms=0.0)
