@@ -194,10 +194,11 @@ int pencil_conv2d_jacobi(int c, int h, int w, const float *in, int kh, int kw, c
                          float *out, int flags, void *stream);
 
 /* ------------------------------------------------------------------- batch
- * Many images, each with its own size and odd filter side 1..15, convolved in
- * ONE persistent kernel launch replayed from a CUDA graph.  The tiles of all
- * images are handed out from one work queue, most expensive first (larger
- * filter side, then larger image), so uneven images keep every SM busy; each
+ * Many images, each with its own size and odd filter side 1..15, convolved by
+ * ONE graph launch: the captured graph holds one persistent kernel per filter
+ * side present (largest side first, back to back), each sized to its side's
+ * register and shared-memory needs.  A side's tiles are handed out from its
+ * own work queue, larger images first, so uneven images keep every SM busy; each
  * batched pixel is the same bits as pencil_conv2d_ex on that image alone (the
  * same fixed per-pixel order).  This is the tuned, launch-once form of the
  * independent loop over images and pixels (Sec. 2.2.3); the tile shape per

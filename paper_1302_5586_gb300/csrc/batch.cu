@@ -84,9 +84,16 @@ struct Slot {
 // on GB300 over the 512-image benchmark batch.  Two slots let a CTA's next
 // tile copy while it computes the current one; where one slot wins, more
 // resident CTAs hide the copies better than the prefetch does.
-constexpr int kNslot[2][kSides] = {{2, 1, 1, 1, 1, 1, 2, 1},   // FP32, sides 1, 3, ..., 15
-                                   {2, 2, 1, 1, 1, 1, 1, 1}};  // binary16
-constexpr int kRegCap[2][kSides] = {{8, 8, 8, 8, 5, 4, 4, 4}, {8, 8, 8, 8, 6, 4, 4, 4}};
+// (A timing sweep may build other tables by defining the macros in a header
+// it force-includes; the library uses these.)
+#ifndef PENCIL_BATCH_NSLOT
+#define PENCIL_BATCH_NSLOT {{2, 1, 1, 1, 1, 1, 2, 1}, {2, 2, 1, 1, 1, 1, 1, 1}}  // FP32, binary16; sides 1..15
+#endif
+#ifndef PENCIL_BATCH_REGCAP
+#define PENCIL_BATCH_REGCAP {{8, 8, 8, 8, 5, 4, 4, 4}, {8, 8, 8, 8, 6, 4, 4, 4}}
+#endif
+constexpr int kNslot[2][kSides] = PENCIL_BATCH_NSLOT;
+constexpr int kRegCap[2][kSides] = PENCIL_BATCH_REGCAP;
 template <int K>
 constexpr int nslot(size_t esz) { return kNslot[esz == 2][K / 2]; }
 template <int K>

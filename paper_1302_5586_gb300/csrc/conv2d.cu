@@ -99,7 +99,8 @@ cudaError_t run_direct_k(int K, int c, int h, int w, const T *in, const float *k
             case 1: return run_direct<T, 1, 32, 4, 8, 1, 8, true>(c, h, w, in, k, out, vec_ok, border, s);
             case 3: return run_direct<T, 3, 32, 4, 8, 1, 8, true>(c, h, w, in, k, out, vec_ok, border, s);
             case 5: return run_direct<T, 5, 32, 4, 8, 1, 8, true>(c, h, w, in, k, out, vec_ok, border, s);
-            case 7: return run_direct<T, 7, 32, 4, 8, 1, 8, true>(c, h, w, in, k, out, vec_ok, border, s);
+            // 256-thread CTAs (64-row tiles): 0.418 -> 0.394 ms on 3 x 8192^2
+            case 7: return run_direct<T, 7, 32, 8, 8, 1, 4, true>(c, h, w, in, k, out, vec_ok, border, s);
             default: break;
         }
     } else {
@@ -125,12 +126,33 @@ cudaError_t run_sep_any(int c, int h, int w, const T *in, int kx, const float *g
                         const float *gy, T *out, bool vec_ok, int border, cudaStream_t s) {
     // Tiles from timing sweeps at 8192 x 8192 x 3; the 15-tap tiles are 128
     // rows tall (the row pass recomputes 14 halo rows per tile, 11% extra).
+    // Binary16 images: the row pass reads the staged binary16 tile directly
+    // (no FP32 copy, no widening pass), 256-thread CTAs of 8 rows per thread;
+    // that measured 17-40% faster than widening the tile first on every side
+    // (15 taps: 0.375 -> 0.299 ms, 3 taps: 0.257 -> 0.156 ms).
+    if constexpr (sizeof(T) == 2) {
+        if (kx == ky) {
+            switch (kx) {
+                case 3: return run_sep<T, 3, 32, 8, 8, 3, false, sep_pair<T>(3), 1, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+                case 5: return run_sep<T, 5, 32, 8, 8, 3, false, sep_pair<T>(5), 1, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+                case 7: return run_sep<T, 7, 32, 8, 8, 3, false, sep_pair<T>(7), 1, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+                case 9: return run_sep<T, 9, 32, 8, 8, 3, false, sep_pair<T>(9), 1, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+                case 11: return run_sep<T, 11, 16, 16, 8, 3, false, sep_pair<T>(11), 1, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+                case 13: return run_sep<T, 13, 16, 16, 8, 3, false, sep_pair<T>(13), 1, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+                case 15: return run_sep<T, 15, 16, 16, 8, 3, false, sep_pair<T>(15), 1, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+                default: break;
+            }
+        }
+        return run_sep_generic<T>(c, h, w, in, kx, gx, ky, gy, out, border, s);
+    }
+    // FP32 sides 3..9: in-place tiles of 8 or 16 rows per thread measured 3-12%
+    // faster than the 4-row tiles with a separate row-pass buffer.
     if (kx == ky) {
         switch (kx) {
-            case 3: return run_sep<T, 3, 32, 8, 4, 1, false, sep_pair<T>(3)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
-            case 5: return run_sep<T, 5, 32, 8, 4, 1, false, sep_pair<T>(5)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
-            case 7: return run_sep<T, 7, 32, 8, 4, 1, false, sep_pair<T>(7)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
-            case 9: return run_sep<T, 9, 16, 8, 8, 4, true, sep_pair<T>(9)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 3: return run_sep<T, 3, 32, 4, 8, 4, true, sep_pair<T>(3)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 5: return run_sep<T, 5, 16, 8, 16, 4, true, sep_pair<T>(5)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 7: return run_sep<T, 7, 32, 4, 8, 4, true, sep_pair<T>(7)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+            case 9: return run_sep<T, 9, 16, 8, 16, 4, true, sep_pair<T>(9)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
             case 11: return run_sep<T, 11, 16, 8, 8, 4, true, sep_pair<T>(11)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
             case 13: return run_sep<T, 13, 16, 8, 8, 4, true, sep_pair<T>(13)>(c, h, w, in, gx, gy, out, vec_ok, border, s);
             case 15: return run_sep<T, 15, 16, 8, 16, 4, true, sep_pair<T>(15)>(c, h, w, in, gx, gy, out, vec_ok, border, s);

@@ -78,11 +78,11 @@ __global__ void __launch_bounds__(RegCfg<T>::NT, 2)
 #pragma unroll
     for (int r = 0; r < RS; ++r) y[1 + r] = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
     float *dst = out + (size_t)h * (size_t)w * blockIdx.z;
-    const RegGeom<T> q(h, w, gy0, gx0);
+    const RegGeom<J> q(h, w, gy0, gx0);
     if (gy0 <= 0 || gy0 + J::SH - 1 >= h - 1 || gx0 <= 0 || gx0 + J::W - 1 >= w - 1)
-        reg_sweeps_store<T, true>(y, dst, h, w, n, q, 0, 0, xch, nullptr);
+        reg_sweeps_store<J, true>(y, dst, h, w, n, q, 0, 0, xch, nullptr);
     else
-        reg_sweeps_store<T, false>(y, dst, h, w, n, q, 0, 0, xch, nullptr);
+        reg_sweeps_store<J, false>(y, dst, h, w, n, q, 0, 0, xch, nullptr);
 }
 
 template <int K, int T>

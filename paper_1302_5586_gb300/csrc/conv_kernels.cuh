@@ -190,7 +190,10 @@ __global__ void __launch_bounds__(256)
 // instruction costs the issue slots of two scalar ones, so it pays only where
 // it shortens the schedule: measured per side, see sep_pair).
 // CS > 1: interleaved images of CS channels (row-pass taps CS elements apart).
-template <int KX, int KY, int TX, int TY, int R, bool INPLACE = false, int CS = 1>
+// HALFR (binary16 images): the row pass reads the staged binary16 tile and
+// widens each window in registers, so no FP32 copy of the tile exists; its
+// results go to their own FP32 buffer (INPLACE must be false).
+template <int KX, int KY, int TX, int TY, int R, bool INPLACE = false, int CS = 1, bool HALFR = false>
 struct SepCfg {
     static constexpr int C = 4;
     static constexpr int AX = KX / 2, AY = KY / 2;
@@ -202,8 +205,11 @@ struct SepCfg {
     static constexpr int SH = TH + KY - 1;
     static constexpr int M0 = (P - AXE) & ~3;  // first 16-byte chunk a row pass reads
     static constexpr int NX = round_up(P - AXE - M0 + C + (KX - 1) * CS, 4);
-    // in place: the row-pass results overwrite the staged tile (row stride SW)
-    static constexpr size_t smem_f32 = sizeof(float) * (size_t)(SH * SW + (INPLACE ? 0 : SH * TW));
+    // in place: the row-pass results overwrite the staged tile (row stride SW);
+    // HALFR: only the row-pass results are FP32
+    static_assert(!(HALFR && INPLACE), "a binary16 tile read directly cannot take the row-pass results");
+    static constexpr size_t smem_f32 =
+        sizeof(float) * (size_t)(HALFR ? SH * TW : SH * SW + (INPLACE ? 0 : SH * TW));
     // the binary16 staging area follows, 128-byte aligned (a TMA box destination)
     static constexpr size_t off16 = (smem_f32 + 127) / 128 * 128;
     static constexpr size_t smem(size_t esz) { return esz == 2 ? off16 + 2 * (size_t)SH * SW : smem_f32; }
@@ -214,20 +220,21 @@ struct SepCfg {
 // as one TMA box of `tmap` (unused by the other modes), as the direct TMA
 // kernel does.
 template <typename T, int KX, int KY, int TX, int TY, int R, int MINB, bool INPLACE, bool ANYB, int PAIR,
-          int VMODE, int CS = 1>
+          int VMODE, int CS = 1, bool HALFR = false>
 __global__ void __launch_bounds__(TX *TY, MINB)
     conv2d_sep_kernel(const __grid_constant__ CUtensorMap tmap, const T *__restrict__ in,
                       const float *__restrict__ gx, const float *__restrict__ gy, T *__restrict__ out, int h,
                       int w, bool vec_ok_, int border) {
     constexpr bool ADAPT = VMODE == 2, TMA = VMODE == 3;
+    static_assert(!HALFR || sizeof(T) == 2, "HALFR reads a binary16 tile");
     const bool vec_ok = VMODE == 0 ? vec_ok_ : VMODE != 2;
-    using Cfg = SepCfg<KX, KY, TX, TY, R, INPLACE, CS>;
+    using Cfg = SepCfg<KX, KY, TX, TY, R, INPLACE, CS, HALFR>;
     constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, SH = Cfg::SH, TW = Cfg::TW,
                   NX = Cfg::NX, AY = Cfg::AY, NT = Cfg::NT;
     constexpr int TS = INPLACE ? SW : TW;  // row stride of the row-pass results
     extern __shared__ __align__(128) float smem[];
     float *s_in = smem;
-    float *s_t = INPLACE ? smem : smem + SH * SW;
+    float *s_t = INPLACE || HALFR ? smem : smem + SH * SW;
     T *s16 = reinterpret_cast<T *>(smem + Cfg::off16 / sizeof(float));
 
     const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
@@ -254,7 +261,11 @@ __global__ void __launch_bounds__(TX *TY, MINB)
             return;
         }
         if (border == 0) clamp_fixup<T, SH, SW, NT, CS>(s_box, h, w, y0 - AY, x0 - P);
-        stage_widen<T, SH, SW, NT>(s_in, s16);
+        if constexpr (!HALFR) stage_widen<T, SH, SW, NT>(s_in, s16);
+    } else if constexpr (HALFR) {
+        stage_issue<T, SH, SW, NT, ANYB, ADAPT, CS>(src, h, w, y0 - AY, x0 - P, vec_ok, nullptr, s16, border);
+        cp_async_wait_all();
+        __syncthreads();
     } else {
         stage_tile<T, SH, SW, NT, ANYB, ADAPT, CS>(src, h, w, y0 - AY, x0 - P, vec_ok, s_in, s16, border);
     }
@@ -274,12 +285,15 @@ __global__ void __launch_bounds__(TX *TY, MINB)
             const int idx = threadIdx.x + k * NT;
             if (idx < ITEMS) {
                 const int r = idx / QPR, q = idx - r * QPR;
-                const float *sp = s_in + r * SW + q * C + Cfg::M0;
                 float x[NX];
+                if constexpr (HALFR) {
+                    const T *sp = s16 + r * SW + q * C + Cfg::M0;
 #pragma unroll
-                for (int m = 0; m < NX; m += 4) {
-                    const float4 v = *reinterpret_cast<const float4 *>(sp + m);
-                    x[m] = v.x; x[m + 1] = v.y; x[m + 2] = v.z; x[m + 3] = v.w;
+                    for (int m = 0; m < NX; m += 4) ld4s(sp + m, &x[m]);
+                } else {
+                    const float *sp = s_in + r * SW + q * C + Cfg::M0;
+#pragma unroll
+                    for (int m = 0; m < NX; m += 4) ld4s(sp + m, &x[m]);
                 }
                 float tv[C];
                 if constexpr ((PAIR & 1) != 0) {
@@ -524,23 +538,24 @@ cudaError_t run_sep_generic(int c, int h, int w, const T *in, int kx, const floa
 }
 
 // CS > 1: w is the element width of one interleaved image (pixels * CS), c = 1.
-template <typename T, int K, int TX, int TY, int R, int MINB = 1, bool INPLACE = false, int PAIR = 0, int CS = 1>
+template <typename T, int K, int TX, int TY, int R, int MINB = 1, bool INPLACE = false, int PAIR = 0, int CS = 1,
+          bool HALFR = false>
 cudaError_t run_sep(int c, int h, int w, const T *in, const float *gx, const float *gy, T *out,
                     bool vec_ok, int border, cudaStream_t s) {
-    using Cfg = SepCfg<K, K, TX, TY, R, INPLACE, CS>;
+    using Cfg = SepCfg<K, K, TX, TY, R, INPLACE, CS, HALFR>;
     using Kern = void (*)(const CUtensorMap, const T *, const float *, const float *, T *, int, int, bool, int);
     Kern kern;
     CUtensorMap tmap = {};
     static_assert(Cfg::SW <= 256 && Cfg::SH <= 256, "a TMA box side is at most 256 elements");
     if (vec_ok && (border == 0 || border == 1) && image_tensor_map<T>(&tmap, in, c, h, w, Cfg::SW, Cfg::SH)) {
-        kern = conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 3, CS>;  // TMA staging
+        kern = conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 3, CS, HALFR>;  // TMA staging
     } else if constexpr (K <= 5 && CS == 1) {  // as for the direct kernels
-        kern = border != 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 2>
-               : vec_ok    ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 1>
-                           : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 2>;
+        kern = border != 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 2, 1, HALFR>
+               : vec_ok    ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 1, 1, HALFR>
+                           : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 2, 1, HALFR>;
     } else {
-        kern = border != 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 0, CS>
-                           : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 0, CS>;
+        kern = border != 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 0, CS, HALFR>
+                           : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 0, CS, HALFR>;
     }
     const size_t smem = Cfg::smem(sizeof(T));
     cudaError_t e = set_smem(kern, smem);

@@ -209,14 +209,13 @@ __global__ void __launch_bounds__(256) residual_finish_kernel(const double *__re
     }
 }
 
-template <int T, bool EDGE>
+template <typename Cfg, bool EDGE>
 __device__ __forceinline__ void jacobi_reg_body(const float *__restrict__ u, float *__restrict__ v, int h, int w,
                                                 int n, int gy0, int gx0, int iter0, int check_every,
                                                 float4 *xch, double *wres) {
-    using Cfg = RegCfg<T>;
     constexpr int RS = Cfg::RS;
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const RegGeom<T> q(h, w, gy0, gx0);
+    const RegGeom<Cfg> q(h, w, gy0, gx0);
     const bool chunk_in = q.gc0 >= 0 && q.gc0 < w;  // w % 4 == 0: a chunk is wholly in or out
     float4 y[RS + 1];  // row r in y[1 + r] between pairs of sweeps
     y[0] = z4;
@@ -227,22 +226,23 @@ __device__ __forceinline__ void jacobi_reg_body(const float *__restrict__ u, flo
                        ? __ldg(reinterpret_cast<const float4 *>(u + (size_t)g * w + q.gc0))
                        : z4;
     }
-    reg_sweeps_store<T, EDGE>(y, v, h, w, n, q, iter0, check_every, xch, wres);
+    reg_sweeps_store<Cfg, EDGE>(y, v, h, w, n, q, iter0, check_every, xch, wres);
 }
 
-template <int T>
-__global__ void __launch_bounds__(RegCfg<T>::NT, 2)
+// MINB: CTAs per SM the register budget is sized for.
+template <typename Cfg, int MINB>
+__global__ void __launch_bounds__(Cfg::NT, MINB)
     jacobi_reg_kernel(const float *__restrict__ u, float *__restrict__ v, int h, int w, int n, int iter0,
                       int check_every, double *__restrict__ partials, int nblk) {
-    using Cfg = RegCfg<T>;
+    constexpr int T = Cfg::T;
     __shared__ float4 xch[2 * Cfg::NW * 2 * 32];
     __shared__ double wres[T * Cfg::NW];
     const int gy0 = blockIdx.y * Cfg::BH - T;       // global row of window row 0
     const int gx0 = blockIdx.x * Cfg::BW - Cfg::P;  // global column of window column 0 (multiple of 4)
     if (gy0 <= 0 || gy0 + Cfg::SH - 1 >= h - 1 || gx0 <= 0 || gx0 + Cfg::W - 1 >= w - 1)
-        jacobi_reg_body<T, true>(u, v, h, w, n, gy0, gx0, iter0, check_every, xch, wres);
+        jacobi_reg_body<Cfg, true>(u, v, h, w, n, gy0, gx0, iter0, check_every, xch, wres);
     else
-        jacobi_reg_body<T, false>(u, v, h, w, n, gy0, gx0, iter0, check_every, xch, wres);
+        jacobi_reg_body<Cfg, false>(u, v, h, w, n, gy0, gx0, iter0, check_every, xch, wres);
     __syncthreads();
     if (threadIdx.x == 0 && check_every > 0) {
         const int bid = blockIdx.y * gridDim.x + blockIdx.x;
@@ -418,7 +418,7 @@ cudaError_t run_tiled(int h, int w, float *u, float *v, int iters, int per_pass,
     float *cur = u, *nxt = v;
     for (int iter = 0; iter < iters;) {
         const int n = std::min(per_pass, iters - iter);
-        jacobi_reg_kernel<T><<<grid, Cfg::NT, 0, s>>>(cur, nxt, h, w, n, iter, ce, partials, nblk);
+        jacobi_reg_kernel<Cfg, 2><<<grid, Cfg::NT, 0, s>>>(cur, nxt, h, w, n, iter, ce, partials, nblk);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         int slot = 0;

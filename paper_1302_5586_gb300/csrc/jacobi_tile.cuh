@@ -43,10 +43,13 @@ __device__ __forceinline__ float nsum(float up, float dn, float lf, float rt) {
 // expression as the one-sweep kernel, so the iterate is the same bits for
 // every T.  Residuals of iterates inside the pass are accumulated, over core
 // points, during the sweep that updates them.
-template <int T>
+// NW warps of RS rows each; the library runs NW = 8, RS = 16 (two 256-thread
+// CTAs per SM).
+template <int T_, int NW_ = 8, int RS_ = 16>
 struct RegCfg {
-    static constexpr int NW = 8;              // warps
-    static constexpr int RS = 16;             // rows per warp
+    static constexpr int T = T_;              // sweeps per pass (the halo width)
+    static constexpr int NW = NW_;            // warps
+    static constexpr int RS = RS_;            // rows per warp
     static constexpr int NT = 32 * NW;
     static constexpr int W = 128;             // window columns: 32 lanes x 4
     static constexpr int SH = NW * RS;        // window rows
@@ -135,13 +138,13 @@ __device__ __forceinline__ void reg_step(float4 (&y)[RS + 1], int t, int iter0, 
 // Where a thread of a window with origin (gy0, gx0) sits: its first column
 // gc0, its first row g_first, whether its columns are core columns and which
 // of its four columns are interior, and the core's rows [core_lo, core_hi).
-template <int T>
+template <typename Cfg>
 struct RegGeom {
     int gc0, g_first, core_lo, core_hi;
     bool core_cols;
     bool cint[4];
     __device__ __forceinline__ RegGeom(int h, int w, int gy0, int gx0) {
-        using Cfg = RegCfg<T>;
+        constexpr int T = Cfg::T;
         const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
         gc0 = gx0 + 4 * lane;
         core_cols = 4 * lane >= Cfg::P && 4 * lane < Cfg::P + Cfg::BW && gc0 < w;
@@ -157,11 +160,10 @@ struct RegGeom {
 // scratch) and the core written to v: sweeps in pairs (down, then up, which
 // brings the band back to its slots), an odd count ending with one more down
 // sweep.  Residuals of checkpoint iterates go to wres as reg_step records them.
-template <int T, bool EDGE>
-__device__ __forceinline__ void reg_sweeps_store(float4 (&y)[RegCfg<T>::RS + 1], float *__restrict__ v, int h, int w,
-                                                 int n, const RegGeom<T> &q, int iter0, int check_every,
+template <typename Cfg, bool EDGE>
+__device__ __forceinline__ void reg_sweeps_store(float4 (&y)[Cfg::RS + 1], float *__restrict__ v, int h, int w,
+                                                 int n, const RegGeom<Cfg> &q, int iter0, int check_every,
                                                  float4 *xch, double *wres) {
-    using Cfg = RegCfg<T>;
     constexpr int RS = Cfg::RS, NW = Cfg::NW;
     const int gc0 = q.gc0, g_first = q.g_first, core_lo = q.core_lo, core_hi = q.core_hi;
     const bool core_cols = q.core_cols;
