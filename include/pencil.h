@@ -216,15 +216,20 @@ typedef struct pencil_image {
  * max_images images and max_tiles tiles, and the captured graph. */
 typedef struct pencil_batch pencil_batch;
 
-/* Tile shapes the batched kernel offers: 0 = 32 x 128, 1 = 16 x 128 outputs. */
-#define PENCIL_BATCH_VARIANTS 2
+/* Tile variants of the batched kernels, each its own kernel per filter side:
+ * 0 = 32 x 128 outputs, 128 threads   2 = 64 x 128 outputs, 256 threads
+ * 1 = 16 x 128 outputs, 128 threads   3 = 32 x 128 outputs, 256 threads
+ * (so tile height, rows per thread and CTA size differ between them). */
+#define PENCIL_BATCH_VARIANTS 4
 
 /* Create a plan for dtype PENCIL_F32 or PENCIL_F16 (allocates; captures the
  * graph).  All sides start with variant 0.  Errors: NULL, ARG, NOMEM, CUDA. */
 int pencil_batch_create(int dtype, int max_images, long long max_tiles, pencil_batch **out);
 
-/* Tile shape used for images whose filter side is ks (odd 1..15).
- * Errors: NULL, ARG. */
+/* Tile variant used for images whose filter side is ks (odd 1..15).  It swaps
+ * the side's kernel and drops the plan's captured graphs (the next run
+ * captures again), so call it while no batch of the plan is in flight.
+ * Errors: NULL, ARG, CUDA. */
 int pencil_batch_set_variant(pencil_batch *b, int ks, int variant);
 
 /* Number of tiles n images need with the plan's current variants (host only).

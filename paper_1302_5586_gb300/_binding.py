@@ -44,7 +44,7 @@ class PencilImage(ctypes.Structure):
                 ("h", ctypes.c_int), ("w", ctypes.c_int), ("ks", ctypes.c_int)]
 
 
-PENCIL_BATCH_VARIANTS = 2
+PENCIL_BATCH_VARIANTS = 4
 
 
 class PencilError(RuntimeError):

@@ -195,7 +195,8 @@ const char *pencil_strerror(int status) {
     }
 }
 
-int pencil_version(void) { return 100; }
+// 0.2.0: interleaved layouts, the conv -> Jacobi chain, four batch tile variants.
+int pencil_version(void) { return 200; }
 
 int pencil_device_info(char *name, int len, int *sm_count, int *driver_version) {
     int dev = 0;

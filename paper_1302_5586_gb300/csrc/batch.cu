@@ -46,19 +46,23 @@ struct BatchImage {
     int vec_ok, pad;
 };
 
-constexpr int BT = 128;     // threads per CTA of the batched kernels
 constexpr int kSides = 8;   // filter sides 1, 3, ..., 15; side index = ks / 2
 
-// Tile shapes (all 128 threads): variant 0 = 32 x 128, variant 1 = 16 x 128.
-// Sides up to 7 use one 4-column group per thread; larger sides two groups.
-__host__ __device__ constexpr int var_th(int v) { return v == 0 ? 32 : 16; }
+// Tile variants, all 128 columns wide; each is its own kernel per side, so
+// the tuner chooses tile height, rows per thread and CTA size per side:
+//   0: 32-row tiles, 128 threads     2: 64-row tiles, 256 threads
+//   1: 16-row tiles, 128 threads     3: 32-row tiles, 256 threads
+// Sides up to 7 give a thread one 4-column group (32 threads across a row),
+// larger sides two groups (16 threads across); the rows per thread follow.
+__host__ __device__ constexpr int var_th(int v) { return v == 1 ? 16 : (v == 2 ? 64 : 32); }
+__host__ __device__ constexpr int var_nt(int v) { return v >= 2 ? 256 : 128; }
 constexpr int kTileW = 128;
 __host__ __device__ constexpr int btx(int k) { return k <= 7 ? 32 : 16; }
-__host__ __device__ constexpr int bty(int k) { return k <= 7 ? 4 : 8; }
 __host__ __device__ constexpr int bg(int k) { return k <= 7 ? 1 : 2; }
-__host__ __device__ constexpr int brows(int k, int v) { return k <= 7 ? (v == 0 ? 8 : 4) : (v == 0 ? 4 : 2); }
+__host__ __device__ constexpr int bty(int k, int v) { return var_nt(v) / btx(k); }
+__host__ __device__ constexpr int brows(int k, int v) { return var_th(v) / bty(k, v); }
 template <int K, int V>
-using BCfg = DirectCfg<K, K, btx(K), bty(K), brows(K, V), bg(K)>;
+using BCfg = DirectCfg<K, K, btx(K), bty(K, V), brows(K, V), bg(K)>;
 
 // Binary16 sides up to 7 compute from the staged binary16 tile (no FP32 copy;
 // the standalone kernels do the same).
@@ -68,24 +72,23 @@ __host__ __device__ constexpr bool bhalfw(int k, size_t esz) { return esz == 2 &
 // (less code around their FMA loop), as the standalone kernels do.
 __host__ __device__ constexpr bool badapt(int k) { return k <= 5; }
 
-// A staging slot of side K: filter rows | FP32 tile (variant 0, the larger) |
-// binary16 tile; without the FP32 tile where the binary16 tile is read directly.
-template <int K>
+// A staging slot of side K, variant V: filter rows | FP32 tile | binary16
+// tile; without the FP32 tile where the binary16 tile is read directly.
+template <int K, int V>
 struct Slot {
-    static constexpr int KF = K * BCfg<K, 0>::KWP;  // a multiple of 4 floats
-    static constexpr int IN = BCfg<K, 0>::SH * BCfg<K, 0>::SW;
-    static_assert(BCfg<K, 1>::SH * BCfg<K, 1>::SW <= IN, "variant 1 tile larger than the slot");
+    static constexpr int KF = K * BCfg<K, V>::KWP;  // a multiple of 4 floats
+    static constexpr int IN = BCfg<K, V>::SH * BCfg<K, V>::SW;
     __host__ __device__ static constexpr int f16_off(int esz) { return KF + (bhalfw(K, esz) ? 0 : IN); }
     __host__ __device__ static constexpr int floats(int esz) {
         return bhalfw(K, esz) ? KF + IN / 2 : KF + IN + (esz == 2 ? IN / 2 : 0);
     }
 };
-// Staging slots and CTAs per SM (the register budget) per side, from sweeps
-// on GB300 over the 512-image benchmark batch.  Two slots let a CTA's next
-// tile copy while it computes the current one; where one slot wins, more
-// resident CTAs hide the copies better than the prefetch does.
-// (A timing sweep may build other tables by defining the macros in a header
-// it force-includes; the library uses these.)
+// Staging slots and CTAs per SM (the register budget, for 128-thread CTAs;
+// halved for 256-thread ones) per side, from sweeps on GB300 over the
+// 512-image benchmark batch.  Two slots let a CTA's next tile copy while it
+// computes the current one; where one slot wins, more resident CTAs hide the
+// copies better than the prefetch does.  (A timing sweep may build other
+// tables by defining the macros in a header it force-includes.)
 #ifndef PENCIL_BATCH_NSLOT
 #define PENCIL_BATCH_NSLOT {{2, 1, 1, 1, 1, 1, 2, 1}, {2, 2, 1, 1, 1, 1, 1, 1}}  // FP32, binary16; sides 1..15
 #endif
@@ -96,74 +99,63 @@ constexpr int kNslot[2][kSides] = PENCIL_BATCH_NSLOT;
 constexpr int kRegCap[2][kSides] = PENCIL_BATCH_REGCAP;
 template <int K>
 constexpr int nslot(size_t esz) { return kNslot[esz == 2][K / 2]; }
-template <int K>
+template <int K, int V>
 constexpr size_t batch_smem(size_t esz) {
-    return nslot<K>(esz) * sizeof(float) * (size_t)Slot<K>::floats((int)esz);
+    return nslot<K>(esz) * sizeof(float) * (size_t)Slot<K, V>::floats((int)esz);
 }
-// CTAs per SM the register budget is sized for: the table's, or fewer where
-// the shared memory holds fewer.
-template <int K>
+// CTAs per SM the register budget is sized for: the table's (in 128-thread
+// CTAs), or fewer where the shared memory holds fewer.
+template <int K, int V>
 constexpr int batch_minb(size_t esz) {
-    return std::min<int>(kRegCap[esz == 2][K / 2],
-                         std::max<int>(1, (int)((228 * 1024) / (batch_smem<K>(esz) + 1024))));
+    return std::max<int>(1, std::min<int>(kRegCap[esz == 2][K / 2] * 128 / var_nt(V),
+                                          (int)((228 * 1024) / (batch_smem<K, V>(esz) + 1024))));
 }
 
 // Issue the copies of one tile (filter and halo tile) into a slot; one commit group.
 template <typename T, int K, int V>
 __device__ __forceinline__ void issue_tile(const BatchImage &d, int y0, int x0, float *slot) {
     using Cfg = BCfg<K, V>;
-    stage_filter_async<K, K, Cfg::KWP, BT>(d.k, slot);
-    stage_issue<T, Cfg::SH, Cfg::SW, BT, false, badapt(K)>(static_cast<const T *>(d.in), d.h, d.w, y0 - Cfg::AH,
-                                                            x0 - Cfg::P,
-                                         d.vec_ok, slot + Slot<K>::KF,
-                                         reinterpret_cast<T *>(slot + Slot<K>::f16_off(sizeof(T))));
+    stage_filter_async<K, K, Cfg::KWP, Cfg::NT>(d.k, slot);
+    stage_issue<T, Cfg::SH, Cfg::SW, Cfg::NT, false, badapt(K)>(static_cast<const T *>(d.in), d.h, d.w,
+                                                                y0 - Cfg::AH, x0 - Cfg::P, d.vec_ok,
+                                                                slot + Slot<K, V>::KF,
+                                                                reinterpret_cast<T *>(slot + Slot<K, V>::f16_off(sizeof(T))));
 }
 
 // Widen (binary16, unless read directly) and compute one staged tile.
 template <typename T, int K, int V>
 __device__ __forceinline__ void compute_tile(const BatchImage &d, int y0, int x0, float *slot) {
     using Cfg = BCfg<K, V>;
-    const T *s16 = reinterpret_cast<const T *>(slot + Slot<K>::f16_off(sizeof(T)));
+    const T *s16 = reinterpret_cast<const T *>(slot + Slot<K, V>::f16_off(sizeof(T)));
     if constexpr (bhalfw(K, sizeof(T))) {
-        direct_compute<T, K, K, btx(K), bty(K), brows(K, V), bg(K), T, badapt(K)>(s16, slot, static_cast<T *>(d.out),
-                                                                                  d.h, d.w, d.vec_ok, y0, x0);
+        direct_compute<T, K, K, btx(K), bty(K, V), brows(K, V), bg(K), T, badapt(K)>(s16, slot, static_cast<T *>(d.out),
+                                                                                     d.h, d.w, d.vec_ok, y0, x0);
     } else {
-        stage_widen<T, Cfg::SH, Cfg::SW, BT>(slot + Slot<K>::KF, s16);
-        direct_compute<T, K, K, btx(K), bty(K), brows(K, V), bg(K), float, badapt(K)>(slot + Slot<K>::KF, slot,
-                                                                   static_cast<T *>(d.out), d.h, d.w, d.vec_ok,
-                                                                   y0, x0);
+        stage_widen<T, Cfg::SH, Cfg::SW, Cfg::NT>(slot + Slot<K, V>::KF, s16);
+        direct_compute<T, K, K, btx(K), bty(K, V), brows(K, V), bg(K), float, badapt(K)>(
+            slot + Slot<K, V>::KF, slot, static_cast<T *>(d.out), d.h, d.w, d.vec_ok, y0, x0);
     }
 }
 
-template <typename T, int K, bool ISSUE>
-__device__ __forceinline__ void tile_op(const BatchImage &d, int y0, int x0, float *slot) {
-    if (d.var == 0) {
-        if (ISSUE) issue_tile<T, K, 0>(d, y0, x0, slot);
-        else compute_tile<T, K, 0>(d, y0, x0, slot);
-    } else {
-        if (ISSUE) issue_tile<T, K, 1>(d, y0, x0, slot);
-        else compute_tile<T, K, 1>(d, y0, x0, slot);
-    }
-}
-
+template <int V>
 __device__ __forceinline__ void tile_origin(const BatchImage &d, int t, int &y0, int &x0) {
     const int local = t - d.tile_base;
     const int ty = local / d.tiles_x, tx = local - ty * d.tiles_x;
-    y0 = ty * var_th(d.var);
+    y0 = ty * var_th(V);
     x0 = tx * kTileW;
 }
 
-// The tiles of one filter side.  NSLOT = 2: while tile i is computed from
-// one staging slot, the copies of tile i+1 are already in flight into the
-// other.  NSLOT = 1 (binary16, whose slots are larger): the next tile's
-// copies are issued after the compute.
-template <typename T, int K, int NSLOT, int MINB>
-__global__ void __launch_bounds__(BT, MINB)
+// The tiles of one filter side under one tile variant.  NSLOT = 2: while
+// tile i is computed from one staging slot, the copies of tile i+1 are
+// already in flight into the other.  NSLOT = 1: the next tile's copies are
+// issued after the compute.
+template <typename T, int K, int V, int NSLOT, int MINB>
+__global__ void __launch_bounds__(var_nt(V), MINB)
     conv2d_batch_kernel(BatchHeader *__restrict__ hdr, const BatchImage *__restrict__ imgs,
                         const int *__restrict__ tile_img) {
     extern __shared__ __align__(16) float smem[];
     __shared__ int s_next;
-    constexpr int SLOT = Slot<K>::floats(sizeof(T));
+    constexpr int SLOT = Slot<K, V>::floats(sizeof(T));
     const int total = hdr->total, start = hdr->start;
     if (threadIdx.x == 0) s_next = atomicAdd(&hdr->next, 1);
     __syncthreads();
@@ -173,8 +165,8 @@ __global__ void __launch_bounds__(BT, MINB)
     if (threadIdx.x == 0) s_next = atomicAdd(&hdr->next, 1);
     BatchImage d = imgs[__ldg(tile_img + start + t)];
     int y0, x0;
-    tile_origin(d, start + t, y0, x0);
-    tile_op<T, K, true>(d, y0, x0, smem);
+    tile_origin<V>(d, start + t, y0, x0);
+    issue_tile<T, K, V>(d, y0, x0, smem);
     __syncthreads();
     int tn = s_next;
     for (int i = 0; t < total; ++i) {
@@ -184,19 +176,19 @@ __global__ void __launch_bounds__(BT, MINB)
         int yn = 0, xn = 0;
         if (tn < total) {
             dn = imgs[__ldg(tile_img + start + tn)];
-            tile_origin(dn, start + tn, yn, xn);
+            tile_origin<V>(dn, start + tn, yn, xn);
         }
         if (NSLOT == 2 && tn < total) {
-            tile_op<T, K, true>(dn, yn, xn, nxt);
+            issue_tile<T, K, V>(dn, yn, xn, nxt);
             cp_async_wait_prev();  // the current tile's group has landed
         } else {
             cp_async_wait_all();
         }
         __syncthreads();  // every thread has read s_next (end of the previous iteration)
         if (threadIdx.x == 0) s_next = atomicAdd(&hdr->next, 1);
-        tile_op<T, K, false>(d, y0, x0, cur);
+        compute_tile<T, K, V>(d, y0, x0, cur);
         __syncthreads();  // `cur` is free; s_next is visible
-        if (NSLOT == 1 && tn < total) tile_op<T, K, true>(dn, yn, xn, nxt);
+        if (NSLOT == 1 && tn < total) issue_tile<T, K, V>(dn, yn, xn, nxt);
         t = tn;
         d = dn;
         y0 = yn;
@@ -210,25 +202,36 @@ using BatchKernel = void (*)(BatchHeader *, const BatchImage *, const int *);
 struct SideKernel {
     BatchKernel fn;
     size_t smem;
+    int nt;  // threads per CTA
 };
 
-template <typename T, int K>
+template <typename T, int K, int V>
 SideKernel side_kernel() {
     constexpr size_t esz = sizeof(T);
-    return {conv2d_batch_kernel<T, K, nslot<K>(esz), batch_minb<K>(esz)>, batch_smem<K>(esz)};
+    return {conv2d_batch_kernel<T, K, V, nslot<K>(esz), batch_minb<K, V>(esz)>, batch_smem<K, V>(esz), var_nt(V)};
+}
+
+template <typename T, int K>
+SideKernel side_kernel_v(int v) {
+    switch (v) {
+        case 0: return side_kernel<T, K, 0>();
+        case 1: return side_kernel<T, K, 1>();
+        case 2: return side_kernel<T, K, 2>();
+        default: return side_kernel<T, K, 3>();
+    }
 }
 
 template <typename T>
-SideKernel side_kernel(int idx) {
+SideKernel side_kernel(int idx, int v) {
     switch (idx) {
-        case 0: return side_kernel<T, 1>();
-        case 1: return side_kernel<T, 3>();
-        case 2: return side_kernel<T, 5>();
-        case 3: return side_kernel<T, 7>();
-        case 4: return side_kernel<T, 9>();
-        case 5: return side_kernel<T, 11>();
-        case 6: return side_kernel<T, 13>();
-        default: return side_kernel<T, 15>();
+        case 0: return side_kernel_v<T, 1>(v);
+        case 1: return side_kernel_v<T, 3>(v);
+        case 2: return side_kernel_v<T, 5>(v);
+        case 3: return side_kernel_v<T, 7>(v);
+        case 4: return side_kernel_v<T, 9>(v);
+        case 5: return side_kernel_v<T, 11>(v);
+        case 6: return side_kernel_v<T, 13>(v);
+        default: return side_kernel_v<T, 15>(v);
     }
 }
 
@@ -249,8 +252,10 @@ struct pencil_batch {
     void *hbuf[2] = {nullptr, nullptr};  // pinned host staging (ping-pong)
     cudaEvent_t uploaded[2] = {nullptr, nullptr};
     int flip = 0;
+    int sms = 0;                 // SMs of the plan's device
     int grid[kSides] = {};       // resident grid of each side's kernel
     size_t smem[kSides] = {};    // its dynamic shared memory
+    int nt[kSides] = {};         // its threads per CTA
     BatchKernel fn[kSides] = {};
     std::map<unsigned, cudaGraphExec_t> exec;  // graph per set of sides present
     std::mutex mu;
@@ -324,7 +329,7 @@ cudaError_t graph_for(pencil_batch *b, unsigned mask, cudaGraphExec_t *out) {
         cudaError_t le = cudaSuccess;
         for (int i = kSides - 1; i >= 0 && le == cudaSuccess; --i)
             if (mask & (1u << i)) {
-                b->fn[i]<<<b->grid[i], BT, b->smem[i], cs>>>(hdr + i, imgs, tile_img);
+                b->fn[i]<<<b->grid[i], b->nt[i], b->smem[i], cs>>>(hdr + i, imgs, tile_img);
                 le = cudaGetLastError();
             }
         e = cudaStreamEndCapture(cs, &g);
@@ -340,9 +345,28 @@ cudaError_t graph_for(pencil_batch *b, unsigned mask, cudaGraphExec_t *out) {
     return e;
 }
 
-void release(pencil_batch *b) {
+void drop_graphs(pencil_batch *b) {
     for (auto &kv : b->exec) cudaGraphExecDestroy(kv.second);
     b->exec.clear();
+}
+
+// Side i runs tile variant v: its kernel, shared memory, CTA size and a
+// resident grid of every CTA the SMs hold at once.
+cudaError_t load_side(pencil_batch *b, int i, int v) {
+    const SideKernel sk = b->dtype == PENCIL_F32 ? side_kernel<float>(i, v) : side_kernel<__half>(i, v);
+    cudaError_t e = cudaFuncSetAttribute(sk.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sk.smem);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sk.fn, sk.nt, sk.smem);
+    if (e != cudaSuccess) return e;
+    b->fn[i] = sk.fn;
+    b->smem[i] = sk.smem;
+    b->nt[i] = sk.nt;
+    b->grid[i] = std::max(1, per_sm) * b->sms;
+    return cudaSuccess;
+}
+
+void release(pencil_batch *b) {
+    drop_graphs(b);
     for (int i = 0; i < 2; ++i) {
         if (b->uploaded[i]) cudaEventDestroy(b->uploaded[i]);
         if (b->hbuf[i]) cudaFreeHost(b->hbuf[i]);
@@ -371,18 +395,10 @@ int pencil_batch_create(int dtype, int max_images, long long max_tiles, pencil_b
         e = cudaMallocHost(&b->hbuf[i], b->bytes);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded[i], cudaEventDisableTiming);
     }
-    int dev = 0, sms = 0;
+    int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    for (int i = 0; i < kSides && e == cudaSuccess; ++i) {
-        const SideKernel sk = dtype == PENCIL_F32 ? side_kernel<float>(i) : side_kernel<__half>(i);
-        b->fn[i] = sk.fn;
-        b->smem[i] = sk.smem;
-        e = cudaFuncSetAttribute(sk.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sk.smem);
-        int per_sm = 0;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sk.fn, BT, sk.smem);
-        b->grid[i] = std::max(1, per_sm) * sms;
-    }
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int i = 0; i < kSides && e == cudaSuccess; ++i) e = load_side(b, i, 0);
     if (e != cudaSuccess) {
         release(b);
         delete b;
@@ -397,7 +413,11 @@ int pencil_batch_set_variant(pencil_batch *b, int ks, int variant) {
     if (ks < 1 || ks > 15 || !(ks & 1) || variant < 0 || variant >= PENCIL_BATCH_VARIANTS)
         return PENCIL_ERR_ARG;
     std::lock_guard<std::mutex> lk(b->mu);
+    if (b->var_of_k[ks] == variant) return PENCIL_OK;
+    const cudaError_t e = load_side(b, ks / 2, variant);
+    if (e != cudaSuccess) return cuda_fail(e);
     b->var_of_k[ks] = (unsigned char)variant;
+    drop_graphs(b);  // the captured graphs launch the side's previous kernel
     return PENCIL_OK;
 }
 

@@ -251,9 +251,12 @@ class Server:
             self.arena = None
 
     def set_variants(self, variants: dict):
+        """Tile variant per filter side (a change drops the plans' captured
+        graphs, so the warm-up runs again before any request is served)."""
         for p in self.plans:
             for ks, v in variants.items():
                 b.pencil_batch_set_variant(p, int(ks), int(v))
+        self.warm_up()
 
     def _view(self, off: int, n: int):
         return self.pool[off:off + n * self.esz].view(self.tdtype)

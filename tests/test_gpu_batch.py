@@ -1,6 +1,7 @@
-"""The batched persistent conv2d kernel: bit-identical to the standalone
-kernel on every image, within tolerance of the FP64 oracle, for both tile
-variants, across batches replayed from the same captured graph."""
+"""The batched persistent conv2d kernels: bit-identical to the standalone
+kernel on every image, within tolerance of the FP64 oracle, for every tile
+variant (and a mix of variants across sides), across batches replayed from
+the same captured graph and after a variant change drops the graphs."""
 import numpy as np
 import pytest
 
@@ -38,13 +39,18 @@ def standalone(it, dtype):
 
 
 @pytest.mark.parametrize("dtype", [pg.PENCIL_F32, pg.PENCIL_F16])
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", list(range(pg.PENCIL_BATCH_VARIANTS)) + ["mixed"])
 def test_batch_matches_standalone_bitwise_and_oracle(dtype, variant):
-    items, host = make_batch(3 + variant, 48, 1, 300, dtype)
+    items, host = make_batch(3 + (variant if variant != "mixed" else 7), 48, 1, 300, dtype)
     plan = pg.pencil_batch_create(dtype, 64, 1 << 16)
     try:
+        pg.pencil_batch_run(plan, pg.make_images(items))  # captures graphs with variant 0 first
+        torch.cuda.synchronize()
         for ks in range(1, 16, 2):
-            pg.pencil_batch_set_variant(plan, ks, variant)
+            v = variant if variant != "mixed" else (ks // 2) % pg.PENCIL_BATCH_VARIANTS
+            pg.pencil_batch_set_variant(plan, ks, v)
+        for it in items:
+            it[1].fill_(float("nan"))
         pg.pencil_batch_run(plan, pg.make_images(items))
         torch.cuda.synchronize()
         tol = 1e-6 if dtype == pg.PENCIL_F32 else 2.0 ** -10
