@@ -220,12 +220,13 @@ int pencil_last_cuda_error(void) { return g_last_cuda; }
 
 int pencil_device_status(void) {
     unsigned n = 0, m = 0;
-    unsigned q = 0;
+    unsigned q = 0, r = 0;
     cudaError_t e = wait_timeouts(&n, true);
     if (e == cudaSuccess) e = wait_timeouts_hwc(&m, true);
     if (e == cudaSuccess) e = wait_timeouts_cj(&q, true);
+    if (e == cudaSuccess) e = wait_timeouts_chain(&r, true);
     if (e != cudaSuccess) return cuda_fail(e);
-    return n + m + q ? PENCIL_ERR_TIMEOUT : PENCIL_OK;
+    return n + m + q + r ? PENCIL_ERR_TIMEOUT : PENCIL_OK;
 }
 
 int pencil_selftest_wait_timeout(unsigned limit_us, int *completed) {

@@ -12,8 +12,10 @@
 //
 // Specialised kernel (square odd k1, k2 in {3, 5, 7}), one CTA per
 // 32 x 128 output tile, 256 threads:
-//   1. stage the input rows and columns the tile's intermediate region needs
-//      (clamped, cp.async, as the direct kernel does);
+//   1. stage the input rows and columns the tile's intermediate region needs:
+//      FP32 images with 16-byte aligned rows as one TMA box (the clamp
+//      rebuilt in shared memory on edge tiles, as the direct TMA kernel does),
+//      others clamped with cp.async;
 //   2. compute the intermediate region (32 + k2 - 1 rows, 128 + k2 - 1
 //      columns) into shared memory: up to 7 warps each own a band of R1 rows,
 //      one lane per 4 columns, and the last warp takes the columns beyond 128;
@@ -23,7 +25,7 @@
 //      register blocking (4 rows x 4 columns per thread), stored to HBM.
 // Any other pair of sizes takes a generic fused kernel (runtime sizes; the
 // intermediate computed at clamped positions from global memory).
-#include "conv_tile.cuh"
+#include "conv_kernels.cuh"
 
 #ifndef PENCIL_CHAIN_MINB
 #define PENCIL_CHAIN_MINB 4  // CTAs per SM the register budget is sized for
@@ -70,6 +72,7 @@ struct ChainCfg {
     static_assert(HI <= SWY, "intermediate block beyond its row");
     static_assert(OFF_Y % 4 == 0 && OFF_K1 % 4 == 0 && OFF_K2 % 4 == 0 && OFF_16 % 4 == 0 && (XH * SWX) % 8 == 0,
                   "alignment");
+    static_assert(XH <= 256 && SWX <= 256, "a TMA box side is at most 256 elements");
 };
 
 template <typename T>
@@ -80,13 +83,16 @@ __device__ __forceinline__ float storage_round(float v) {
         return v;
 }
 
-template <typename T, int K1, int K2, int MINB>
+// TMA: the input region arrives as one box of `tmap` (FP32 images whose rows
+// are 16-byte aligned); otherwise it is staged with cp.async from `in`.
+template <typename T, int K1, int K2, int MINB, bool TMA>
 __global__ void __launch_bounds__(256, MINB)
-    conv2d_chain_kernel(const T *__restrict__ in, const float *__restrict__ k1,
-                        const float *__restrict__ k2, T *__restrict__ out, int h, int w, bool vec_ok) {
+    conv2d_chain_kernel(const __grid_constant__ CUtensorMap tmap, const T *__restrict__ in,
+                        const float *__restrict__ k1, const float *__restrict__ k2, T *__restrict__ out, int h,
+                        int w, bool vec_ok) {
     using Cfg = ChainCfg<K1, K2>;
     constexpr int NT = Cfg::NT, SWX = Cfg::SWX, SWY = Cfg::SWY, YH = Cfg::YH, R1 = Cfg::R1;
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
     float *s_x = smem;
     float *s_y = smem + Cfg::OFF_Y;
     float *s_k1 = smem + Cfg::OFF_K1;
@@ -98,11 +104,34 @@ __global__ void __launch_bounds__(256, MINB)
     const int yr0 = y0 - Cfg::A2, yc0 = x0 - Cfg::P2;  // global position of s_y[0][0]
 
     // 1. filters and the input region (clamped)
-    stage_filter_async<K1, K1, Cfg::KWP1, NT>(k1, s_k1);
-    stage_filter_async<K2, K2, Cfg::KWP2, NT>(k2, s_k2);
-    stage_issue<T, Cfg::XH, SWX, NT, false, false>(in + plane, h, w, yr0 - Cfg::A1, yc0 - Cfg::P1, vec_ok, s_x,
-                                                 s16);
-    stage_finish<T, Cfg::XH, SWX, NT>(s_x, s16);
+    if constexpr (TMA) {
+        static_assert(sizeof(T) == 4, "the TMA path stages FP32 images");
+        __shared__ __align__(8) uint64_t bar;
+        if ((tma::smem_addr(s_x) & 127u) != 0) {  // a TMA box needs a 128-byte aligned destination
+            if (threadIdx.x == 0) atomicAdd(&g_wait_timeouts, 1u);
+            return;
+        }
+        if (threadIdx.x == 0) tma::mbar_init(&bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tma::mbar_arrive_expect_tx(&bar, (unsigned)(sizeof(float) * Cfg::XH * SWX));
+            tma::load_3d(s_x, &tmap, yc0 - Cfg::P1, yr0 - Cfg::A1, (int)blockIdx.z, &bar);
+        }
+        stage_filter<K1, K1, Cfg::KWP1, NT>(k1, s_k1);
+        stage_filter<K2, K2, Cfg::KWP2, NT>(k2, s_k2);
+        if (!__syncthreads_and(tma::mbar_wait(&bar, 0, tma::kLoadWaitNs))) {
+            if (threadIdx.x == 0) atomicAdd(&g_wait_timeouts, 1u);  // skip the tile; let the copy land
+            tma::mbar_wait(&bar, 0, tma::kLoadWaitNs);
+            return;
+        }
+        clamp_fixup<float, Cfg::XH, SWX, NT>(s_x, h, w, yr0 - Cfg::A1, yc0 - Cfg::P1);
+    } else {
+        stage_filter_async<K1, K1, Cfg::KWP1, NT>(k1, s_k1);
+        stage_filter_async<K2, K2, Cfg::KWP2, NT>(k2, s_k2);
+        stage_issue<T, Cfg::XH, SWX, NT, false, false>(in + plane, h, w, yr0 - Cfg::A1, yc0 - Cfg::P1, vec_ok, s_x,
+                                                     s16);
+        stage_finish<T, Cfg::XH, SWX, NT>(s_x, s16);
+    }
 
     // 2. the intermediate region
     {
@@ -205,24 +234,23 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-template <typename Kern>
-cudaError_t set_smem(Kern kern, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
 template <typename T, int K1, int K2>
 cudaError_t run_chain(int c, int h, int w, const T *in, const float *k1, const float *k2, T *out,
                       bool vec_ok, cudaStream_t s) {
     using Cfg = ChainCfg<K1, K2>;
     // a 7-tap first filter needs more than 64 registers a thread
     constexpr int MINB = K1 >= 7 ? PENCIL_CHAIN_MINB - 1 : PENCIL_CHAIN_MINB;
-    auto kern = conv2d_chain_kernel<T, K1, K2, MINB>;
+    CUtensorMap tmap = {};
+    auto kern = conv2d_chain_kernel<T, K1, K2, MINB, false>;
+    if constexpr (sizeof(T) == 4) {
+        if (vec_ok && image_tensor_map<T>(&tmap, in, c, h, w, Cfg::SWX, Cfg::XH))
+            kern = conv2d_chain_kernel<T, K1, K2, MINB, true>;
+    }
     const size_t smem = Cfg::smem(sizeof(T));
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((w + Cfg::TW - 1) / Cfg::TW, (h + Cfg::TH - 1) / Cfg::TH, c);
-    kern<<<grid, Cfg::NT, smem, s>>>(in, k1, k2, out, h, w, vec_ok);
+    kern<<<grid, Cfg::NT, smem, s>>>(tmap, in, k1, k2, out, h, w, vec_ok);
     return cudaGetLastError();
 }
 
@@ -263,6 +291,8 @@ bool rows_aligned(const void *p, int w, int vec) { return (w % vec == 0) && ((ui
 size_t chain_generic_smem(int kh2, int kw2) {
     return sizeof(float) * (size_t)(GTH + kh2 - 1) * (size_t)(GTW + kw2 - 1);
 }
+
+cudaError_t wait_timeouts_chain(unsigned *n, bool clear) { return read_wait_counter(n, clear); }
 
 cudaError_t launch_conv2d_chain(int dtype, int c, int h, int w, const void *in, int kh1, int kw1,
                                 const float *k1, int kh2, int kw2, const float *k2, void *out,

@@ -90,6 +90,7 @@ PENCIL_HWC_DECL(hwc4_f16)
 // of the interleaved units'.
 cudaError_t wait_timeouts(unsigned *n, bool clear);
 cudaError_t wait_timeouts_hwc(unsigned *n, bool clear);
+cudaError_t wait_timeouts_chain(unsigned *n, bool clear);
 // Run the bounded mbarrier wait against a barrier that never completes, for
 // limit_ns; *completed = 1 if it completed (it should not), 0 if it ran out.
 cudaError_t wait_selftest(uint64_t limit_ns, int *completed);
