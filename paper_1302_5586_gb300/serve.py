@@ -8,8 +8,11 @@ a Poisson trace.  The scheduler loop:
   kept by the native pencil_arena) has room for the request's input and
   output; a request that does not fit waits until completions free memory,
   and one that could not fit even an empty arena is rejected on arrival;
-* packs every request admitted in one pass into a wave and issues it on the
-  next of `streams` CUDA streams: host-to-device copies of the inputs (from
+* packs requests admitted in one pass into a wave and issues it on one of
+  `streams` CUDA streams -- an idle stream if there is one, the pending
+  requests spread evenly over the idle streams (so at low load a request
+  runs alone, with the latency of a plain launch), else the next stream in
+  turn with up to `max_wave` requests (batching grows with the queue): host-to-device copies of the inputs (from
   pinned host memory into the arena), ONE batched persistent conv2d launch
   (pencil_batch_run, graph replay; one plan per stream) -- or, for a wave of
   a single request, its one standalone launch, which costs the host less
@@ -173,6 +176,17 @@ class Admission:
         self.inflight -= len(items)
 
 
+def wave_limit(mode: str, pending: int, idle_streams: int, max_wave: int) -> int:
+    """Requests the next wave may take.  Plain mode: one.  Served: with idle
+    streams, the pending requests spread evenly over them (a lone request
+    goes alone); with every stream busy, up to max_wave."""
+    if mode != "served":
+        return 1
+    if idle_streams > 0:
+        return max(1, min(max_wave, -(-pending // idle_streams)))
+    return max_wave
+
+
 @dataclasses.dataclass
 class Stats:
     mode: str
@@ -321,13 +335,20 @@ class Server:
                     progressed = True
             # admission: arrival order, while a slot and arena memory are free
             dropped = adm.dropped
-            wave = adm.wave(self.max_wave if mode == "served" else 1, time.perf_counter() - t0)
+            # batch only under load: with idle streams the queue is spread over them
+            # (a lone request runs alone, as fast as a plain launch); when every
+            # stream is busy the whole queue, up to max_wave, forms the next wave
+            idle = [i for i, fq in enumerate(inflight) if not fq]
+            limit = wave_limit(mode, len(adm.pending), len(idle), self.max_wave)
+            wave = adm.wave(limit, time.perf_counter() - t0)
             progressed = progressed or adm.dropped != dropped
             if wave:
-                s = self.streams[rr % len(self.streams)]
-                plan = self.plans[rr % len(self.plans)]
-                q = inflight[rr % len(self.streams)]
-                rr += 1
+                si = idle[0] if idle else rr % len(self.streams)
+                if not idle:
+                    rr += 1
+                s = self.streams[si]
+                plan = self.plans[si]
+                q = inflight[si]
                 with torch.cuda.stream(s):
                     for r, oi, _ in wave:
                         hw = r.h * r.w

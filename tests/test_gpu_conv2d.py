@@ -304,3 +304,19 @@ def test_full_size_gaussian_separable_sampled():
     pts = sample_points(99, c, h, w, 50000)
     ref, bound = oracle.conv2d_sep_points(img, g, g, pts)
     assert_within(gather(d_out, pts), ref, bound, F32_TOL, "gaussian sep full")
+
+
+def test_small_workload_512x512_5x5_whole_image():
+    """The small plain workload exactly: one 512 x 512 FP32 image with pixels
+    U[0,1) and a 5 x 5 filter of normalised U[0,1) weights, clamp-to-edge,
+    every output pixel against the oracle (1e-6 * sum|k||x|), through the
+    stream-ordered call and the synchronous plain call on host arrays (the
+    same bits)."""
+    img = synth.image_f32(synth.SEEDS["conv512"], 1, 512, 512)
+    k = synth.filter_f32(synth.SEEDS["conv512"] + 1, 5, 5)
+    got = run_conv(img, k).cpu().numpy()
+    ref, bound = oracle.conv2d(img, k)
+    assert_within(got, ref, bound, F32_TOL, "512x512 5x5")
+    host_out = np.empty((512, 512), dtype=np.float32)
+    pg.pencil_conv2d(512, 512, img[0], 5, 5, k, host_out)
+    np.testing.assert_array_equal(host_out.view(np.uint32), got[0].view(np.uint32))

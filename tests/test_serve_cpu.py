@@ -273,3 +273,14 @@ def test_server_loop_on_a_fake_device(fake_server, mode):
     assert none is None and st2.expired > 0
     assert st2.expired + int(np.isfinite(st2.latency_ms).sum()) == n
     assert pg.pencil_arena_free_bytes(srv.arena) == 1 << 20
+
+
+def test_waves_batch_only_under_load():
+    from paper_1302_5586_gb300 import serve
+    assert serve.wave_limit("plain", 50, 4, 64) == 1
+    assert serve.wave_limit("served", 1, 4, 64) == 1        # a lone request goes alone
+    assert serve.wave_limit("served", 3, 4, 64) == 1        # fewer requests than idle streams
+    assert serve.wave_limit("served", 10, 4, 64) == 3       # spread over the idle streams
+    assert serve.wave_limit("served", 10, 0, 64) == 64      # every stream busy: the queue forms a wave
+    assert serve.wave_limit("served", 500, 2, 64) == 64     # never beyond max_wave
+    assert serve.wave_limit("served", 0, 4, 64) == 1
