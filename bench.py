@@ -668,7 +668,7 @@ def measure_batched(torch, pg, dev, stream):
     return res, keep
 
 
-def measure_e2e(torch, pg, img, ks, g, steps):
+def measure_e2e(torch, pg, img, ks, g, steps, down_streams=1):
     """The step end to end from pinned HOST memory through the public
     stream-ordered calls: every step uploads its 3 x 8192^2 input image once
     (768 MiB), runs the four passes (pencil_conv2d_ex x3, pencil_conv2d_sep_ex)
@@ -684,13 +684,14 @@ def measure_e2e(torch, pg, img, ks, g, steps):
     d_out = [[torch.empty_like(h_in, device=dev) for _ in range(PASSES)] for _ in range(2)]
     d_ks = [torch.from_numpy(k).to(dev) for k in ks]
     d_g = torch.from_numpy(g).to(dev)
-    up, comp, down = (torch.cuda.Stream(dev) for _ in range(3))
+    up, comp = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    downs = [torch.cuda.Stream(dev) for _ in range(down_streams)]  # pass n downloads on downs[n % len]
     in_free = [torch.cuda.Event() for _ in range(2)]            # compute done reading d_in[b]
     out_free = [[torch.cuda.Event() for _ in range(PASSES)] for _ in range(2)]  # download of d_out[b][n] done
     for b in range(2):
         in_free[b].record(comp)
         for n in range(PASSES):
-            out_free[b][n].record(down)
+            out_free[b][n].record(downs[n % len(downs)])
 
     def step(i):
         bb = i & 1
@@ -710,6 +711,7 @@ def measure_e2e(torch, pg, img, ks, g, steps):
                                         comp.cuda_stream)
             done = torch.cuda.Event()
             done.record(comp)
+            down = downs[n % len(downs)]
             down.wait_event(done)
             with torch.cuda.stream(down):
                 h_out[n].copy_(d_out[bb][n], non_blocking=True)

@@ -196,7 +196,7 @@ int pencil_conv2d_jacobi(int c, int h, int w, const float *in, int kh, int kw, c
 /* ------------------------------------------------------------------- batch
  * Many images, each with its own size and odd filter side 1..15, convolved by
  * ONE graph launch: the captured graph holds one persistent kernel per filter
- * side present (largest side first, back to back), each sized to its side's
+ * side present (independent graph nodes that may run side by side), each sized to its side's
  * register and shared-memory needs.  A side's tiles are handed out from its
  * own work queue, larger images first, so uneven images keep every SM busy; each
  * batched pixel is the same bits as pencil_conv2d_ex on that image alone (the

@@ -4,15 +4,15 @@
 // The host builds a tile table grouped by filter side (within a side, images
 // with more tiles first) and a queue header {next, total, start} per side;
 // every tile of image i gets the entry i.  Header, image descriptors and
-// table are copied to a device buffer owned by the plan.  The graph launches,
+// table are copied to a device buffer owned by the plan.  The graph holds,
 // for every side present in the batch, a resident grid (SMs x CTAs per SM)
-// of that side's kernel; its CTAs take tile indices from the side's `next`
-// with one atomicAdd per tile, look the image up, and run the same tile body
-// as the standalone direct kernel, so every batched pixel is the same bits as
-// pencil_conv2d_ex on that image alone.  One kernel per side keeps each
-// kernel's code small (one tile body, two tile heights) and gives it its own
-// register budget and shared-memory slot size, so small filters run more CTAs
-// per SM.  Each side has one or two staging slots (two: the copies of a
+// of that side's kernel, as independent nodes that may run side by side; its
+// CTAs take tile indices from the side's `next` with one atomicAdd per tile,
+// look the image up, and run the same tile body as the standalone direct
+// kernel, so every batched pixel is the same bits as pencil_conv2d_ex on that
+// image alone.  One kernel per side and tile variant keeps each kernel's code
+// small (one tile body) and gives it its own register budget and
+// shared-memory slot size, so small filters run more CTAs per SM.  Each side has one or two staging slots (two: the copies of a
 // CTA's next tile run while the current one is computed), chosen per side by
 // measurement, as is its CTA count per SM.  Kernels read the tile counts
 // from the device headers, so the graph captured for a set of sides serves
@@ -308,36 +308,39 @@ bool batch_disjoint(int n, const pencil_image *imgs, size_t esz) {
     return true;
 }
 
-// The graph for a set of sides (bit i = side 2i+1): one launch per side, largest first.
+// The graph for a set of sides (bit i = side 2i+1): one kernel node per side,
+// with no edges between them, so the sides' kernels may run side by side: a
+// side whose queue is short (a small wave of requests) leaves SMs to the
+// next side at once instead of holding the others back, and at the end of a
+// long side the next one fills the SMs it frees.
 cudaError_t graph_for(pencil_batch *b, unsigned mask, cudaGraphExec_t *out) {
     auto it = b->exec.find(mask);
     if (it != b->exec.end()) {
         *out = it->second;
         return cudaSuccess;
     }
-    cudaStream_t cs;
-    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return e;
     BatchHeader *hdr = static_cast<BatchHeader *>(b->dbuf);
     BatchImage *imgs = reinterpret_cast<BatchImage *>(static_cast<char *>(b->dbuf) +
                                                       align256(sizeof(BatchHeader) * kSides));
     int *tile_img = reinterpret_cast<int *>(static_cast<char *>(b->dbuf) + head_bytes(b->max_images));
     cudaGraph_t g = nullptr;
     cudaGraphExec_t x = nullptr;
-    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        cudaError_t le = cudaSuccess;
-        for (int i = kSides - 1; i >= 0 && le == cudaSuccess; --i)
-            if (mask & (1u << i)) {
-                b->fn[i]<<<b->grid[i], b->nt[i], b->smem[i], cs>>>(hdr + i, imgs, tile_img);
-                le = cudaGetLastError();
-            }
-        e = cudaStreamEndCapture(cs, &g);
-        if (e == cudaSuccess) e = le;
-    }
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    for (int i = kSides - 1; i >= 0 && e == cudaSuccess; --i)
+        if (mask & (1u << i)) {
+            BatchHeader *h = hdr + i;
+            void *args[] = {&h, &imgs, &tile_img};
+            cudaKernelNodeParams p = {};
+            p.func = reinterpret_cast<void *>(b->fn[i]);
+            p.gridDim = dim3((unsigned)b->grid[i]);
+            p.blockDim = dim3((unsigned)b->nt[i]);
+            p.sharedMemBytes = (unsigned)b->smem[i];
+            p.kernelParams = args;
+            cudaGraphNode_t node;
+            e = cudaGraphAddKernelNode(&node, g, nullptr, 0, &p);
+        }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
     if (g) cudaGraphDestroy(g);
-    cudaStreamDestroy(cs);
     if (e == cudaSuccess) {
         b->exec[mask] = x;
         *out = x;

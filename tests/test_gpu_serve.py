@@ -26,6 +26,8 @@ def alone(req, host_pool, bank, dtype):
 def test_each_result_is_the_same_alone_and_in_the_mix(dtype):
     tr = serve.make_trace(77, rate=20000.0, duration=0.01, lo=8, hi=400, klo=1, khi=15, pool_elems=1 << 20)
     assert len(tr.requests) > 100
+    for r in tr.requests:  # one burst: every stream is soon busy, so the queue forms batched waves
+        r.arrival = 0.0
     pool = serve.host_pool(tr, dtype, 78)
     bank = torch.from_numpy(tr.filters).to(dev())
     srv = serve.Server(dtype=dtype, budget_bytes=64 << 20, streams=3, max_wave=16, max_inflight=48)
