@@ -243,16 +243,21 @@ class Server:
 
     def warm_up(self):
         """Before serving: load every filter side's kernels (batched and
-        standalone) and build each plan's one-side launch graphs, on a tiny
-        image, so the first requests do not pay those one-time costs."""
+        standalone) and build each plan's launch graph for every set of filter
+        sides a wave can hold (255 sets), on tiny images, so no request waits
+        behind a one-time kernel load or graph instantiation on the serving
+        thread."""
         torch = self.torch
-        img = torch.zeros((16, 16), dtype=self.tdtype, device=self.dev)
-        out = torch.empty_like(img)
+        imgs = torch.zeros((8, 16, 16), dtype=self.tdtype, device=self.dev)
+        outs = torch.empty_like(imgs)
         k = torch.zeros(15 * 15, dtype=torch.float32, device=self.dev)
         for s, plan in zip(self.streams, self.plans):
             for ks in range(1, 16, 2):
-                b.pencil_batch_run(plan, b.make_images([(img, out, k, 16, 16, ks)]), s.cuda_stream)
-                b.pencil_conv2d_ex(1, 16, 16, img, ks, ks, k, out, self.dtype, 0, s.cuda_stream)
+                b.pencil_conv2d_ex(1, 16, 16, imgs[0], ks, ks, k, outs[0], self.dtype, 0, s.cuda_stream)
+            for mask in range(1, 256):
+                sides = [2 * i + 1 for i in range(8) if mask >> i & 1]
+                b.pencil_batch_run(plan, b.make_images([(imgs[j], outs[j], k, 16, 16, ks)
+                                                        for j, ks in enumerate(sides)]), s.cuda_stream)
         torch.cuda.synchronize(self.dev)
 
     def close(self):
