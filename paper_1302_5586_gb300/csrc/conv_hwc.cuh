@@ -23,19 +23,23 @@ namespace {
 
 using namespace tile;
 
-// Element tiles of 32 rows x 128 elements, one 4-element group per thread
-// (the tap window of a group is (kw-1)*CS + 4 elements wide).  Binary16
-// images up to side 7 read their staged tile as binary16, as the planar
-// kernels do.  Rows that are 16-byte aligned (clamp or zero border) load by
-// TMA; every other case takes one cp.async kernel per side that handles all
-// border modes.
-template <typename T, int K, int TX, int TY, int R, int MINB, bool HW, int CS>
+// Element tiles of TY*R rows x TX*C elements, C consecutive elements per
+// thread: C = 12 (three 16-byte chunks) for sides from 5 up, so one tap
+// window of (kw-1)*CS + C elements feeds 12 outputs instead of 4 -- with taps
+// CS elements apart, a 4-element group re-reads most of its window from
+// shared memory for every 4 outputs, and that traffic, not the FMAs, bounded
+// the 4-wide tiles.  Binary16 images up to side 7 read their staged tile as
+// binary16, as the planar kernels do.  Rows that are 16-byte aligned (clamp or
+// zero border) load by TMA; every other case takes one cp.async kernel per
+// side that handles all border modes.
+template <typename T, int K, int TX, int TY, int R, int MINB, bool HW, int CS, int C = 4>
 cudaError_t run_direct_hwc_k(int h, int we, const T *in, const float *k, T *out, bool vec_ok, int border,
                              cudaStream_t s) {
-    using Cfg = DirectCfg<K, K, TX, TY, R, 1, CS>;
+    using Cfg = DirectCfg<K, K, TX, TY, R, 1, CS, C>;
     cudaError_t err = cudaSuccess;
-    if (try_direct_tma<T, K, TX, TY, R, 1, MINB, HW, CS>(1, h, we, in, k, out, vec_ok, border, s, &err)) return err;
-    auto kern = conv2d_direct_kernel<T, K, K, TX, TY, R, 1, MINB, true, HW, 0, CS>;
+    if (try_direct_tma<T, K, TX, TY, R, 1, MINB, HW, CS, C>(1, h, we, in, k, out, vec_ok, border, s, &err))
+        return err;
+    auto kern = conv2d_direct_kernel<T, K, K, TX, TY, R, 1, MINB, true, HW, 0, CS, C>;
     const size_t smem = HW ? Cfg::smem_half : Cfg::smem(sizeof(T));
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
@@ -47,33 +51,46 @@ cudaError_t run_direct_hwc_k(int h, int we, const T *in, const float *k, T *out,
 template <typename T, int CS>
 cudaError_t run_direct_hwc(int K, int h, int we, const T *in, const float *k, T *out, bool vec_ok, int border,
                            cudaStream_t s) {
-    constexpr bool HW = sizeof(T) == 2;
+    constexpr bool F16 = sizeof(T) == 2;
+#define PENCIL_HWC_RUN(K_, TX, TY, R, MINB, HW, C) \
+    return run_direct_hwc_k<T, K_, TX, TY, R, MINB, HW, CS, C>(h, we, in, k, out, vec_ok, border, s)
     switch (K) {
-        case 1: return run_direct_hwc_k<T, 1, 32, 8, 4, 8, HW, CS>(h, we, in, k, out, vec_ok, border, s);
-        case 3: return run_direct_hwc_k<T, 3, 32, 8, 4, 8, HW, CS>(h, we, in, k, out, vec_ok, border, s);
-        case 5: return run_direct_hwc_k<T, 5, 32, 8, 4, 6, HW, CS>(h, we, in, k, out, vec_ok, border, s);
-        case 7: return run_direct_hwc_k<T, 7, 32, 8, 4, 4, HW, CS>(h, we, in, k, out, vec_ok, border, s);
-        case 9: return run_direct_hwc_k<T, 9, 32, 8, 4, 2, false, CS>(h, we, in, k, out, vec_ok, border, s);
-        case 11: return run_direct_hwc_k<T, 11, 32, 8, 4, 2, false, CS>(h, we, in, k, out, vec_ok, border, s);
-        case 13: return run_direct_hwc_k<T, 13, 32, 8, 4, 2, false, CS>(h, we, in, k, out, vec_ok, border, s);
-        case 15: return run_direct_hwc_k<T, 15, 32, 8, 4, 2, false, CS>(h, we, in, k, out, vec_ok, border, s);
+        case 1: PENCIL_HWC_RUN(1, 32, 8, 4, 8, F16, 4);
+        case 3:
+            if constexpr (F16) PENCIL_HWC_RUN(3, 16, 8, 2, 8, true, 12);
+            else PENCIL_HWC_RUN(3, 32, 8, 4, 8, false, 4);
+        case 5:
+            if constexpr (F16) PENCIL_HWC_RUN(5, 16, 8, 4, 4, true, 12);
+            else PENCIL_HWC_RUN(5, 16, 8, 2, 6, false, 12);
+        case 7:
+            if constexpr (F16) PENCIL_HWC_RUN(7, 16, 8, 4, 3, true, 12);
+            else PENCIL_HWC_RUN(7, 16, 8, 2, CS == 3 ? 6 : 5, false, 12);
+        case 9: PENCIL_HWC_RUN(9, 16, 8, 2, 3, false, 12);
+        case 11: PENCIL_HWC_RUN(11, 16, 8, 2, 3, false, 12);
+        case 13: PENCIL_HWC_RUN(13, 16, 8, 2, 3, false, 12);
+        case 15:
+            if constexpr (F16) PENCIL_HWC_RUN(15, 16, 16, 2, 2, false, 12);
+            else PENCIL_HWC_RUN(15, 16, 8, 2, 4, false, 12);
         default: return cudaErrorInvalidValue;
     }
+#undef PENCIL_HWC_RUN
 }
 
-// Separable: the planar tiles, row-pass taps CS elements apart; TMA for
-// aligned rows (clamp or zero border), one cp.async kernel otherwise.
-template <typename T, int K, int TX, int TY, int R, int MINB, bool INPLACE, int CS>
+// Separable: the planar tiles, row-pass taps CS elements apart, row-pass
+// items of 12 elements (three chunks share one tap window; the column pass
+// keeps 4-column items); TMA for aligned rows (clamp or zero border), one
+// cp.async kernel otherwise.
+template <typename T, int K, int TX, int TY, int R, int MINB, bool INPLACE, int CS, int CR = 4>
 cudaError_t run_sep_hwc_k(int h, int we, const T *in, const float *gx, const float *gy, T *out, bool vec_ok,
                           int border, cudaStream_t s) {
-    using Cfg = SepCfg<K, K, TX, TY, R, INPLACE, CS>;
+    using Cfg = SepCfg<K, K, TX, TY, R, INPLACE, CS, false, CR>;
     using Kern = void (*)(const CUtensorMap, const T *, const float *, const float *, T *, int, int, bool, int);
     static_assert(Cfg::SW <= 256 && Cfg::SH <= 256, "a TMA box side is at most 256 elements");
     constexpr int PAIR = sep_pair<T>(K);
     CUtensorMap tmap = {};
-    Kern kern = conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 0, CS>;
+    Kern kern = conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 0, CS, false, CR>;
     if (vec_ok && (border == 0 || border == 1) && image_tensor_map<T>(&tmap, in, 1, h, we, Cfg::SW, Cfg::SH))
-        kern = conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 3, CS>;
+        kern = conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 3, CS, false, CR>;
     const size_t smem = Cfg::smem(sizeof(T));
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
@@ -85,16 +102,21 @@ cudaError_t run_sep_hwc_k(int h, int we, const T *in, const float *gx, const flo
 template <typename T, int CS>
 cudaError_t run_sep_hwc(int K, int h, int we, const T *in, const float *gx, const float *gy, T *out, bool vec_ok,
                         int border, cudaStream_t s) {
+#define PENCIL_HWC_SEP(K_, TX, TY, R, MINB, IP) \
+    return run_sep_hwc_k<T, K_, TX, TY, R, MINB, IP, CS, 12>(h, we, in, gx, gy, out, vec_ok, border, s)
     switch (K) {
-        case 3: return run_sep_hwc_k<T, 3, 32, 8, 4, 1, false, CS>(h, we, in, gx, gy, out, vec_ok, border, s);
-        case 5: return run_sep_hwc_k<T, 5, 32, 8, 4, 1, false, CS>(h, we, in, gx, gy, out, vec_ok, border, s);
-        case 7: return run_sep_hwc_k<T, 7, 32, 8, 4, 1, false, CS>(h, we, in, gx, gy, out, vec_ok, border, s);
-        case 9: return run_sep_hwc_k<T, 9, 16, 8, 8, 2, true, CS>(h, we, in, gx, gy, out, vec_ok, border, s);
-        case 11: return run_sep_hwc_k<T, 11, 16, 8, 8, 2, true, CS>(h, we, in, gx, gy, out, vec_ok, border, s);
-        case 13: return run_sep_hwc_k<T, 13, 16, 8, 8, 2, true, CS>(h, we, in, gx, gy, out, vec_ok, border, s);
-        case 15: return run_sep_hwc_k<T, 15, 16, 8, 16, 2, true, CS>(h, we, in, gx, gy, out, vec_ok, border, s);
+        case 3: PENCIL_HWC_SEP(3, 48, 4, 4, 2, false);
+        case 5: PENCIL_HWC_SEP(5, 24, 8, 4, 2, false);
+        case 7: PENCIL_HWC_SEP(7, 24, 8, 4, 2, false);
+        case 9: PENCIL_HWC_SEP(9, 24, 8, 8, 2, true);
+        case 11: PENCIL_HWC_SEP(11, 24, 8, 8, 2, true);
+        case 13: PENCIL_HWC_SEP(13, 24, 8, 8, 2, true);
+        case 15:
+            if constexpr (sizeof(T) == 2) PENCIL_HWC_SEP(15, 24, 8, 8, 2, true);
+            else PENCIL_HWC_SEP(15, 24, 8, 16, 1, true);
         default: return cudaErrorInvalidValue;
     }
+#undef PENCIL_HWC_SEP
 }
 
 }  // namespace

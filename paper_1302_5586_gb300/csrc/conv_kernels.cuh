@@ -37,15 +37,15 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 // CS > 1: one interleaved image of CS channels, w = pixels * CS elements per
 // row (grid.z = 1).
 template <typename T, int KH, int KW, int TX, int TY, int R, int G, int MINB, bool ANYB, bool HALFW, int VMODE,
-          int CS = 1>
+          int CS = 1, int C = 4>
 __global__ void __launch_bounds__(TX *TY, MINB)
     conv2d_direct_kernel(const T *__restrict__ in, const float *__restrict__ k, T *__restrict__ out,
                          int h, int w, bool vec_ok, int border) {
-    using Cfg = DirectCfg<KH, KW, TX, TY, R, G, CS>;
+    using Cfg = DirectCfg<KH, KW, TX, TY, R, G, CS, C>;
     extern __shared__ __align__(128) float smem[];
     const size_t plane = (size_t)h * (size_t)w * blockIdx.z;
     const bool vok = VMODE == 0 ? vec_ok : VMODE == 1;
-    direct_tile<T, KH, KW, TX, TY, R, G, ANYB, HALFW, VMODE == 2, CS>(in + plane, k, out + plane, h, w, vok,
+    direct_tile<T, KH, KW, TX, TY, R, G, ANYB, HALFW, VMODE == 2, CS, C>(in + plane, k, out + plane, h, w, vok,
                                                    blockIdx.y * Cfg::TH, blockIdx.x * Cfg::TW, smem, border);
 }
 
@@ -107,11 +107,12 @@ __device__ __forceinline__ void clamp_fixup(S *__restrict__ t, int h, int w, int
 // the shared tile body, so the bits are those of the cp.async kernel.
 // Shared memory: the staged tile (type T, first, 128-byte aligned), the FP32
 // copy of a binary16 tile unless HALFW, the filter rows.
-template <typename T, int KH, int KW, int TX, int TY, int R, int G, int MINB, bool HALFW, bool CLAMP, int CS = 1>
+template <typename T, int KH, int KW, int TX, int TY, int R, int G, int MINB, bool HALFW, bool CLAMP, int CS = 1,
+          int C = 4>
 __global__ void __launch_bounds__(TX *TY, MINB)
     conv2d_direct_tma_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ k,
                              T *__restrict__ out, int h, int w) {
-    using Cfg = DirectCfg<KH, KW, TX, TY, R, G, CS>;
+    using Cfg = DirectCfg<KH, KW, TX, TY, R, G, CS, C>;
     constexpr int SW = Cfg::SW, SH = Cfg::SH, KWP = Cfg::KWP, NT = Cfg::NT;
     constexpr bool F16 = sizeof(T) == 2;
     extern __shared__ __align__(128) float smem[];
@@ -142,10 +143,10 @@ __global__ void __launch_bounds__(TX *TY, MINB)
     if (CLAMP) clamp_fixup<T, SH, SW, NT, CS>(s_t, h, w, gy0, gx0);
     T *dst = out + (size_t)h * (size_t)w * blockIdx.z;
     if constexpr (F16 && HALFW) {
-        direct_compute<T, KH, KW, TX, TY, R, G, T, false, CS>(s_t, s_k, dst, h, w, true, y0, x0);
+        direct_compute<T, KH, KW, TX, TY, R, G, T, false, CS, C>(s_t, s_k, dst, h, w, true, y0, x0);
     } else {
         stage_widen<T, SH, SW, NT>(s_in, s_t);
-        direct_compute<T, KH, KW, TX, TY, R, G, float, false, CS>(s_in, s_k, dst, h, w, true, y0, x0);
+        direct_compute<T, KH, KW, TX, TY, R, G, float, false, CS, C>(s_in, s_k, dst, h, w, true, y0, x0);
     }
 }
 
@@ -193,9 +194,13 @@ __global__ void __launch_bounds__(256)
 // HALFR (binary16 images): the row pass reads the staged binary16 tile and
 // widens each window in registers, so no FP32 copy of the tile exists; its
 // results go to their own FP32 buffer (INPLACE must be false).
-template <int KX, int KY, int TX, int TY, int R, bool INPLACE = false, int CS = 1, bool HALFR = false>
+// CR: columns per row-pass item (a multiple of 4 dividing the tile width);
+// the column pass always takes 4.  Wider items share one tap window among
+// more outputs, which pays where the taps are CS apart.
+template <int KX, int KY, int TX, int TY, int R, bool INPLACE = false, int CS = 1, bool HALFR = false,
+          int CR_ = 4>
 struct SepCfg {
-    static constexpr int C = 4;
+    static constexpr int C = 4, CR = CR_;
     static constexpr int AX = KX / 2, AY = KY / 2;
     static constexpr int AXE = AX * CS;       // row-pass halo in elements
     static constexpr int NT = TX * TY;
@@ -204,7 +209,8 @@ struct SepCfg {
     static constexpr int SW = TW + 2 * P;
     static constexpr int SH = TH + KY - 1;
     static constexpr int M0 = (P - AXE) & ~3;  // first 16-byte chunk a row pass reads
-    static constexpr int NX = round_up(P - AXE - M0 + C + (KX - 1) * CS, 4);
+    static constexpr int NX = round_up(P - AXE - M0 + CR + (KX - 1) * CS, 4);
+    static_assert(CR % 4 == 0 && TW % CR == 0, "row-pass items of whole 16-byte chunks tile a row");
     // in place: the row-pass results overwrite the staged tile (row stride SW);
     // HALFR: only the row-pass results are FP32
     static_assert(!(HALFR && INPLACE), "a binary16 tile read directly cannot take the row-pass results");
@@ -220,7 +226,7 @@ struct SepCfg {
 // as one TMA box of `tmap` (unused by the other modes), as the direct TMA
 // kernel does.
 template <typename T, int KX, int KY, int TX, int TY, int R, int MINB, bool INPLACE, bool ANYB, int PAIR,
-          int VMODE, int CS = 1, bool HALFR = false>
+          int VMODE, int CS = 1, bool HALFR = false, int CR = 4>
 __global__ void __launch_bounds__(TX *TY, MINB)
     conv2d_sep_kernel(const __grid_constant__ CUtensorMap tmap, const T *__restrict__ in,
                       const float *__restrict__ gx, const float *__restrict__ gy, T *__restrict__ out, int h,
@@ -228,7 +234,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
     constexpr bool ADAPT = VMODE == 2, TMA = VMODE == 3;
     static_assert(!HALFR || sizeof(T) == 2, "HALFR reads a binary16 tile");
     const bool vec_ok = VMODE == 0 ? vec_ok_ : VMODE != 2;
-    using Cfg = SepCfg<KX, KY, TX, TY, R, INPLACE, CS, HALFR>;
+    using Cfg = SepCfg<KX, KY, TX, TY, R, INPLACE, CS, HALFR, CR>;
     constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, SH = Cfg::SH, TW = Cfg::TW,
                   NX = Cfg::NX, AY = Cfg::AY, NT = Cfg::NT;
     constexpr int TS = INPLACE ? SW : TW;  // row stride of the row-pass results
@@ -270,16 +276,17 @@ __global__ void __launch_bounds__(TX *TY, MINB)
         stage_tile<T, SH, SW, NT, ANYB, ADAPT, CS>(src, h, w, y0 - AY, x0 - P, vec_ok, s_in, s16, border);
     }
 
-    // row pass: t[r][q*C + c] = sum_b gx[b] * in[r][q*C + c + b - AX]
+    // row pass: t[r][q*CR + c] = sum_b gx[b] * in[r][q*CR + c + b - AX]
     {
         float fx[KX];
 #pragma unroll
         for (int b = 0; b < KX; ++b) fx[b] = __ldg(gx + b);
         constexpr int X0 = P - Cfg::AXE - Cfg::M0;  // window index of tap 0 of column 0
-        constexpr int QPR = TW / C;
+        constexpr int QPR = TW / CR;
         constexpr int ITEMS = SH * QPR;
         constexpr int PER = (ITEMS + NT - 1) / NT;  // items per thread
-        float4 res[INPLACE ? PER : 1];
+        constexpr int NQ = CR / 4;                  // 16-byte chunks per item
+        float4 res[INPLACE ? PER : 1][NQ];
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
             const int idx = threadIdx.x + k * NT;
@@ -287,18 +294,18 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                 const int r = idx / QPR, q = idx - r * QPR;
                 float x[NX];
                 if constexpr (HALFR) {
-                    const T *sp = s16 + r * SW + q * C + Cfg::M0;
+                    const T *sp = s16 + r * SW + q * CR + Cfg::M0;
 #pragma unroll
                     for (int m = 0; m < NX; m += 4) ld4s(sp + m, &x[m]);
                 } else {
-                    const float *sp = s_in + r * SW + q * C + Cfg::M0;
+                    const float *sp = s_in + r * SW + q * CR + Cfg::M0;
 #pragma unroll
                     for (int m = 0; m < NX; m += 4) ld4s(sp + m, &x[m]);
                 }
-                float tv[C];
+                float tv[CR];
                 if constexpr ((PAIR & 1) != 0) {
 #pragma unroll
-                    for (int c = 0; c < C; c += 2) {
+                    for (int c = 0; c < CR; c += 2) {
                         float2 sum = mul2(make_float2(fx[0], fx[0]), make_float2(x[X0 + c], x[X0 + c + 1]));
 #pragma unroll
                         for (int b = 1; b < KX; ++b)
@@ -309,18 +316,21 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                     }
                 } else {
 #pragma unroll
-                    for (int c = 0; c < C; ++c) {
+                    for (int c = 0; c < CR; ++c) {
                         float sum = __fmul_rn(fx[0], x[X0 + c]);
 #pragma unroll
                         for (int b = 1; b < KX; ++b) sum = __fmaf_rn(fx[b], x[X0 + c + b * CS], sum);
                         tv[c] = sum;
                     }
                 }
-                const float4 t4 = make_float4(tv[0], tv[1], tv[2], tv[3]);
-                if (INPLACE)
-                    res[k] = t4;
-                else
-                    *reinterpret_cast<float4 *>(s_t + r * TS + q * C) = t4;
+#pragma unroll
+                for (int j = 0; j < NQ; ++j) {
+                    const float4 t4 = make_float4(tv[4 * j], tv[4 * j + 1], tv[4 * j + 2], tv[4 * j + 3]);
+                    if (INPLACE)
+                        res[k][j] = t4;
+                    else
+                        *reinterpret_cast<float4 *>(s_t + r * TS + q * CR + 4 * j) = t4;
+                }
             }
         }
         if (INPLACE) {
@@ -330,7 +340,8 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                 const int idx = threadIdx.x + k * NT;
                 if (idx < ITEMS) {
                     const int r = idx / QPR, q = idx - r * QPR;
-                    *reinterpret_cast<float4 *>(s_t + r * TS + q * C) = res[k];
+#pragma unroll
+                    for (int j = 0; j < NQ; ++j) *reinterpret_cast<float4 *>(s_t + r * TS + q * CR + 4 * j) = res[k][j];
                 }
             }
         }
@@ -472,16 +483,16 @@ bool image_tensor_map(CUtensorMap *m, const T *base, int c, int h, int w, int bw
 // side is at most 256 elements); false, with nothing launched, where it does
 // not apply.
 // CS > 1: w is the element width of one interleaved image (pixels * CS), c = 1.
-template <typename T, int K, int TX, int TY, int R, int G, int MINB, bool HALFW, int CS = 1>
+template <typename T, int K, int TX, int TY, int R, int G, int MINB, bool HALFW, int CS = 1, int C = 4>
 bool try_direct_tma(int c, int h, int w, const T *in, const float *k, T *out, bool vec_ok, int border,
                     cudaStream_t s, cudaError_t *err) {
-    using Cfg = DirectCfg<K, K, TX, TY, R, G, CS>;
+    using Cfg = DirectCfg<K, K, TX, TY, R, G, CS, C>;
     static_assert(Cfg::SW <= 256 && Cfg::SH <= 256, "a TMA box side is at most 256 elements");
     CUtensorMap tmap;
     if (!vec_ok || (border != 0 && border != 1) || !image_tensor_map<T>(&tmap, in, c, h, w, Cfg::SW, Cfg::SH))
         return false;
-    auto kern = border == 0 ? conv2d_direct_tma_kernel<T, K, K, TX, TY, R, G, MINB, HALFW, true, CS>
-                            : conv2d_direct_tma_kernel<T, K, K, TX, TY, R, G, MINB, HALFW, false, CS>;
+    auto kern = border == 0 ? conv2d_direct_tma_kernel<T, K, K, TX, TY, R, G, MINB, HALFW, true, CS, C>
+                            : conv2d_direct_tma_kernel<T, K, K, TX, TY, R, G, MINB, HALFW, false, CS, C>;
     const size_t smem = HALFW ? Cfg::smem_half : Cfg::smem(sizeof(T));
     *err = set_smem(kern, smem);
     if (*err == cudaSuccess) {

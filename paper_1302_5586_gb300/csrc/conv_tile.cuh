@@ -308,9 +308,12 @@ __device__ __forceinline__ void store_block(T *__restrict__ dst, int h, int w, i
 // so the loads of a warp stay contiguous (conflict-free LDS.128) in every group.
 // CS > 1: columns are elements of an interleaved image of CS channels; tap b
 // of an element lies b*CS elements further, so the halo is AW*CS elements.
-template <int KH, int KW, int TX, int TY, int R, int G, int CS_ = 1>
+// C_: adjacent columns per group (a multiple of 4): wider groups share one
+// window load among more outputs, which pays where the taps are CS apart.
+template <int KH, int KW, int TX, int TY, int R, int G, int CS_ = 1, int C_ = 4>
 struct DirectCfg {
-    static constexpr int C = 4;
+    static constexpr int C = C_;
+    static_assert(C_ % 4 == 0, "groups of whole 16-byte chunks");
     static constexpr int CS = CS_;
     static constexpr int AH = KH / 2, AW = KW / 2;
     static constexpr int AWE = AW * CS;             // left halo in elements
@@ -347,9 +350,10 @@ __device__ __forceinline__ void ld4s(const __half *p, float *d) {
 // One staged input row r applied to every output row o that uses it (filter
 // row a = r - o).  CHECK tests a against [0, KH); for a compile-time r the test
 // folds away.
-template <bool CHECK, int R, int G, int GS, int KH, int KW, int KWP, int NX, int B0, typename S, int CS = 1>
+template <bool CHECK, int R, int G, int GS, int KH, int KW, int KWP, int NX, int B0, typename S, int CS = 1,
+          int C = 4>
 __device__ __forceinline__ void direct_row(int r, const S *__restrict__ xrow,
-                                           const float *__restrict__ s_k, float (&acc)[R][G * 4]) {
+                                           const float *__restrict__ s_k, float (&acc)[R][G * C]) {
     float x[G][NX];
 #pragma unroll
     for (int g = 0; g < G; ++g)
@@ -368,11 +372,11 @@ __device__ __forceinline__ void direct_row(int r, const S *__restrict__ xrow,
 #pragma unroll
             for (int g = 0; g < G; ++g)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < C; ++c) {
                     float sum = __fmul_rn(kr[0], x[g][B0 + c]);
 #pragma unroll
                     for (int b = 1; b < KW; ++b) sum = __fmaf_rn(kr[b], x[g][B0 + c + b * CS], sum);
-                    acc[o][g * 4 + c] = __fadd_rn(acc[o][g * 4 + c], sum);
+                    acc[o][g * C + c] = __fadd_rn(acc[o][g * C + c], sum);
                 }
         }
     }
@@ -385,16 +389,17 @@ __device__ __forceinline__ void direct_row(int r, const S *__restrict__ xrow,
 // far as the taps of column 3 reach.  S: the staged type (FP32, or binary16
 // widened as it is read).  CS: element distance between taps (the channels
 // of an interleaved image).
-template <int KH, int KW, int R, int G, int GS, int SW, int KWP, int B0_, typename S = float, int CS = 1>
+template <int KH, int KW, int R, int G, int GS, int SW, int KWP, int B0_, typename S = float, int CS = 1,
+          int C = 4>
 __device__ __forceinline__ void direct_accumulate(const S *__restrict__ srow_,
-                                                  const float *__restrict__ s_k, float (&acc)[R][G * 4]) {
+                                                  const float *__restrict__ s_k, float (&acc)[R][G * C]) {
     constexpr int M0 = B0_ & ~3, B0 = B0_ - M0;
-    constexpr int NX = round_up(B0 + 4 + (KW - 1) * CS, 4);
+    constexpr int NX = round_up(B0 + C + (KW - 1) * CS, 4);
     const S *srow = srow_ + M0;
 #pragma unroll
     for (int o = 0; o < R; ++o)
 #pragma unroll
-        for (int c = 0; c < G * 4; ++c) acc[o][c] = 0.0f;
+        for (int c = 0; c < G * C; ++c) acc[o][c] = 0.0f;
 
     // Rows r < R-1 and r >= KH feed only some output rows: fully unrolled, so
     // the validity tests are resolved at compile time.  Rows R-1 <= r <= KH-1
@@ -404,39 +409,41 @@ __device__ __forceinline__ void direct_accumulate(const S *__restrict__ srow_,
     constexpr int EPI = (KH > PRO) ? KH : PRO;
 #pragma unroll
     for (int r = 0; r < PRO; ++r)
-        direct_row<true, R, G, GS, KH, KW, KWP, NX, B0, S, CS>(r, srow + r * SW, s_k, acc);
+        direct_row<true, R, G, GS, KH, KW, KWP, NX, B0, S, CS, C>(r, srow + r * SW, s_k, acc);
 #pragma unroll 1
     for (int r = PRO; r < EPI; ++r)
-        direct_row<false, R, G, GS, KH, KW, KWP, NX, B0, S, CS>(r, srow + r * SW, s_k, acc);
+        direct_row<false, R, G, GS, KH, KW, KWP, NX, B0, S, CS, C>(r, srow + r * SW, s_k, acc);
 #pragma unroll
     for (int r = EPI; r < NR; ++r)
-        direct_row<true, R, G, GS, KH, KW, KWP, NX, B0, S, CS>(r, srow + r * SW, s_k, acc);
+        direct_row<true, R, G, GS, KH, KW, KWP, NX, B0, S, CS, C>(r, srow + r * SW, s_k, acc);
 }
 
 // Compute and store one TH x TW output tile with origin (y0, x0) from a
 // staged tile s_in (see stage_tile; FP32, or the binary16 staging area read
 // directly) and staged filter rows s_k.
 template <typename T, int KH, int KW, int TX, int TY, int R, int G, typename S = float, bool ADAPT = true,
-          int CS = 1>
+          int CS = 1, int C_ = 4>
 __device__ __forceinline__ void direct_compute(const S *__restrict__ s_in,
                                                const float *__restrict__ s_k, T *__restrict__ dst,
                                                int h, int w, bool vec_ok, int y0, int x0) {
-    using Cfg = DirectCfg<KH, KW, TX, TY, R, G, CS>;
+    using Cfg = DirectCfg<KH, KW, TX, TY, R, G, CS, C_>;
     constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, KWP = Cfg::KWP, GS = Cfg::GS;
     constexpr int B0 = P - Cfg::AWE;  // x index of tap 0 for column 0
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    float acc[R][G * 4];
-    direct_accumulate<KH, KW, R, G, GS, SW, KWP, B0, S, CS>(s_in + (ty * R) * SW + tx * C, s_k, acc);
+    float acc[R][G * C];
+    direct_accumulate<KH, KW, R, G, GS, SW, KWP, B0, S, CS, C>(s_in + (ty * R) * SW + tx * C, s_k, acc);
 
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-        float blk[R][4];
+    for (int g = 0; g < G; ++g)
 #pragma unroll
-        for (int o = 0; o < R; ++o)
+        for (int q = 0; q < C / 4; ++q) {
+            float blk[R][4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) blk[o][c] = acc[o][g * 4 + c];
-        store_block<T, R, ADAPT>(dst, h, w, y0 + ty * R, x0 + g * GS + tx * C, vec_ok, blk);
-    }
+            for (int o = 0; o < R; ++o)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) blk[o][c] = acc[o][g * C + q * 4 + c];
+            store_block<T, R, ADAPT>(dst, h, w, y0 + ty * R, x0 + g * GS + tx * C + q * 4, vec_ok, blk);
+        }
 }
 
 // Filter rows into shared memory with 4-byte cp.async (part of the caller's
@@ -468,11 +475,11 @@ __device__ __forceinline__ void stage_filter(const float *__restrict__ k, float 
 // memory and is widened as the windows are read -- half the shared-memory
 // traffic of an FP32 copy, for sides where that traffic is the limit.
 template <typename T, int KH, int KW, int TX, int TY, int R, int G, bool ANYB = false, bool HALFW = false,
-          bool ADAPT = true, int CS = 1>
+          bool ADAPT = true, int CS = 1, int C = 4>
 __device__ __forceinline__ void direct_tile(const T *__restrict__ src, const float *__restrict__ k,
                                             T *__restrict__ dst, int h, int w, bool vec_ok, int y0,
                                             int x0, float *__restrict__ smem, int border = 0) {
-    using Cfg = DirectCfg<KH, KW, TX, TY, R, G, CS>;
+    using Cfg = DirectCfg<KH, KW, TX, TY, R, G, CS, C>;
     constexpr int SW = Cfg::SW, SH = Cfg::SH, KWP = Cfg::KWP, AH = Cfg::AH, P = Cfg::P;
     if constexpr (HALFW) {
         static_assert(sizeof(T) == 2, "HALFW reads a binary16 tile");
@@ -482,14 +489,14 @@ __device__ __forceinline__ void direct_tile(const T *__restrict__ src, const flo
         stage_issue<T, SH, SW, Cfg::NT, ANYB, ADAPT, CS>(src, h, w, y0 - AH, x0 - P, vec_ok, nullptr, s16, border);
         cp_async_wait_all();
         __syncthreads();
-        direct_compute<T, KH, KW, TX, TY, R, G, T, ADAPT, CS>(s16, s_k, dst, h, w, vec_ok, y0, x0);
+        direct_compute<T, KH, KW, TX, TY, R, G, T, ADAPT, CS, C>(s16, s_k, dst, h, w, vec_ok, y0, x0);
     } else {
         float *s_in = smem;
         float *s_k = smem + SH * SW;
         T *s16 = reinterpret_cast<T *>(smem + SH * SW + KH * KWP);
         stage_filter<KH, KW, KWP, Cfg::NT>(k, s_k);
         stage_tile<T, SH, SW, Cfg::NT, ANYB, ADAPT, CS>(src, h, w, y0 - AH, x0 - P, vec_ok, s_in, s16, border);
-        direct_compute<T, KH, KW, TX, TY, R, G, float, ADAPT, CS>(s_in, s_k, dst, h, w, vec_ok, y0, x0);
+        direct_compute<T, KH, KW, TX, TY, R, G, float, ADAPT, CS, C>(s_in, s_k, dst, h, w, vec_ok, y0, x0);
     }
 }
 
