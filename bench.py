@@ -256,7 +256,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = flops_15 / (k15_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
     traffic = traffic_record("conv2d_direct_f32_15x15_8192x8192x3")
-    roofline = {"bound": "alu", "kernel": "conv2d_direct_tma_kernel<float,15,15,16,8,4,2,3,false,true,1,4>",
+    roofline = {"bound": "alu", "kernel": "conv2d_direct_tma_kernel<float,15,15,16,8,2,1,3,false,true,1,12>",
                 "achieved": round(achieved, 3),
                 "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                 "peak_source": _PEAK["source"],

@@ -86,10 +86,11 @@ cudaError_t run_direct_k(int K, int c, int h, int w, const T *in, const float *k
     cudaError_t err = cudaSuccess;
     if (try_direct_small<T>(K, c, h, w, in, k, out, vec_ok, border, s, &err)) return err;
     // Tile shapes and register caps per side, from timing sweeps on GB300 at
-    // 8192 x 8192 x 3 (small sides: occupancy for HBM streaming; large sides:
-    // two column groups so each filter-row load feeds eight FMA chains).  All
-    // tiles are 128 columns wide, so the staged box (at most 144 columns)
-    // fits one TMA load.
+    // 8192 x 8192 x 3 (small sides: occupancy for HBM streaming; side 9: two
+    // 4-column groups so each filter-row load feeds eight FMA chains; sides
+    // 11..15: one 12-column group over 2 rows, 192-column tiles, 1-3% faster
+    // than the two groups).  The staged box (at most 208 columns) fits one
+    // TMA load.
     // Binary16 images up to side 7 keep the tile binary16 in shared memory
     // (HALFW): those kernels are bound by shared-memory traffic, which the
     // FP32 copy doubles; from side 9 the widening in the inner loop costs more
@@ -112,11 +113,16 @@ cudaError_t run_direct_k(int K, int c, int h, int w, const T *in, const float *k
             default: break;
         }
     }
+    constexpr bool F16 = sizeof(T) == 2;
     switch (K) {
         case 9: return run_direct<T, 9, 16, 8, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
-        case 11: return run_direct<T, 11, 16, 8, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
-        case 13: return run_direct<T, 13, 16, 8, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
-        case 15: return run_direct<T, 15, 16, 8, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
+        case 11:
+            if constexpr (F16) return run_direct<T, 11, 16, 8, 4, 2, 3>(c, h, w, in, k, out, vec_ok, border, s);
+            else return run_direct<T, 11, 16, 8, 2, 1, 3, false, 1, 12>(c, h, w, in, k, out, vec_ok, border, s);
+        case 13: return run_direct<T, 13, 16, 8, 2, 1, 3, false, 1, 12>(c, h, w, in, k, out, vec_ok, border, s);
+        case 15:
+            if constexpr (F16) return run_direct<T, 15, 16, 16, 2, 1, 2, false, 1, 12>(c, h, w, in, k, out, vec_ok, border, s);
+            else return run_direct<T, 15, 16, 8, 2, 1, 3, false, 1, 12>(c, h, w, in, k, out, vec_ok, border, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -129,17 +135,19 @@ cudaError_t run_sep_any(int c, int h, int w, const T *in, int kx, const float *g
     // Binary16 images: the row pass reads the staged binary16 tile directly
     // (no FP32 copy, no widening pass), 256-thread CTAs of 8 rows per thread;
     // that measured 17-40% faster than widening the tile first on every side
-    // (15 taps: 0.375 -> 0.299 ms, 3 taps: 0.257 -> 0.156 ms).
+    // (15 taps: 0.375 -> 0.299 ms, 3 taps: 0.257 -> 0.156 ms).  Row-pass
+    // items of 8 columns (sides 11..15) or 12 (side 3) widen each binary16
+    // window once for more outputs: 3-5% more.
     if constexpr (sizeof(T) == 2) {
         if (kx == ky) {
             switch (kx) {
-                case 3: return run_sep<T, 3, 32, 8, 8, 3, false, sep_pair<T>(3), 1, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+                case 3: return run_sep<T, 3, 48, 4, 8, 3, false, sep_pair<T>(3), 1, true, 12>(c, h, w, in, gx, gy, out, vec_ok, border, s);
                 case 5: return run_sep<T, 5, 32, 8, 8, 3, false, sep_pair<T>(5), 1, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
                 case 7: return run_sep<T, 7, 32, 8, 8, 3, false, sep_pair<T>(7), 1, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
                 case 9: return run_sep<T, 9, 32, 8, 8, 3, false, sep_pair<T>(9), 1, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
-                case 11: return run_sep<T, 11, 16, 16, 8, 3, false, sep_pair<T>(11), 1, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
-                case 13: return run_sep<T, 13, 16, 16, 8, 3, false, sep_pair<T>(13), 1, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
-                case 15: return run_sep<T, 15, 16, 16, 8, 3, false, sep_pair<T>(15), 1, true>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+                case 11: return run_sep<T, 11, 16, 16, 8, 3, false, sep_pair<T>(11), 1, true, 8>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+                case 13: return run_sep<T, 13, 16, 16, 8, 3, false, sep_pair<T>(13), 1, true, 8>(c, h, w, in, gx, gy, out, vec_ok, border, s);
+                case 15: return run_sep<T, 15, 16, 16, 8, 3, false, sep_pair<T>(15), 1, true, 8>(c, h, w, in, gx, gy, out, vec_ok, border, s);
                 default: break;
             }
         }

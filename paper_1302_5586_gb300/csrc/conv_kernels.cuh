@@ -150,6 +150,72 @@ __global__ void __launch_bounds__(TX *TY, MINB)
     }
 }
 
+// Planar images whose rows are not 16-byte aligned, clamp (CLAMP) or zero
+// border: the tile staged by row-wise TMA boxes of the flat image (tile's
+// RowStage), then realigned -- in place for FP32 (the tile is the landing
+// area, row stride LP), into a binary16 tile for HALFW, widened into an FP32
+// tile for other binary16 images (each measured faster than the other
+// choices) -- and the same compute as the other direct kernels.  Stores take
+// the widest access each address allows.  Shared memory: landing rows
+// (128-byte aligned, first), the separate tile, the filter rows.
+template <typename T, int KH, int KW, int TX, int TY, int R, int G, int MINB, bool HALFW, bool CLAMP, int C = 4>
+struct DirectRows {
+    using Cfg = DirectCfg<KH, KW, TX, TY, R, G, 1, C>;
+    using RS = RowStage<T, Cfg::SH, Cfg::SW>;
+    static constexpr bool INPLACE = sizeof(T) == 4;
+    static constexpr size_t tile_bytes = INPLACE ? 0 : (HALFW ? 2 : 4) * (size_t)Cfg::SH * Cfg::SW;
+    static constexpr size_t smem = RS::bytes + tile_bytes + sizeof(float) * KH * Cfg::KWP;
+};
+
+template <typename T, int KH, int KW, int TX, int TY, int R, int G, int MINB, bool HALFW, bool CLAMP, int C = 4>
+__global__ void __launch_bounds__(TX *TY, MINB)
+    conv2d_direct_rows_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ k,
+                              T *__restrict__ out, int h, int w) {
+    using DR = DirectRows<T, KH, KW, TX, TY, R, G, MINB, HALFW, CLAMP, C>;
+    using Cfg = typename DR::Cfg;
+    using RS = typename DR::RS;
+    constexpr int SW = Cfg::SW, SH = Cfg::SH, KWP = Cfg::KWP, NT = Cfg::NT;
+    static_assert(!HALFW || sizeof(T) == 2, "HALFW reads a binary16 tile");
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_shift[SH];
+    T *land = reinterpret_cast<T *>(smem);
+    float *s_in = smem + RS::bytes / sizeof(float);  // the separate tile (FP32, or HALFW binary16)
+    T *s16 = reinterpret_cast<T *>(s_in);
+    float *s_k = s_in + DR::tile_bytes / sizeof(float);
+    const int y0 = blockIdx.y * Cfg::TH, x0 = blockIdx.x * Cfg::TW;
+    const int gy0 = y0 - Cfg::AH, gx0 = x0 - Cfg::P;
+    if ((tma::smem_addr(land) & 127u) != 0) {  // a TMA box needs a 128-byte aligned destination
+        if (threadIdx.x == 0) atomicAdd(&g_wait_timeouts, 1u);
+        return;
+    }
+    if (threadIdx.x == 0) tma::mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x < 32)
+        rows_issue<T, SH, SW, CLAMP>(&tmap, (long long)h * w * blockIdx.z, h, w, gy0, gx0, land, s_shift, &bar);
+    stage_filter<KH, KW, KWP, NT>(k, s_k);
+    const bool ok = __syncthreads_and(tma::mbar_wait(&bar, 0, tma::kLoadWaitNs));
+    if (!ok) {  // the copies did not complete in time: report, let them land, skip the tile
+        if (threadIdx.x == 0) atomicAdd(&g_wait_timeouts, 1u);
+        tma::mbar_wait(&bar, 0, tma::kLoadWaitNs);
+        return;
+    }
+    T *dst = out + (size_t)h * (size_t)w * blockIdx.z;
+    if constexpr (DR::INPLACE) {
+        rows_realign_inplace<T, SH, SW, NT, CLAMP>(land, s_shift, w, gx0);
+        __syncthreads();
+        direct_compute<T, KH, KW, TX, TY, R, G, T, true, 1, C, RS::LP>(land, s_k, dst, h, w, false, y0, x0);
+    } else if constexpr (HALFW) {
+        rows_realign<T, T, SH, SW, NT, CLAMP>(land, s_shift, s16, w, gx0);
+        __syncthreads();
+        direct_compute<T, KH, KW, TX, TY, R, G, T, true, 1, C>(s16, s_k, dst, h, w, false, y0, x0);
+    } else {
+        rows_realign<T, float, SH, SW, NT, CLAMP>(land, s_shift, s_in, w, gx0);
+        __syncthreads();
+        direct_compute<T, KH, KW, TX, TY, R, G, float, true, 1, C>(s_in, s_k, dst, h, w, false, y0, x0);
+    }
+}
+
 // ------------------------------------------------------------ generic kernel
 // Any kh, kw: one output per thread, reads straight from global memory with
 // clamped indices (L1/L2 serve the reuse).  Same per-pixel order as above.
@@ -444,7 +510,9 @@ __global__ void __launch_bounds__(256)
 // ------------------------------------------------------------------ launch
 template <typename Kern>
 cudaError_t set_smem(Kern kern, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+    // without the attribute, static and dynamic shared memory share 48 KB;
+    // the kernels' static part stays under 1 KB
+    if (bytes + 1024 <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -479,6 +547,47 @@ bool image_tensor_map(CUtensorMap *m, const T *base, int c, int h, int w, int bw
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 1-D tensor map over the n elements of an image (box of `box` elements);
+// false if it cannot be made: base not 16-byte aligned, or n too large for
+// the 32-bit box coordinates.
+template <typename T>
+bool flat_tensor_map(CUtensorMap *m, const T *base, long long n, int box) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || n <= 0 || n > 0x7fffff00ll || ((uintptr_t)base & 15u) != 0) return false;
+    const cuuint64_t dims[1] = {(cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)n * sizeof(T)};  // unused for one dimension
+    const cuuint32_t boxd[1] = {(cuuint32_t)box};
+    const cuuint32_t elem[1] = {1u};
+    return enc(m, sizeof(T) == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 1,
+               const_cast<T *>(base), dims, strides, boxd, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The row-staged launch for planar images whose rows are not 16-byte aligned
+// (clamp or zero border); false, with nothing launched, where it does not
+// apply.
+template <typename T, int K, int TX, int TY, int R, int G, int MINB, bool HALFW, int C = 4>
+bool try_direct_rows(int c, int h, int w, const T *in, const float *k, T *out, int border, cudaStream_t s,
+                     cudaError_t *err) {
+    using DR = DirectRows<T, K, K, TX, TY, R, G, MINB, HALFW, true, C>;
+    using Cfg = typename DR::Cfg;
+    CUtensorMap tmap;
+    const long long n = (long long)c * h * w;
+    if ((border != 0 && border != 1) || n < DR::RS::LB || !flat_tensor_map<T>(&tmap, in, n, DR::RS::LB))
+        return false;
+    auto kern = border == 0 ? conv2d_direct_rows_kernel<T, K, K, TX, TY, R, G, MINB, HALFW, true, C>
+                            : conv2d_direct_rows_kernel<T, K, K, TX, TY, R, G, MINB, HALFW, false, C>;
+    const size_t smem = DR::smem;
+    *err = set_smem(kern, smem);
+    if (*err == cudaSuccess) {
+        dim3 grid((w + Cfg::TW - 1) / Cfg::TW, (h + Cfg::TH - 1) / Cfg::TH, c);
+        kern<<<grid, Cfg::NT, smem, s>>>(tmap, k, out, h, w);
+        *err = cudaGetLastError();
+    }
+    return true;
+}
+
 // The TMA-staged launch for aligned rows with the clamp or zero border (a box
 // side is at most 256 elements); false, with nothing launched, where it does
 // not apply.
@@ -503,24 +612,41 @@ bool try_direct_tma(int c, int h, int w, const T *in, const float *k, T *out, bo
     return true;
 }
 
-template <typename T, int K, int TX, int TY, int R, int G = 1, int MINB = 1, bool HALFW = false, int CS = 1>
+// Planar rows that are not 16-byte aligned take the row staging on images
+// of at least 2^20 elements (smaller ones are latency-bound, and there the
+// cp.async staging measured faster): binary16 images at every side, FP32 up
+// to side 7 (larger FP32 sides are compute-bound; there it measured the same
+// or slower).
+constexpr long long kRowsMin = 1ll << 20;
+template <typename T, int K>
+constexpr bool rows_pay() {
+    return sizeof(T) == 2 || K <= 7;
+}
+
+template <typename T, int K, int TX, int TY, int R, int G = 1, int MINB = 1, bool HALFW = false, int CS = 1,
+          int C = 4>
 cudaError_t run_direct(int c, int h, int w, const T *in, const float *k, T *out, bool vec_ok,
                        int border, cudaStream_t s) {
-    using Cfg = DirectCfg<K, K, TX, TY, R, G, CS>;
+    using Cfg = DirectCfg<K, K, TX, TY, R, G, CS, C>;
     cudaError_t err = cudaSuccess;
-    if (try_direct_tma<T, K, TX, TY, R, G, MINB, HALFW, CS>(c, h, w, in, k, out, vec_ok, border, s, &err))
+    if (try_direct_tma<T, K, TX, TY, R, G, MINB, HALFW, CS, C>(c, h, w, in, k, out, vec_ok, border, s, &err))
         return err;
+    if constexpr (CS == 1 && rows_pay<T, K>()) {
+        if (!vec_ok && (long long)c * h * w >= kRowsMin &&
+            try_direct_rows<T, K, TX, TY, R, G, MINB, HALFW, C>(c, h, w, in, k, out, border, s, &err))
+            return err;
+    }
     // sides up to 5 (memory-bound): an aligned-row kernel and an adaptive
     // any-row kernel; larger sides: one kernel with vec_ok at run time
     using Kern = void (*)(const T *, const float *, T *, int, int, bool, int);
     Kern kern;
     if constexpr (K <= 5 && CS == 1)
-        kern = border != 0 ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, true, HALFW, 2>
-               : vec_ok    ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 1>
-                           : conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 2>;
+        kern = border != 0 ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, true, HALFW, 2, 1, C>
+               : vec_ok    ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 1, 1, C>
+                           : conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 2, 1, C>;
     else  // interleaved images keep to one kernel per border class (their aligned rows take TMA)
-        kern = border != 0 ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, true, HALFW, 0, CS>
-                           : conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 0, CS>;
+        kern = border != 0 ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, true, HALFW, 0, CS, C>
+                           : conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 0, CS, C>;
     const size_t smem = HALFW ? Cfg::smem_half : Cfg::smem(sizeof(T));
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
@@ -549,24 +675,25 @@ cudaError_t run_sep_generic(int c, int h, int w, const T *in, int kx, const floa
 }
 
 // CS > 1: w is the element width of one interleaved image (pixels * CS), c = 1.
+// CR: columns per row-pass item (SepCfg).
 template <typename T, int K, int TX, int TY, int R, int MINB = 1, bool INPLACE = false, int PAIR = 0, int CS = 1,
-          bool HALFR = false>
+          bool HALFR = false, int CR = 4>
 cudaError_t run_sep(int c, int h, int w, const T *in, const float *gx, const float *gy, T *out,
                     bool vec_ok, int border, cudaStream_t s) {
-    using Cfg = SepCfg<K, K, TX, TY, R, INPLACE, CS, HALFR>;
+    using Cfg = SepCfg<K, K, TX, TY, R, INPLACE, CS, HALFR, CR>;
     using Kern = void (*)(const CUtensorMap, const T *, const float *, const float *, T *, int, int, bool, int);
     Kern kern;
     CUtensorMap tmap = {};
     static_assert(Cfg::SW <= 256 && Cfg::SH <= 256, "a TMA box side is at most 256 elements");
     if (vec_ok && (border == 0 || border == 1) && image_tensor_map<T>(&tmap, in, c, h, w, Cfg::SW, Cfg::SH)) {
-        kern = conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 3, CS, HALFR>;  // TMA staging
+        kern = conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 3, CS, HALFR, CR>;  // TMA staging
     } else if constexpr (K <= 5 && CS == 1) {  // as for the direct kernels
-        kern = border != 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 2, 1, HALFR>
-               : vec_ok    ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 1, 1, HALFR>
-                           : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 2, 1, HALFR>;
+        kern = border != 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 2, 1, HALFR, CR>
+               : vec_ok    ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 1, 1, HALFR, CR>
+                           : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 2, 1, HALFR, CR>;
     } else {
-        kern = border != 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 0, CS, HALFR>
-                           : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 0, CS, HALFR>;
+        kern = border != 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 0, CS, HALFR, CR>
+                           : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 0, CS, HALFR, CR>;
     }
     const size_t smem = Cfg::smem(sizeof(T));
     cudaError_t e = set_smem(kern, smem);

@@ -5,6 +5,7 @@
 #pragma once
 
 #include "internal.cuh"
+#include "tma.cuh"
 
 namespace pencil {
 namespace tile {
@@ -279,6 +280,138 @@ __device__ __forceinline__ void stage_tile(const T *__restrict__ src, int h, int
     stage_finish<T, SH, SW, NT>(s, s16);
 }
 
+// ------------------------------------------------------------ row staging
+// TMA staging for images whose rows are not 16-byte aligned (a TMA box must
+// start on a 16-byte boundary, and a 2-D tensor map needs a row pitch that
+// is a multiple of 16 bytes).  The image is seen as one flat array (a 1-D
+// tensor map over all its elements) and each staged row is one box of
+// LB = SW + V elements, started at the 16-byte boundary at or below the
+// row's first staged element: the row lands in a landing row of LP elements
+// shifted by its misalignment s (0 <= s < V), which is recorded.  Rows
+// outside the image take the edge row (clamp) or none (zero border).  The
+// realign pass then moves each landing row into its place in the tile,
+// taking the clamp (or zero) for columns outside the image: the tile always
+// overlaps the image, so the edge column a clamp reads lies inside the box.
+// Elements past either end of the array read as zeros, so no copy leaves the
+// allocation.  Planar images (CS = 1) only.
+template <typename T, int SH, int SW>
+struct RowStage {
+    static constexpr int V = 16 / (int)sizeof(T);                 // elements per 16 bytes
+    static constexpr int LB = SW + V;                             // box elements
+    static constexpr int LP = round_up(LB, 128 / (int)sizeof(T));  // landing row pitch: 128-byte rows
+    static constexpr size_t bytes = sizeof(T) * (size_t)SH * LP;
+    static_assert(LB <= 256, "a TMA box side is at most 256 elements");
+    static_assert(sizeof(T) * (size_t)SH * LB < (1u << 20), "an mbarrier counts fewer than 2^20 bytes");
+};
+
+// Issue the boxes of the SH staged rows of a tile whose top-left staged
+// element is (gy0, gx0) in plane `plane` (its first flat element), all
+// completing `bar`; shift[r] gets row r's misalignment, or -1 for a zero
+// row.  Called by the 32 threads of one warp, after `bar` is initialised and
+// visible.
+template <typename T, int SH, int SW, bool CLAMP>
+__device__ __forceinline__ void rows_issue(const CUtensorMap *map, long long plane, int h, int w, int gy0,
+                                           int gx0, T *__restrict__ land, int *__restrict__ shift,
+                                           uint64_t *bar) {
+    using RS = RowStage<T, SH, SW>;
+    const int lane = threadIdx.x & 31;
+    const int lo = CLAMP ? 0 : max(0, -gy0), hi = CLAMP ? SH : min(SH, h - gy0);
+    const int n = max(0, hi - lo);  // boxes issued
+    if (lane == 0) tma::mbar_arrive_expect_tx(bar, (unsigned)(n * RS::LB * (int)sizeof(T)));
+    __syncwarp();
+    for (int r = lane; r < SH; r += 32) {
+        int gr = gy0 + r;
+        if (CLAMP) {
+            gr = clampi(gr, 0, h - 1);
+        } else if (gr < 0 || gr >= h) {
+            shift[r] = -1;
+            continue;
+        }
+        const long long f = plane + (long long)gr * w + gx0;  // flat index of staged column 0
+        const int s = (int)(((f % RS::V) + RS::V) % RS::V);   // floor remainder (f may be negative)
+        shift[r] = s;
+        tma::load_1d(land + r * RS::LP, map, (int)(f - s), bar);
+    }
+}
+
+template <typename D, typename T>
+__device__ __forceinline__ D row_elem(T v) {
+    if constexpr (sizeof(D) == sizeof(T)) return v;
+    else return __half2float(v);
+}
+
+// After the boxes have landed and a barrier: every landing row into its
+// place in the tile (row stride SW), as D (float: widened; T: as stored).
+// One warp per row, lanes on consecutive columns (conflict-free).
+template <typename T, typename D, int SH, int SW, int NT, bool CLAMP>
+__device__ __forceinline__ void rows_realign(const T *__restrict__ land, const int *__restrict__ shift,
+                                             D *__restrict__ tile, int w, int gx0) {
+    using RS = RowStage<T, SH, SW>;
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const bool inside = gx0 >= 0 && gx0 + SW <= w;  // no staged column outside the image
+    for (int r = wp; r < SH; r += NW) {
+        const int s = shift[r];
+        D *dr = tile + r * SW;
+        if (s < 0) {
+#pragma unroll
+            for (int t = lane; t < SW; t += 32) dr[t] = static_cast<D>(0.0f);
+            continue;
+        }
+        const T *lr = land + r * RS::LP + s;  // lr[t]: the element of staged column t
+        if (inside) {
+#pragma unroll
+            for (int t = lane; t < SW; t += 32) dr[t] = row_elem<D>(lr[t]);
+        } else {
+#pragma unroll
+            for (int t = lane; t < SW; t += 32) {
+                const int c = gx0 + t;
+                if (CLAMP)
+                    dr[t] = row_elem<D>(lr[clampi(c, 0, w - 1) - gx0]);
+                else
+                    dr[t] = c >= 0 && c < w ? row_elem<D>(lr[t]) : static_cast<D>(0.0f);
+            }
+        }
+    }
+}
+
+// The same in place: each landing row shifted to its start, so the tile is
+// the landing area with row stride LP.  A warp reads its whole row into
+// registers before writing it back.
+template <typename T, int SH, int SW, int NT, bool CLAMP>
+__device__ __forceinline__ void rows_realign_inplace(T *__restrict__ land, const int *__restrict__ shift, int w,
+                                                     int gx0) {
+    using RS = RowStage<T, SH, SW>;
+    constexpr int NW = NT / 32, NR = (SW + 31) / 32;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const bool inside = gx0 >= 0 && gx0 + SW <= w;
+    for (int r = wp; r < SH; r += NW) {
+        const int s = shift[r];
+        T *lr = land + r * RS::LP;
+        T v[NR];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            const int t = lane + 32 * j;
+            v[j] = static_cast<T>(0.0f);
+            if (t < SW && s >= 0) {
+                const int c = gx0 + t;
+                if (inside)
+                    v[j] = lr[s + t];
+                else if (CLAMP)
+                    v[j] = lr[s + clampi(c, 0, w - 1) - gx0];
+                else if (c >= 0 && c < w)
+                    v[j] = lr[s + t];
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            const int t = lane + 32 * j;
+            if (t < SW) lr[t] = v[j];
+        }
+    }
+}
+
 // Write a thread's R x 4 block (rows y, cols x..x+3), bounds-checked.  Rows
 // that are not 16-byte aligned: the widest stores each address allows
 // (ADAPT), or scalar stores.
@@ -421,13 +554,14 @@ __device__ __forceinline__ void direct_accumulate(const S *__restrict__ srow_,
 // Compute and store one TH x TW output tile with origin (y0, x0) from a
 // staged tile s_in (see stage_tile; FP32, or the binary16 staging area read
 // directly) and staged filter rows s_k.
+// PITCH: the staged tile's row stride, when it is wider than SW.
 template <typename T, int KH, int KW, int TX, int TY, int R, int G, typename S = float, bool ADAPT = true,
-          int CS = 1, int C_ = 4>
+          int CS = 1, int C_ = 4, int PITCH = 0>
 __device__ __forceinline__ void direct_compute(const S *__restrict__ s_in,
                                                const float *__restrict__ s_k, T *__restrict__ dst,
                                                int h, int w, bool vec_ok, int y0, int x0) {
     using Cfg = DirectCfg<KH, KW, TX, TY, R, G, CS, C_>;
-    constexpr int C = Cfg::C, P = Cfg::P, SW = Cfg::SW, KWP = Cfg::KWP, GS = Cfg::GS;
+    constexpr int C = Cfg::C, P = Cfg::P, SW = PITCH ? PITCH : Cfg::SW, KWP = Cfg::KWP, GS = Cfg::GS;
     constexpr int B0 = P - Cfg::AWE;  // x index of tap 0 for column 0
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     float acc[R][G * C];

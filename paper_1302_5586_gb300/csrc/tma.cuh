@@ -69,6 +69,18 @@ __device__ __forceinline__ void load_3d(void *dst, const CUtensorMap *map, int x
         : "memory");
 }
 
+// Copy the box of the 1-D tensor map starting at element x into shared
+// memory at dst, completing `bar`'s transaction count.  Same rules as
+// load_3d: x * element size a multiple of 16 bytes, dst 128-byte aligned,
+// elements outside the tensor read as zeros.
+__device__ __forceinline__ void load_1d(void *dst, const CUtensorMap *map, int x, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.1d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2}], "
+        "[%3];\n" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(smem_addr(bar))
+        : "memory");
+}
+
 // Bound of a wait on one tile load: far beyond any load's latency (a few
 // microseconds), short enough that a lost completion ends the kernel.
 constexpr uint64_t kLoadWaitNs = 1000000000ull;

@@ -65,6 +65,31 @@ def test_specialised_and_generic_kernels_agree_bitwise(K, shape):
     np.testing.assert_array_equal(a16.view(np.uint16), b16.view(np.uint16))
 
 
+# Planar images of at least 2^20 elements whose rows are not 16-byte aligned
+# (w % 4 = 1, 2, 3) take the row-staged TMA kernels (binary16 at every side,
+# FP32 up to side 7); the generic kernel shares the per-pixel order, so the
+# two agree bit for bit, and the oracle checks both.
+ROW_SHAPES = [(1, 1031, 1029), (2, 767, 1366), (1, 1100, 1023)]
+
+
+@pytest.mark.parametrize("K", [1, 3, 5, 7, 9, 11, 13, 15])
+@pytest.mark.parametrize("border", ["clamp", "zero"])
+@pytest.mark.parametrize("shape", ROW_SHAPES)
+def test_row_staged_unaligned_rows(K, border, shape):
+    c, h, w = shape
+    assert c * h * w >= 1 << 20 and w % 4 != 0
+    img = synth.image_f32(900 + K + w, c, h, w)
+    k = synth.filter_f32(910 + K, K, K)
+    m = pg.PENCIL_BORDER(pg.BORDER_MODES[border])
+    for dt, img_t, tol, view in ((pg.PENCIL_F32, img, F32_TOL, np.uint32),
+                                 (pg.PENCIL_F16, synth.to_f16(img), F16_TOL, np.uint16)):
+        a = run_conv(img_t, k, dt, m).cpu().numpy()
+        b = run_conv(img_t, k, dt, m | pg.PENCIL_CONV_GENERIC).cpu().numpy()
+        np.testing.assert_array_equal(a.view(view), b.view(view))
+        ref, bound = oracle.conv2d(img_t, k, border=border)
+        assert_within(a, ref, bound, tol, f"{border} K={K} {shape} dtype={dt}")
+
+
 @pytest.mark.parametrize("kh,kw", [(4, 6), (2, 1), (1, 9), (31, 3), (17, 17), (3, 5)])
 def test_generic_sizes_match_oracle(kh, kw):
     img = synth.image_f32(77, 2, 45, 70)
