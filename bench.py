@@ -360,8 +360,15 @@ def measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g, serve_seconds=SE
                                                                      pg.PENCIL_F16, 0, sraw), 10)
     per16["gauss15-sep"] = _pass_entry(ms, 4, 0, hbm)
     o16s.append(o16)
+    # the 15x15 pass again on the tensor cores (PENCIL_CONV_TENSOR: within the
+    # binary16 tolerance, not the same bits); its output is checked as well
+    o16t = torch.empty_like(d16)
+    ms = _time_stream(torch, stream, lambda: pg.pencil_conv2d_ex(C, H, W, d16, 15, 15, d_ks[-1], o16t, pg.PENCIL_F16,
+                                                                 pg.PENCIL_CONV_TENSOR, sraw), 10)
+    per16["15x15-tensor"] = _pass_entry(ms, 4, 2 * 15 * 15, hbm)
     out["passes_f16"] = per16
     keep["f16"] = (d16, o16s)
+    keep["f16_tensor"] = o16t
     # Jacobi 8192^2, 100 sweeps, residual after every 10 sweeps
     n = 8192
     u0h = synth.jacobi_init_f32(synth.SEEDS["jacobi8192"], n, n)
@@ -845,6 +852,15 @@ def cpu_baseline(torch, img, ks, g, d_out=None, keep=None, budget_s=15.0):
             got = o16[:, r16:r16 + rows16, :].cpu().numpy()
             f16[name] = max(_ratio_max(got, want[:, a:a + rows16], bound[:, a:a + rows16]),
                             _ratio_max(_gather(o16, pts), pw, pb))
+        o16t = keep.get("f16_tensor")
+        if o16t is not None:  # the tensor-core 15x15 pass, same bound
+            a = DIRECT_K[-1] // 2
+            sub = x16[:, r16 - a:r16 + rows16 + a, :]
+            want, bound = oracle.conv2d(sub, ks[-1])
+            pw, pb = oracle.conv2d_points(x16, ks[-1], pts)
+            got = o16t[:, r16:r16 + rows16, :].cpu().numpy()
+            f16["15x15-tensor"] = max(_ratio_max(got, want[:, a:a + rows16], bound[:, a:a + rows16]),
+                                      _ratio_max(_gather(o16t, pts), pw, pb))
         prec["conv_f16_err_over_bound"] = {k: float(f"{v:.3g}") for k, v in f16.items()}
         worst = max(worst, max(f16.values()) / TOL_F16)
     if keep.get("plain512"):
@@ -934,8 +950,9 @@ def run_case(name, reps):
 
     dev = torch.device("cuda", 0)
     if name.startswith("conv"):
-        f16 = name.endswith("h")
-        K = int(name[4:].rstrip("h").split("-")[0])
+        tensor = name.endswith("t")  # binary16 on the tensor cores
+        f16 = name.endswith("h") or tensor
+        K = int(name[4:].rstrip("ht").split("-")[0])
         c, h, w = 2, 4096, 4096
         img = torch.from_numpy(synth.image_f32(1, c, h, w)).to(dev)
         if f16:  # binary16 storage: twice the pixels, so the image is still larger than L2
@@ -944,7 +961,8 @@ def run_case(name, reps):
         k = torch.from_numpy(synth.filter_f32(2, K, K)).to(dev)
         out = torch.empty_like(img)
         for _ in range(reps):
-            pg.pencil_conv2d_ex(c, h, w, img, K, K, k, out, pg.PENCIL_F16 if f16 else pg.PENCIL_F32)
+            pg.pencil_conv2d_ex(c, h, w, img, K, K, k, out, pg.PENCIL_F16 if f16 else pg.PENCIL_F32,
+                                pg.PENCIL_CONV_TENSOR if tensor else 0)
     elif name in ("sep15", "sep15h"):
         f16 = name.endswith("h")
         c, h, w = (4 if f16 else 2), 4096, 4096  # binary16: twice the pixels, still larger than L2
@@ -1012,7 +1030,8 @@ def run_case(name, reps):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default=None,
-                    help="profile one kernel on a reduced workload: conv3, conv7, conv15, conv3h (binary16), sep15, sep15h "
+                    help="profile one kernel on a reduced workload: conv3, conv7, conv15, conv3h (binary16), conv15t "
+                         "(binary16 on the tensor cores), sep15, sep15h "
                          "(binary16), batch, jacobi, jacobi-tN (N sweeps per pass), op2-ordered, op2-atomic, "
                          "chain3, chain5, chain7, cj3, cj5, cj7 (filter then 10 Jacobi sweeps, fused)")
     ap.add_argument("--reps", type=int, default=3)

@@ -84,6 +84,19 @@ enum { PENCIL_F32 = 0, PENCIL_F16 = 1 };
  * other channel counts a generic kernel.  w*c must fit an int
  * (PENCIL_ERR_UNSUPPORTED otherwise). */
 #define PENCIL_LAYOUT_HWC 4
+/* pencil_conv2d_ex flag: binary16 images on the tensor cores.  For planar
+ * binary16 images with odd square filters of side 9..15 (where it measured
+ * faster than the CUDA cores), rows 16-byte aligned (w a multiple of 8, in and out 16-byte aligned) and the clamp or
+ * zero border, each filter row becomes a banded-matrix product on the
+ * 5th-generation tensor cores: the weights, scaled by a power of two, are
+ * split into two binary16 terms each (about 22 significant bits), products
+ * accumulate in FP32 in tensor memory, and the result is rounded to binary16
+ * once (Sec. 3.1: precision traded against speed, here within the binary16
+ * tolerance -- |out - exact| <= 2^-10 * sum |k| |in| -- but not the same
+ * bits as the CUDA-core kernels, whose summation order differs).  Ignored
+ * for FP32 images, with PENCIL_CONV_GENERIC or PENCIL_LAYOUT_HWC, and where
+ * the conditions above do not hold (the CUDA-core kernels run). */
+#define PENCIL_CONV_TENSOR 16
 
 /* Border modes for the _ex conv2d calls, passed in flags as PENCIL_BORDER(m);
  * index i of an axis of length n reads (the plain calls always clamp):
@@ -127,8 +140,8 @@ int pencil_conv2d(int h, int w, PENCIL_ARR2(const float, in, h, w), int kh, int 
 /* Stream-ordered, c planar channels, storage dtype PENCIL_F32 or PENCIL_F16
  * (binary16 images; FP32 accumulation; binary16 results rounded to nearest
  * even).  in, out: c*h*w elements of dtype, device memory; k: kh*kw FP32,
- * device memory.  flags: PENCIL_CONV_GENERIC, PENCIL_LAYOUT_HWC and/or one
- * PENCIL_BORDER(m).
+ * device memory.  flags: PENCIL_CONV_GENERIC, PENCIL_LAYOUT_HWC,
+ * PENCIL_CONV_TENSOR and/or one PENCIL_BORDER(m).
  * Speed, not results, depends on alignment: images whose rows are 16-byte
  * aligned (w a multiple of 4 for FP32, of 8 for binary16, and in and out
  * 16-byte aligned) with the clamp or zero border load their tiles with the

@@ -21,6 +21,7 @@ PENCIL_F32 = 0
 PENCIL_F16 = 1
 PENCIL_CONV_GENERIC = 1
 PENCIL_LAYOUT_HWC = 4  # channels interleaved [h][w][c] instead of planar [c][h][w]
+PENCIL_CONV_TENSOR = 16  # binary16 images on the tensor cores (within the binary16 tolerance, not the same bits)
 PENCIL_BORDER_CLAMP, PENCIL_BORDER_ZERO, PENCIL_BORDER_REFLECT, PENCIL_BORDER_MIRROR, PENCIL_BORDER_WRAP = range(5)
 BORDER_MODES = {"clamp": 0, "zero": 1, "reflect": 2, "mirror": 3, "wrap": 4}
 

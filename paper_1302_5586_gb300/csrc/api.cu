@@ -220,13 +220,14 @@ int pencil_last_cuda_error(void) { return g_last_cuda; }
 
 int pencil_device_status(void) {
     unsigned n = 0, m = 0;
-    unsigned q = 0, r = 0;
+    unsigned q = 0, r = 0, t = 0;
     cudaError_t e = wait_timeouts(&n, true);
     if (e == cudaSuccess) e = wait_timeouts_hwc(&m, true);
     if (e == cudaSuccess) e = wait_timeouts_cj(&q, true);
     if (e == cudaSuccess) e = wait_timeouts_chain(&r, true);
+    if (e == cudaSuccess) e = wait_timeouts_tc(&t, true);
     if (e != cudaSuccess) return cuda_fail(e);
-    return n + m + q + r ? PENCIL_ERR_TIMEOUT : PENCIL_OK;
+    return n + m + q + r + t ? PENCIL_ERR_TIMEOUT : PENCIL_OK;
 }
 
 int pencil_selftest_wait_timeout(unsigned limit_us, int *completed) {
@@ -250,7 +251,8 @@ int check_layout(int c, int w, int flags) {
 int pencil_conv2d_ex(int c, int h, int w, const void *in, int kh, int kw, const float *k, void *out,
                      int dtype, int flags, void *stream) {
     const int border = (flags >> 8) & 0xF;
-    if (c <= 0 || kh <= 0 || kw <= 0 || (flags & ~(PENCIL_CONV_GENERIC | PENCIL_LAYOUT_HWC | 0xF00)) != 0 ||
+    if (c <= 0 || kh <= 0 || kw <= 0 ||
+        (flags & ~(PENCIL_CONV_GENERIC | PENCIL_LAYOUT_HWC | PENCIL_CONV_TENSOR | 0xF00)) != 0 ||
         border > PENCIL_BORDER_WRAP)
         return PENCIL_ERR_ARG;
     if (dtype != PENCIL_F32 && dtype != PENCIL_F16) return PENCIL_ERR_ARG;
@@ -267,7 +269,14 @@ int pencil_conv2d_ex(int c, int h, int w, const void *in, int kh, int kw, const 
     const cudaStream_t s = (cudaStream_t)stream;
     const bool generic = flags & PENCIL_CONV_GENERIC;
     cudaError_t e;
-    if ((flags & PENCIL_LAYOUT_HWC) && c > 1)  // one channel interleaved is the planar layout
+    const bool hwc = (flags & PENCIL_LAYOUT_HWC) && c > 1;  // one channel interleaved is the planar layout
+    if ((flags & PENCIL_CONV_TENSOR) && dtype == PENCIL_F16 && !generic && !hwc && kh == kw) {
+        bool done = false;
+        e = launch_conv2d_tc(c, h, w, in, kh, k, out, border, s, &done);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (done) return PENCIL_OK;
+    }
+    if (hwc)
         e = generic ? launch_conv2d_hwc_generic(dtype, c, h, w, in, kh, kw, k, out, s, border)
                     : launch_conv2d_hwc(dtype, c, h, w, in, kh, kw, k, out, s, border);
     else

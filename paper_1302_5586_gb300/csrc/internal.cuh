@@ -50,6 +50,12 @@ __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wa
 // border: 0 clamp-to-edge, 1 zero, 2 reflect, 3 mirror, 4 wrap.
 cudaError_t launch_conv2d(int dtype, int c, int h, int w, const void *in, int kh, int kw,
                           const float *k, void *out, cudaStream_t s, int border = 0);
+// Binary16 on the tensor cores (conv_tc.cu): queued only where it applies
+// (odd square side 9..15, rows and pointers 16-byte aligned, clamp or zero
+// border); *done says whether it was.
+cudaError_t launch_conv2d_tc(int c, int h, int w, const void *in, int ks, const float *k, void *out, int border,
+                             cudaStream_t s, bool *done);
+cudaError_t wait_timeouts_tc(unsigned *n, bool clear);
 // Force the generic (any-size) kernel; used by tests of the fixed-order rule.
 // cs = 0: c planar channels; cs = c > 1: one interleaved [h][w][c] image.
 cudaError_t launch_conv2d_generic(int dtype, int c, int h, int w, const void *in, int kh, int kw,

@@ -106,6 +106,7 @@ def test_conv2d_argument_errors_before_cuda(lib, args, status):
 def test_ex_argument_errors_before_cuda(lib):
     assert lib.pencil_conv2d_ex(1, 4, 4, 1, 3, 3, 2, 3, 7, 0, None) == -1   # bad dtype
     assert lib.pencil_conv2d_ex(1, 4, 4, 1, 3, 3, 2, 3, 0, 8, None) == -1   # unknown flag
+    assert lib.pencil_conv2d_ex(1, 4, 4, 1, 3, 3, 2, 3, 0, 32, None) == -1  # unknown flag
     # interleaved rows of w*c elements must fit an int
     assert lib.pencil_conv2d_ex(3, 1, 1 << 30, 1, 3, 3, 2, 3, 0, pg.PENCIL_LAYOUT_HWC, None) == -8
     assert lib.pencil_conv2d_sep_ex(3, 1, 1 << 30, 1, 3, 2, 3, 3, 5, 0, pg.PENCIL_LAYOUT_HWC, None) == -8
