@@ -85,7 +85,7 @@ enum { PENCIL_F32 = 0, PENCIL_F16 = 1 };
  * (PENCIL_ERR_UNSUPPORTED otherwise). */
 #define PENCIL_LAYOUT_HWC 4
 /* pencil_conv2d_ex flag: binary16 images on the tensor cores.  For planar
- * binary16 images with odd square filters of side 9..15 (where it measured
+ * binary16 images with odd square filters of side 7..15 (where it measured
  * faster than the CUDA cores), rows 16-byte aligned (w a multiple of 8, in and out 16-byte aligned) and the clamp or
  * zero border, each filter row becomes a banded-matrix product on the
  * 5th-generation tensor cores: the weights, scaled by a power of two, are

@@ -51,7 +51,7 @@ __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wa
 cudaError_t launch_conv2d(int dtype, int c, int h, int w, const void *in, int kh, int kw,
                           const float *k, void *out, cudaStream_t s, int border = 0);
 // Binary16 on the tensor cores (conv_tc.cu): queued only where it applies
-// (odd square side 9..15, rows and pointers 16-byte aligned, clamp or zero
+// (odd square side 7..15, rows and pointers 16-byte aligned, clamp or zero
 // border); *done says whether it was.
 cudaError_t launch_conv2d_tc(int c, int h, int w, const void *in, int ks, const float *k, void *out, int border,
                              cudaStream_t s, bool *done);
