@@ -11,32 +11,35 @@
 // are zeros.  The weights are scaled by a power of two that puts the largest
 // in [0.5, 1), and each scaled weight is split into two binary16 terms (hi,
 // its rounding; lo, the rounding of the rest), so a weight keeps about 22
-// significant bits.  The two banded matrices of a row are stacked along N:
-// one MMA of M = 128, N = 32 (16 hi + 16 lo columns), K = 16 reads each slice
-// of the input once for both terms (shared-memory operand reads, not the
-// tensor pipe, bound this kernel), two per filter row and block.  Both sums
-// accumulate in FP32 in tensor memory (TMEM); the epilogue adds them, undoes
-// the scale and rounds to binary16 once.  The result stays within the
+// significant bits.  Shared-memory operand reads, not the tensor pipe, bound
+// the MMAs, so each 16-column slice of the input is read once per filter row:
+// one MMA of M = 128, N = 64, K = 16 multiplies it by the hi and lo terms of
+// the first half of the band (for the block at that slice) and of the second
+// half (for the block to its left).  The accumulator is cleared once per tile
+// (an MMA with a zero B operand) and every product accumulates in FP32 in
+// tensor memory (TMEM); the epilogue adds the hi and lo sums, undoes the
+// scale and rounds to binary16 once.  The result stays within the
 // binary16 tolerance of the FP64 correlation but is not the same bits as the
 // CUDA-core kernels (a different summation order).
 //
 // The kernel is persistent and warp-specialised, one CTA per SM looping
-// over 128 x 128 output tiles (eight 16-column blocks, 32 TMEM columns each:
-// hi sums, then lo sums).  The CTA builds the banded matrices once (kh rows x
-// 32 x 32 binary16, hi rows then lo rows, from the filter staged in shared
-// memory).  Warp 0 streams input tiles by TMA into two stages: a tile's
-// (128 + kh - 1) rows x 144 columns, starting 8 columns left of it, arrive as
-// 18 boxes of 8 columns x all rows, each landing as consecutive 16-byte rows
+// over 128 x 96 output tiles (six 16-column blocks, 32 TMEM columns each: hi
+// sums, then lo sums; block b at column 32 (6 - b), so slice c's 64 columns
+// start at 32 (6 - c)).  The CTA builds the banded matrices once (kh B
+// operands of 64 x 16 binary16, from the filter staged in shared memory).
+// Warp 0 streams input tiles by TMA into four stages: a tile's
+// (128 + kh - 1) rows x 112 columns, starting 8 columns left of it, arrive as
+// 14 boxes of 8 columns x all rows, each landing as consecutive 16-byte rows
 // -- the no-swizzle K-major layout of core matrices (8 rows x 16 bytes) -- so
 // the A operand of filter row a is the same data a rows further down: its
 // descriptor start moves by 16 a bytes.  Warp 1 waits for a stage, rebuilds
-// the clamp on edge tiles, and issues the kh x 8 x 2 MMAs of the tile into
+// the clamp on edge tiles, and issues the 1 + kh x 7 MMAs of the tile into
 // one of two TMEM accumulators (2 x 256 columns); its commits free the stage
 // and hand the accumulator on.  Warps 2-9 read the other accumulator (warp w:
 // TMEM lanes 32 (w % 4) .. + 31, its output rows), add the two sums, undo the
-// scale, round and store (eight warps, two per lane quarter, each with two
-// TMEM loads in flight), and hand it back -- so loads, MMAs and stores of
-// neighbouring tiles overlap.  Every wait is bounded; a role that runs out
+// scale, round and store (eight warps, two per lane quarter, each with the
+// TMEM loads of its three blocks in flight), and hand it back -- so loads,
+// MMAs and stores of neighbouring tiles overlap.  Every wait is bounded; a role that runs out
 // stops issuing, records a timeout and lets what it has in flight finish
 // before the CTA frees its TMEM.
 #include "conv_kernels.cuh"
@@ -46,13 +49,16 @@ namespace pencil {
 namespace {
 
 constexpr int kTcM = 128;                      // output rows per tile (the MMA's M)
-constexpr int kTcBlocks = 8;                   // 16-column blocks per tile
+constexpr int kTcBlocks = 6;                   // 16-column blocks per tile
 constexpr int kTcW = 16 * kTcBlocks;           // output columns per tile
-constexpr int kTcChunks = 2 * kTcBlocks + 2;   // staged 8-column chunks (144 columns)
+constexpr int kTcSlices = kTcBlocks + 1;       // 16-column input slices (112 staged columns)
+constexpr int kTcChunks = 2 * kTcSlices;       // staged 8-column chunks
 constexpr int kTcStoreWarps = 8;               // two per TMEM lane quarter, four blocks each
 constexpr int kTcThreads = 32 * (2 + kTcStoreWarps);  // warp 0 loads, warp 1 MMAs, warps 2-9 store
 constexpr int kTcStages = 4;                   // input tiles in flight per SM
-constexpr unsigned kTcAccCols = 32 * kTcBlocks;  // one accumulator: per block 16 hi + 16 lo sums
+// one accumulator: block b's 16 hi + 16 lo sums at columns 32 (blocks - b),
+// plus the two 32-column ends that the first and last slice also write
+constexpr unsigned kTcAccCols = 32 * (kTcBlocks + 2);
 constexpr unsigned kTcTmemCols = 2 * kTcAccCols;
 
 template <int K>
@@ -61,8 +67,9 @@ struct TcCfg {
     static constexpr int SH = kTcM + K - 1;                 // staged rows
     static constexpr int CHB = round_up(SH * 16, 128);      // bytes per staged chunk (TMA destinations 128-byte aligned)
     static constexpr int A_BYTES = kTcChunks * CHB;         // one stage
-    static constexpr int B_BYTES = K * 2048;                // banded matrices: K rows x 32 (hi, lo) x 32 binary16
-    static constexpr size_t smem = kTcStages * (size_t)A_BYTES + B_BYTES;
+    static constexpr int B_BYTES = K * 2048;                // banded matrices: K rows x 64 x 16 binary16
+    static constexpr int Z_BYTES = 256 * 16 * 2;            // zeros: the B operand that clears an accumulator
+    static constexpr size_t smem = kTcStages * (size_t)A_BYTES + B_BYTES + Z_BYTES;
     static constexpr int D = 8 - A;                         // window offset inside the 32 staged columns
     static_assert(15 + D + K - 1 < 32, "a block's window fits two K-steps");
 };
@@ -93,7 +100,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __shared__ volatile int s_abort;
     __shared__ float s_max[kTcThreads / 32];
     __shared__ float s_w[K * K];
-    unsigned char *sb = tc_smem + kTcStages * Cfg::A_BYTES;
+    unsigned char *sb = tc_smem + kTcStages * Cfg::A_BYTES, *sz = sb + Cfg::B_BYTES;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if ((tma::smem_addr(tc_smem) & 127u) != 0) {  // TMA destinations need 128-byte alignment
         if (tid == 0) atomicAdd(&g_wait_timeouts, 1u);
@@ -132,18 +139,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     e = max(-126, min(126, e));
     const float scale = ldexpf(1.0f, -e), unscale = ldexpf(1.0f, e);
 
-    // banded matrices: row a at 2a KB; element (n, k) at (k / 8) * 512 +
-    // n * 16 + (k % 8) * 2, hi terms in rows n < 16, lo terms in rows 16 + n;
-    // one 16-byte chunk row of both per item
-    for (int it = tid; it < K * 16 * 4; it += kTcThreads) {
-        const int a = it / 64, n = (it >> 2) & 15, kc = it & 3;
+    // banded matrices, one 64 x 16 B operand per filter row a (at 2a KB),
+    // element (row, k) at (k / 8) * 1024 + row * 16 + (k % 8) * 2: rows
+    // 32 ks + n (hi) and 32 ks + 16 + n (lo) hold T_a[n][16 ks + k], so one
+    // 16-column input slice feeds the first half (ks = 0) of the window of its
+    // own block and the second half (ks = 1) of the block to its left; one
+    // 8-column chunk row of both terms per item
+    for (int it = tid; it < K * 64; it += kTcThreads) {
+        const int a = it >> 6, n = (it >> 2) & 15, ks = (it >> 1) & 1, kc = it & 1;
         uint32_t hi2[4], lo2[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             __half hv[2], lv[2];
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
-                const int b = kc * 8 + 2 * q + t - n - Cfg::D;
+                const int b = 16 * ks + kc * 8 + 2 * q + t - n - Cfg::D;
                 const float v = (b >= 0 && b < K) ? s_w[a * K + b] * scale : 0.0f;
                 hv[t] = __float2half_rn(v);
                 lv[t] = __float2half_rn(v - __half2float(hv[t]));
@@ -151,10 +161,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             hi2[q] = (uint32_t)__half_as_ushort(hv[0]) | ((uint32_t)__half_as_ushort(hv[1]) << 16);
             lo2[q] = (uint32_t)__half_as_ushort(lv[0]) | ((uint32_t)__half_as_ushort(lv[1]) << 16);
         }
-        unsigned char *row = sb + a * 2048 + kc * 512 + n * 16;
+        unsigned char *row = sb + a * 2048 + kc * 1024 + (32 * ks + n) * 16;
         *reinterpret_cast<uint4 *>(row) = make_uint4(hi2[0], hi2[1], hi2[2], hi2[3]);
         *reinterpret_cast<uint4 *>(row + 256) = make_uint4(lo2[0], lo2[1], lo2[2], lo2[3]);
     }
+    for (int i = tid; i < Cfg::Z_BYTES / 16; i += kTcThreads)
+        reinterpret_cast<uint4 *>(sz)[i] = make_uint4(0u, 0u, 0u, 0u);
     umma::fence_proxy_async();  // the banded matrices, written by threads, are read by the MMAs
     umma::fence_before_sync();
     __syncthreads();
@@ -187,8 +199,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         __syncwarp();
     } else if (warp == 1) {
         // ---- MMAs: tile i from stage i % S into accumulator i % 2
-        constexpr uint32_t idesc = umma::idesc_f16_f32(kTcM, 32);
-        const uint64_t b0 = umma::smem_desc(tma::smem_addr(sb), 512, 128);
+        constexpr uint32_t idesc = umma::idesc_f16_f32(kTcM, 64), idesc_z = umma::idesc_f16_f32(kTcM, 256);
+        const uint64_t b0 = umma::smem_desc(tma::smem_addr(sb), 1024, 128);
+        const uint64_t z0 = umma::smem_desc(tma::smem_addr(sz), 4096, 128);
         int issued = 0;
         for (int i = 0; i < nmine; ++i) {
             const int st = i % kTcStages, ab = i & 1;
@@ -239,16 +252,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (lane == 0) {
                 const uint64_t a0 = umma::smem_desc(tma::smem_addr(sa), Cfg::CHB, 128);
                 const unsigned acc = tmem + kTcAccCols * ab;
+                // clear the accumulator (A times a zero B), then every product accumulates:
+                // slice c writes block c's first half and block c - 1's second half
+                umma::mma_f16(acc, a0, z0, idesc_z, false);
 #pragma unroll 1
-                for (int a = 0; a < K; ++a)
+                for (int a = 0; a < K; ++a) {
+                    const uint64_t db = b0 + ((unsigned)(a * 2048) >> 4);
 #pragma unroll
-                    for (int j = 0; j < kTcBlocks; ++j)
-#pragma unroll
-                        for (int ks = 0; ks < 2; ++ks) {
-                            const uint64_t da = a0 + ((unsigned)((2 * j + 2 * ks) * Cfg::CHB + 16 * a) >> 4);
-                            const uint64_t db = b0 + ((unsigned)(a * 2048 + 1024 * ks) >> 4);
-                            umma::mma_f16(acc + 32 * j, da, db, idesc, a > 0 || ks > 0);
-                        }
+                    for (int c = 0; c < kTcSlices; ++c) {
+                        const uint64_t da = a0 + ((unsigned)(2 * c * Cfg::CHB + 16 * a) >> 4);
+                        umma::mma_f16(acc + 32 * (kTcBlocks - c), da, db, idesc, true);
+                    }
+                }
                 umma::commit(&empty[st]);     // the stage may be refilled
                 umma::commit(&acc_full[ab]);  // the accumulator may be read
             }
@@ -262,7 +277,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         __syncwarp();
     } else {
         // ---- stores: accumulator i % 2 of tile i; warp w owns TMEM lanes
-        // 32 (w % 4) .. + 31 (its output rows) and four of the eight blocks
+        // 32 (w % 4) .. + 31 (its output rows) and three of the six blocks
         const int quarter = warp & 3, j0 = ((warp - 2) >> 2) * (kTcBlocks / 2);
         for (int i = 0; i < nmine; ++i) {
             const int st = i & 1;
@@ -280,34 +295,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int row = tl.y0 + 32 * quarter + lane;
             __half *orow = out + ((size_t)tl.plane * h + (size_t)min(row, h - 1)) * (size_t)w;
             const unsigned acc = tmem + kTcAccCols * st + ((unsigned)(32 * quarter) << 16);
-#pragma unroll 1
-            for (int jj = 0; jj < kTcBlocks / 2; jj += 2) {
-                uint32_t r[2][32];  // two blocks: 16 hi sums, then 16 lo sums each
-                umma::ld32_async(acc + 32 * (j0 + jj), r[0]);
-                umma::ld32_async(acc + 32 * (j0 + jj + 1), r[1]);
-                umma::wait_ld();
+            uint32_t r[kTcBlocks / 2][32];  // per block: 16 hi sums, then 16 lo sums
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int col = tl.x0 + 16 * (j0 + jj + u);
-                    if (row >= h || col >= w) continue;
-                    uint32_t p[8];
+            for (int u = 0; u < kTcBlocks / 2; ++u) umma::ld32_async(acc + 32 * (kTcBlocks - (j0 + u)), r[u]);
+            umma::wait_ld();
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float a0 = __uint_as_float(r[u][2 * q]) + __uint_as_float(r[u][16 + 2 * q]);
-                        const float a1 = __uint_as_float(r[u][2 * q + 1]) + __uint_as_float(r[u][17 + 2 * q]);
-                        p[q] = (uint32_t)__half_as_ushort(__float2half_rn(a0 * unscale)) |
-                               ((uint32_t)__half_as_ushort(__float2half_rn(a1 * unscale)) << 16);
-                    }
-                    if (col + 16 <= w) {
-                        uint4 *d = reinterpret_cast<uint4 *>(orow + col);
-                        d[0] = make_uint4(p[0], p[1], p[2], p[3]);
-                        d[1] = make_uint4(p[4], p[5], p[6], p[7]);
-                    } else {
+            for (int u = 0; u < kTcBlocks / 2; ++u) {
+                const int col = tl.x0 + 16 * (j0 + u);
+                if (row >= h || col >= w) continue;
+                uint32_t p[8];
 #pragma unroll
-                        for (int q = 0; q < 16; ++q)
-                            if (col + q < w)
-                                orow[col + q] = __ushort_as_half((unsigned short)(p[q >> 1] >> (16 * (q & 1))));
-                    }
+                for (int q = 0; q < 8; ++q) {
+                    const float a0 = __uint_as_float(r[u][2 * q]) + __uint_as_float(r[u][16 + 2 * q]);
+                    const float a1 = __uint_as_float(r[u][2 * q + 1]) + __uint_as_float(r[u][17 + 2 * q]);
+                    p[q] = (uint32_t)__half_as_ushort(__float2half_rn(a0 * unscale)) |
+                           ((uint32_t)__half_as_ushort(__float2half_rn(a1 * unscale)) << 16);
+                }
+                if (col + 16 <= w) {
+                    uint4 *d = reinterpret_cast<uint4 *>(orow + col);
+                    d[0] = make_uint4(p[0], p[1], p[2], p[3]);
+                    d[1] = make_uint4(p[4], p[5], p[6], p[7]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        if (col + q < w)
+                            orow[col + q] = __ushort_as_half((unsigned short)(p[q >> 1] >> (16 * (q & 1))));
                 }
             }
             umma::fence_before_sync();
@@ -359,11 +371,11 @@ cudaError_t run_tc(int c, int h, int w, const __half *in, const float *k, __half
 
 // Queue the tensor-core correlation if it applies (binary16, odd side 7..15,
 // rows of in and out 16-byte aligned, clamp or zero border); *done says
-// whether it was queued.  On 3 x 8192^2 each filter row costs ~0.033 ms of
-// MMAs (bound by their shared-memory operand reads) on top of ~0.13 ms per
-// launch, about the time the input takes from HBM: 15x15 0.616 ms against
-// 1.542 on the CUDA cores, 9x9 0.422 against 0.642, 7x7 0.358 against 0.396.
-// Sides 3 and 5 stay on the CUDA cores (3x3: 0.225 against 0.163 ms).
+// whether it was queued.  On 3 x 8192^2 each filter row costs ~0.020 ms of
+// MMAs (bound by their shared-memory operand reads) on top of ~0.18 ms per
+// launch: 15x15 0.481 ms against 1.542 on the CUDA cores, 9x9 0.360 against
+// 0.642, 7x7 0.319 against 0.396.  Sides 3 and 5 stay on the CUDA cores,
+// which are faster there (3x3 0.163 ms, about the HBM time).
 cudaError_t launch_conv2d_tc(int c, int h, int w, const void *in, int ks, const float *k, void *out, int border,
                              cudaStream_t s, bool *done) {
     *done = false;
