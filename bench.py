@@ -360,15 +360,20 @@ def measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g, serve_seconds=SE
                                                                      pg.PENCIL_F16, 0, sraw), 10)
     per16["gauss15-sep"] = _pass_entry(ms, 4, 0, hbm)
     o16s.append(o16)
-    # the 15x15 pass again on the tensor cores (PENCIL_CONV_TENSOR: within the
-    # binary16 tolerance, not the same bits); its output is checked as well
-    o16t = torch.empty_like(d16)
-    ms = _time_stream(torch, stream, lambda: pg.pencil_conv2d_ex(C, H, W, d16, 15, 15, d_ks[-1], o16t, pg.PENCIL_F16,
-                                                                 pg.PENCIL_CONV_TENSOR, sraw), 10)
-    per16["15x15-tensor"] = _pass_entry(ms, 4, 2 * 15 * 15, hbm)
+    # the 7x7 and 15x15 passes again on the tensor cores (PENCIL_CONV_TENSOR:
+    # within the binary16 tolerance, not the same bits); outputs checked too
+    o16ts = {}
+    for K, dk in zip(DIRECT_K, d_ks):
+        if K < 7:
+            continue
+        o16t = torch.empty_like(d16)
+        ms = _time_stream(torch, stream, lambda: pg.pencil_conv2d_ex(C, H, W, d16, K, K, dk, o16t, pg.PENCIL_F16,
+                                                                     pg.PENCIL_CONV_TENSOR, sraw), 10)
+        per16[f"{K}x{K}-tensor"] = _pass_entry(ms, 4, 2 * K * K, hbm)
+        o16ts[K] = o16t
     out["passes_f16"] = per16
     keep["f16"] = (d16, o16s)
-    keep["f16_tensor"] = o16t
+    keep["f16_tensor"] = o16ts
     # Jacobi 8192^2, 100 sweeps, residual after every 10 sweeps
     n = 8192
     u0h = synth.jacobi_init_f32(synth.SEEDS["jacobi8192"], n, n)
@@ -852,15 +857,15 @@ def cpu_baseline(torch, img, ks, g, d_out=None, keep=None, budget_s=15.0):
             got = o16[:, r16:r16 + rows16, :].cpu().numpy()
             f16[name] = max(_ratio_max(got, want[:, a:a + rows16], bound[:, a:a + rows16]),
                             _ratio_max(_gather(o16, pts), pw, pb))
-        o16t = keep.get("f16_tensor")
-        if o16t is not None:  # the tensor-core 15x15 pass, same bound
-            a = DIRECT_K[-1] // 2
+        for K, o16t in (keep.get("f16_tensor") or {}).items():  # the tensor-core passes, same bound
+            kk = ks[DIRECT_K.index(K)]
+            a = K // 2
             sub = x16[:, r16 - a:r16 + rows16 + a, :]
-            want, bound = oracle.conv2d(sub, ks[-1])
-            pw, pb = oracle.conv2d_points(x16, ks[-1], pts)
+            want, bound = oracle.conv2d(sub, kk)
+            pw, pb = oracle.conv2d_points(x16, kk, pts)
             got = o16t[:, r16:r16 + rows16, :].cpu().numpy()
-            f16["15x15-tensor"] = max(_ratio_max(got, want[:, a:a + rows16], bound[:, a:a + rows16]),
-                                      _ratio_max(_gather(o16t, pts), pw, pb))
+            f16[f"{K}x{K}-tensor"] = max(_ratio_max(got, want[:, a:a + rows16], bound[:, a:a + rows16]),
+                                         _ratio_max(_gather(o16t, pts), pw, pb))
         prec["conv_f16_err_over_bound"] = {k: float(f"{v:.3g}") for k, v in f16.items()}
         worst = max(worst, max(f16.values()) / TOL_F16)
     if keep.get("plain512"):

@@ -93,9 +93,12 @@ enum { PENCIL_F32 = 0, PENCIL_F16 = 1 };
  * accumulate in FP32 in tensor memory, and the result is rounded to binary16
  * once (Sec. 3.1: precision traded against speed, here within the binary16
  * tolerance -- |out - exact| <= 2^-10 * sum |k| |in| -- but not the same
- * bits as the CUDA-core kernels, whose summation order differs).  Ignored
- * for FP32 images, with PENCIL_CONV_GENERIC or PENCIL_LAYOUT_HWC, and where
- * the conditions above do not hold (the CUDA-core kernels run). */
+ * bits as the CUDA-core kernels, whose summation order differs).  Inputs
+ * are expected finite: the zeros of a band multiply neighbouring input
+ * values too, so an Inf or NaN input can turn outputs up to 16 columns away
+ * (not only those whose window holds it) into NaN.  Ignored for FP32 images,
+ * with PENCIL_CONV_GENERIC or PENCIL_LAYOUT_HWC, and where the conditions
+ * above do not hold (the CUDA-core kernels run). */
 #define PENCIL_CONV_TENSOR 16
 
 /* Border modes for the _ex conv2d calls, passed in flags as PENCIL_BORDER(m);
