@@ -955,10 +955,12 @@ def run_case(name, reps):
 
     dev = torch.device("cuda", 0)
     if name.startswith("conv"):
+        unaligned = name.endswith("u")  # rows of 4095 elements: not 16-byte aligned
+        name = name.rstrip("u")
         tensor = name.endswith("t")  # binary16 on the tensor cores
         f16 = name.endswith("h") or tensor
         K = int(name[4:].rstrip("ht").split("-")[0])
-        c, h, w = 2, 4096, 4096
+        c, h, w = 2, 4096, 4095 if unaligned else 4096
         img = torch.from_numpy(synth.image_f32(1, c, h, w)).to(dev)
         if f16:  # binary16 storage: twice the pixels, so the image is still larger than L2
             c = 4
@@ -1036,7 +1038,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default=None,
                     help="profile one kernel on a reduced workload: conv3, conv7, conv15, conv3h (binary16), conv15t "
-                         "(binary16 on the tensor cores), sep15, sep15h "
+                         "(binary16 on the tensor cores), conv15u (any conv case with rows of 4095 elements, not "
+                         "16-byte aligned), sep15, sep15h "
                          "(binary16), batch, jacobi, jacobi-tN (N sweeps per pass), op2-ordered, op2-atomic, "
                          "chain3, chain5, chain7, cj3, cj5, cj7 (filter then 10 Jacobi sweeps, fused)")
     ap.add_argument("--reps", type=int, default=3)

@@ -211,14 +211,18 @@ int pencil_conv2d_jacobi(int c, int h, int w, const float *in, int kh, int kw, c
 
 /* ------------------------------------------------------------------- batch
  * Many images, each with its own size and odd filter side 1..15, convolved by
- * ONE graph launch: the captured graph holds one persistent kernel per filter
- * side present (independent graph nodes that may run side by side), each sized to its side's
- * register and shared-memory needs.  A side's tiles are handed out from its
- * own work queue, larger images first, so uneven images keep every SM busy; each
- * batched pixel is the same bits as pencil_conv2d_ex on that image alone (the
- * same fixed per-pixel order).  This is the tuned, launch-once form of the
- * independent loop over images and pixels (Sec. 2.2.3); the tile shape per
- * filter side is chosen by measurement (the auto-tuning step of Sec. 2).
+ * ONE graph launch: the captured graph holds one kernel per filter side
+ * present (independent graph nodes that may run side by side), each sized to
+ * its side's register and shared-memory needs.  A side's tiles form one work
+ * list, larger images first, so uneven images keep every SM busy: either a
+ * persistent grid (every CTA the SMs hold at once) takes them from the side's
+ * queue, or the kernel has one CTA per tile and the hardware block scheduler
+ * hands them out -- which of the two, and the tile shape, is the side's tile
+ * variant.  Each batched pixel is the same bits as pencil_conv2d_ex on that
+ * image alone (the same fixed per-pixel order).  This is the tuned,
+ * launch-once form of the independent loop over images and pixels
+ * (Sec. 2.2.3); the variant per filter side is chosen by measurement (the
+ * auto-tuning step of Sec. 2).
  */
 typedef struct pencil_image {
     const void *in;   /* h*w elements of the batch dtype, device memory */
@@ -235,8 +239,10 @@ typedef struct pencil_batch pencil_batch;
 /* Tile variants of the batched kernels, each its own kernel per filter side:
  * 0 = 32 x 128 outputs, 128 threads   2 = 64 x 128 outputs, 256 threads
  * 1 = 16 x 128 outputs, 128 threads   3 = 32 x 128 outputs, 256 threads
- * (so tile height, rows per thread and CTA size differ between them). */
-#define PENCIL_BATCH_VARIANTS 4
+ * 4 = as 0, one CTA per tile          5 = as 3, one CTA per tile
+ * (so tile height, rows per thread, CTA size and schedule differ between
+ * them: 0-3 run a persistent grid fed from the side's work queue). */
+#define PENCIL_BATCH_VARIANTS 6
 
 /* Create a plan for dtype PENCIL_F32 or PENCIL_F16 (allocates; captures the
  * graph).  All sides start with variant 0.  Errors: NULL, ARG, NOMEM, CUDA. */

@@ -45,7 +45,7 @@ class PencilImage(ctypes.Structure):
                 ("h", ctypes.c_int), ("w", ctypes.c_int), ("ks", ctypes.c_int)]
 
 
-PENCIL_BATCH_VARIANTS = 4
+PENCIL_BATCH_VARIANTS = 6
 
 
 class PencilError(RuntimeError):

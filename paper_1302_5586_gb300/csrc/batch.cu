@@ -1,14 +1,16 @@
 // batch.cu -- many images, each with its own size and filter side, convolved
-// by one graph launch of persistent kernels, one kernel per filter side.
+// by one graph launch, one kernel per filter side.
 //
 // The host builds a tile table grouped by filter side (within a side, images
 // with more tiles first) and a queue header {next, total, start} per side;
 // every tile of image i gets the entry i.  Header, image descriptors and
 // table are copied to a device buffer owned by the plan.  The graph holds,
-// for every side present in the batch, a resident grid (SMs x CTAs per SM)
-// of that side's kernel, as independent nodes that may run side by side; its
-// CTAs take tile indices from the side's `next` with one atomicAdd per tile,
-// look the image up, and run the same tile body as the standalone direct
+// for every side present in the batch, one node of that side's kernel, as
+// independent nodes that may run side by side.  Under a persistent variant
+// the node is a resident grid (SMs x CTAs per SM) whose CTAs take tile
+// indices from the side's `next` with one atomicAdd per tile; under a
+// one-tile variant it has one CTA per tile of the side.  Either way a CTA
+// looks the image up and runs the same tile body as the standalone direct
 // kernel, so every batched pixel is the same bits as pencil_conv2d_ex on that
 // image alone.  One kernel per side and tile variant keeps each kernel's code
 // small (one tile body) and gives it its own register budget and
@@ -16,7 +18,8 @@
 // CTA's next tile run while the current one is computed), chosen per side by
 // measurement, as is its CTA count per SM.  Kernels read the tile counts
 // from the device headers, so the graph captured for a set of sides serves
-// every batch with that set.
+// every batch with that set (a one-tile node's grid is reset to the run's
+// tile count of its side when that changes).
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -49,13 +52,21 @@ struct BatchImage {
 constexpr int kSides = 8;   // filter sides 1, 3, ..., 15; side index = ks / 2
 
 // Tile variants, all 128 columns wide; each is its own kernel per side, so
-// the tuner chooses tile height, rows per thread and CTA size per side:
+// the tuner chooses tile height, rows per thread, CTA size and schedule per
+// side:
 //   0: 32-row tiles, 128 threads     2: 64-row tiles, 256 threads
 //   1: 16-row tiles, 128 threads     3: 32-row tiles, 256 threads
-// Sides up to 7 give a thread one 4-column group (32 threads across a row),
-// larger sides two groups (16 threads across); the rows per thread follow.
+//   4: as 0, one tile per CTA        5: as 3, one tile per CTA
+// Variants 0-3 run a resident grid whose CTAs take tiles from the side's
+// queue; 4 and 5 launch one CTA per tile of the side (the grid is set on the
+// graph node before each run), so the block scheduler hands out the tiles
+// and neighbouring tiles of an image run together, as in the standalone
+// kernels.  Sides up to 7 give a thread one 4-column group (32 threads
+// across a row), larger sides two groups (16 threads across); the rows per
+// thread follow.
 __host__ __device__ constexpr int var_th(int v) { return v == 1 ? 16 : (v == 2 ? 64 : 32); }
-__host__ __device__ constexpr int var_nt(int v) { return v >= 2 ? 256 : 128; }
+__host__ __device__ constexpr int var_nt(int v) { return (v == 2 || v == 3 || v == 5) ? 256 : 128; }
+__host__ __device__ constexpr bool var_onetile(int v) { return v >= 4; }
 constexpr int kTileW = 128;
 __host__ __device__ constexpr int btx(int k) { return k <= 7 ? 32 : 16; }
 __host__ __device__ constexpr int bg(int k) { return k <= 7 ? 1 : 2; }
@@ -97,11 +108,11 @@ struct Slot {
 #endif
 constexpr int kNslot[2][kSides] = PENCIL_BATCH_NSLOT;
 constexpr int kRegCap[2][kSides] = PENCIL_BATCH_REGCAP;
-template <int K>
-constexpr int nslot(size_t esz) { return kNslot[esz == 2][K / 2]; }
+template <int K, int V>
+constexpr int nslot(size_t esz) { return var_onetile(V) ? 1 : kNslot[esz == 2][K / 2]; }
 template <int K, int V>
 constexpr size_t batch_smem(size_t esz) {
-    return nslot<K>(esz) * sizeof(float) * (size_t)Slot<K, V>::floats((int)esz);
+    return nslot<K, V>(esz) * sizeof(float) * (size_t)Slot<K, V>::floats((int)esz);
 }
 // CTAs per SM the register budget is sized for: the table's (in 128-thread
 // CTAs), or fewer where the shared memory holds fewer.
@@ -197,6 +208,26 @@ __global__ void __launch_bounds__(var_nt(V), MINB)
     }
 }
 
+// One tile per CTA: block t of the side's grid computes the side's tile t
+// (the grid is exactly the side's tile count).  Same staging and tile body
+// as the resident kernel, so the same bits.
+template <typename T, int K, int V, int MINB>
+__global__ void __launch_bounds__(var_nt(V), MINB)
+    conv2d_batch_tile_kernel(BatchHeader *__restrict__ hdr, const BatchImage *__restrict__ imgs,
+                             const int *__restrict__ tile_img) {
+    extern __shared__ __align__(16) float smem[];
+    const int t = blockIdx.x;
+    if (t >= hdr->total) return;
+    const int start = hdr->start;
+    const BatchImage d = imgs[__ldg(tile_img + start + t)];
+    int y0, x0;
+    tile_origin<V>(d, start + t, y0, x0);
+    issue_tile<T, K, V>(d, y0, x0, smem);
+    cp_async_wait_all();
+    __syncthreads();
+    compute_tile<T, K, V>(d, y0, x0, smem);
+}
+
 using BatchKernel = void (*)(BatchHeader *, const BatchImage *, const int *);
 
 struct SideKernel {
@@ -208,7 +239,11 @@ struct SideKernel {
 template <typename T, int K, int V>
 SideKernel side_kernel() {
     constexpr size_t esz = sizeof(T);
-    return {conv2d_batch_kernel<T, K, V, nslot<K>(esz), batch_minb<K, V>(esz)>, batch_smem<K, V>(esz), var_nt(V)};
+    if constexpr (var_onetile(V))
+        return {conv2d_batch_tile_kernel<T, K, V, batch_minb<K, V>(esz)>, batch_smem<K, V>(esz), var_nt(V)};
+    else
+        return {conv2d_batch_kernel<T, K, V, nslot<K, V>(esz), batch_minb<K, V>(esz)>, batch_smem<K, V>(esz),
+                var_nt(V)};
 }
 
 template <typename T, int K>
@@ -217,7 +252,9 @@ SideKernel side_kernel_v(int v) {
         case 0: return side_kernel<T, K, 0>();
         case 1: return side_kernel<T, K, 1>();
         case 2: return side_kernel<T, K, 2>();
-        default: return side_kernel<T, K, 3>();
+        case 3: return side_kernel<T, K, 3>();
+        case 4: return side_kernel<T, K, 4>();
+        default: return side_kernel<T, K, 5>();
     }
 }
 
@@ -253,11 +290,20 @@ struct pencil_batch {
     cudaEvent_t uploaded[2] = {nullptr, nullptr};
     int flip = 0;
     int sms = 0;                 // SMs of the plan's device
-    int grid[kSides] = {};       // resident grid of each side's kernel
+    int grid[kSides] = {};       // resident grid of each side's kernel (0: one CTA per tile)
     size_t smem[kSides] = {};    // its dynamic shared memory
     int nt[kSides] = {};         // its threads per CTA
     BatchKernel fn[kSides] = {};
-    std::map<unsigned, cudaGraphExec_t> exec;  // graph per set of sides present
+    // A captured graph per set of sides present.  The graph is kept beside
+    // its executable so that the grid of a one-tile-per-CTA node can be set
+    // to the tile count of each run.
+    struct Captured {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        cudaGraphNode_t node[kSides] = {};
+        unsigned grid[kSides] = {};  // grid each node was captured or last set with
+    };
+    std::map<unsigned, Captured> exec;
     std::mutex mu;
 };
 
@@ -308,48 +354,72 @@ bool batch_disjoint(int n, const pencil_image *imgs, size_t esz) {
     return true;
 }
 
+// Launch parameters of side i's node; a one-tile-per-CTA kernel gets one CTA
+// per tile of the side in this run (`tiles`).
+cudaKernelNodeParams side_params(const pencil_batch *b, int i, unsigned tiles, void **args) {
+    cudaKernelNodeParams p = {};
+    p.func = reinterpret_cast<void *>(b->fn[i]);
+    p.gridDim = dim3(b->grid[i] > 0 ? (unsigned)b->grid[i] : tiles);
+    p.blockDim = dim3((unsigned)b->nt[i]);
+    p.sharedMemBytes = (unsigned)b->smem[i];
+    p.kernelParams = args;
+    return p;
+}
+
 // The graph for a set of sides (bit i = side 2i+1): one kernel node per side,
 // with no edges between them, so the sides' kernels may run side by side: a
 // side whose queue is short (a small wave of requests) leaves SMs to the
 // next side at once instead of holding the others back, and at the end of a
-// long side the next one fills the SMs it frees.
-cudaError_t graph_for(pencil_batch *b, unsigned mask, cudaGraphExec_t *out) {
-    auto it = b->exec.find(mask);
-    if (it != b->exec.end()) {
-        *out = it->second;
-        return cudaSuccess;
-    }
+// long side the next one fills the SMs it frees.  A resident grid reads its
+// tile count from the device header, so its node serves every batch; the
+// grid of a one-tile-per-CTA node is set to this run's tile count of its side
+// (tiles[i]) whenever that count changes (the update applies to later launches
+// of the graph only, never to one already queued).
+cudaError_t graph_for(pencil_batch *b, unsigned mask, const unsigned *tiles, cudaGraphExec_t *out) {
     BatchHeader *hdr = static_cast<BatchHeader *>(b->dbuf);
     BatchImage *imgs = reinterpret_cast<BatchImage *>(static_cast<char *>(b->dbuf) +
                                                       align256(sizeof(BatchHeader) * kSides));
     int *tile_img = reinterpret_cast<int *>(static_cast<char *>(b->dbuf) + head_bytes(b->max_images));
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t x = nullptr;
-    cudaError_t e = cudaGraphCreate(&g, 0);
+    auto it = b->exec.find(mask);
+    if (it != b->exec.end()) {
+        pencil_batch::Captured &c = it->second;
+        for (int i = 0; i < kSides; ++i)
+            if ((mask & (1u << i)) && b->grid[i] == 0 && c.grid[i] != tiles[i]) {
+                BatchHeader *h = hdr + i;
+                void *args[] = {&h, &imgs, &tile_img};
+                const cudaKernelNodeParams p = side_params(b, i, tiles[i], args);
+                const cudaError_t e = cudaGraphExecKernelNodeSetParams(c.x, c.node[i], &p);
+                if (e != cudaSuccess) return e;
+                c.grid[i] = tiles[i];
+            }
+        *out = c.x;
+        return cudaSuccess;
+    }
+    pencil_batch::Captured c;
+    cudaError_t e = cudaGraphCreate(&c.g, 0);
     for (int i = kSides - 1; i >= 0 && e == cudaSuccess; --i)
         if (mask & (1u << i)) {
             BatchHeader *h = hdr + i;
             void *args[] = {&h, &imgs, &tile_img};
-            cudaKernelNodeParams p = {};
-            p.func = reinterpret_cast<void *>(b->fn[i]);
-            p.gridDim = dim3((unsigned)b->grid[i]);
-            p.blockDim = dim3((unsigned)b->nt[i]);
-            p.sharedMemBytes = (unsigned)b->smem[i];
-            p.kernelParams = args;
-            cudaGraphNode_t node;
-            e = cudaGraphAddKernelNode(&node, g, nullptr, 0, &p);
+            const cudaKernelNodeParams p = side_params(b, i, tiles[i], args);
+            e = cudaGraphAddKernelNode(&c.node[i], c.g, nullptr, 0, &p);
+            c.grid[i] = p.gridDim.x;
         }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
-    if (g) cudaGraphDestroy(g);
-    if (e == cudaSuccess) {
-        b->exec[mask] = x;
-        *out = x;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c.x, c.g, 0);
+    if (e != cudaSuccess) {
+        if (c.g) cudaGraphDestroy(c.g);
+        return e;
     }
-    return e;
+    b->exec[mask] = c;
+    *out = c.x;
+    return cudaSuccess;
 }
 
 void drop_graphs(pencil_batch *b) {
-    for (auto &kv : b->exec) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : b->exec) {
+        cudaGraphExecDestroy(kv.second.x);
+        cudaGraphDestroy(kv.second.g);
+    }
     b->exec.clear();
 }
 
@@ -364,7 +434,7 @@ cudaError_t load_side(pencil_batch *b, int i, int v) {
     b->fn[i] = sk.fn;
     b->smem[i] = sk.smem;
     b->nt[i] = sk.nt;
-    b->grid[i] = std::max(1, per_sm) * b->sms;
+    b->grid[i] = var_onetile(v) ? 0 : std::max(1, per_sm) * b->sms;
     return cudaSuccess;
 }
 
@@ -494,8 +564,10 @@ int pencil_batch_run(pencil_batch *b, int n, const pencil_image *imgs, void *str
         sh.total += (int)nt[order[j]];
         base += nt[order[j]];
     }
+    unsigned tiles[kSides];
+    for (int i = 0; i < kSides; ++i) tiles[i] = (unsigned)hh[i].total;
     cudaGraphExec_t x = nullptr;
-    e = graph_for(b, mask, &x);
+    e = graph_for(b, mask, tiles, &x);
     if (e != cudaSuccess) return cuda_fail(e);
     // copy headers + descriptors + the used part of the tile table
     cudaStream_t s = (cudaStream_t)stream;
