@@ -190,9 +190,15 @@ __device__ __forceinline__ void stage_issue(const T *__restrict__ src, int h, in
                 cp_async8(s + r * SW + q * V, row + gc);
                 cp_async8(s + r * SW + q * V + V / 2, row + gc + V / 2);
             }
+        } else if (!F16 && inside) {
+            // unaligned row, chunk inside it: one 4-byte copy per element at
+            // constant offsets from one source and one destination address
+            float *d = s + r * SW + q * V;
+#pragma unroll
+            for (int e = 0; e < V; ++e) cp_async4(d + e, row + gc + e);
         } else if (!F16) {
-            // unaligned row or a chunk across the edge: one 4-byte copy per
-            // element, from the column the border mode selects
+            // a chunk across the edge: one 4-byte copy per element, from the
+            // column the border mode selects
             float *d = s + r * SW + q * V;
 #pragma unroll
             for (int e = 0; e < V; ++e) {
@@ -207,6 +213,11 @@ __device__ __forceinline__ void stage_issue(const T *__restrict__ src, int h, in
             T *d16 = s16 + r * SW + q * V;
 #pragma unroll
             for (int e = 0; e < V; e += 2) cp_async4(d16 + e, row + gc + e);
+        } else if (inside) {
+            // binary16 row aligned to 2 bytes only, chunk inside it
+            T *d16 = s16 + r * SW + q * V;
+#pragma unroll
+            for (int e = 0; e < V; ++e) d16[e] = row[gc + e];
         } else {
             T *d16 = s16 + r * SW + q * V;  // raw binary16 values, widened below
 #pragma unroll
