@@ -266,7 +266,7 @@ def run_ours(args, rank, world, local_rank):
     extras, keep = {}, {}
     if rank == 0 and not args.no_extras:
         extras, keep = measure_extras(torch, pg, dev, stream, d_img, d_out, ks, g, args.serve_seconds)
-    e2e = measure_e2e(torch, pg, img, ks, g, max(3, min(args.steps // 20, 8))) if not args.no_e2e else None
+    e2e = measure_e2e(torch, pg, img, ks, g, max(3, min(args.steps // 20, 24))) if not args.no_e2e else None
 
     if dist is not None:
         dist.barrier()

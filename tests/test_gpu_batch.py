@@ -1,4 +1,4 @@
-"""The batched persistent conv2d kernels: bit-identical to the standalone
+"""The batched conv2d kernels: bit-identical to the standalone
 kernel on every image, within tolerance of the FP64 oracle, for every tile
 variant (and a mix of variants across sides), across batches replayed from
 the same captured graph and after a variant change drops the graphs."""
@@ -75,6 +75,29 @@ def test_one_plan_serves_successive_batches():
             torch.cuda.synchronize()
             for it in items:
                 assert torch.equal(it[1], standalone(it, pg.PENCIL_F32))
+    finally:
+        pg.pencil_batch_destroy(plan)
+
+
+@pytest.mark.parametrize("variant", [4, 5])
+def test_one_tile_variant_follows_the_tile_count_of_each_batch(variant):
+    """Under a one-CTA-per-tile variant the captured graph's grid is reset to
+    each run's tile count: batches of one filter side (so one captured graph)
+    with more, then fewer, then more tiles all match the standalone kernel
+    (outputs start as NaN, so a tile left out shows)."""
+    plan = pg.pencil_batch_create(pg.PENCIL_F32, 40, 1 << 15)
+    try:
+        pg.pencil_batch_set_variant(plan, 5, variant)
+        counts = []
+        for seed, n, hi in ((31, 30, 300), (32, 3, 40), (33, 36, 260)):
+            items, _ = make_batch(seed, n, 5, hi, pg.PENCIL_F32, ks=5)
+            imgs = pg.make_images(items)
+            counts.append(pg.pencil_batch_tiles(plan, imgs))
+            pg.pencil_batch_run(plan, imgs)
+            torch.cuda.synchronize()
+            for it in items:
+                assert torch.equal(it[1], standalone(it, pg.PENCIL_F32))
+        assert counts[1] < counts[0] and counts[2] != counts[1]
     finally:
         pg.pencil_batch_destroy(plan)
 
