@@ -79,9 +79,10 @@ using BCfg = DirectCfg<K, K, btx(K), bty(K, V), brows(K, V), bg(K)>;
 // the standalone kernels do the same).
 __host__ __device__ constexpr bool bhalfw(int k, size_t esz) { return esz == 2 && k <= 7; }
 // Rows that are not 16-byte aligned move in the widest copies and stores each
-// address allows on the memory-bound sides; larger sides keep 4-byte copies
-// (less code around their FMA loop), as the standalone kernels do.
-__host__ __device__ constexpr bool badapt(int k) { return k <= 5; }
+// address allows, except on the FP32 sides from 11, where 4-byte copies and
+// scalar stores measured 0.5-2% faster on the 512-image batch (less code
+// around their FMA loop).
+__host__ __device__ constexpr bool badapt(int k, size_t esz) { return esz == 2 || k <= 9; }
 
 // A staging slot of side K, variant V: filter rows | FP32 tile | binary16
 // tile; without the FP32 tile where the binary16 tile is read directly.
@@ -127,7 +128,7 @@ template <typename T, int K, int V>
 __device__ __forceinline__ void issue_tile(const BatchImage &d, int y0, int x0, float *slot) {
     using Cfg = BCfg<K, V>;
     stage_filter_async<K, K, Cfg::KWP, Cfg::NT>(d.k, slot);
-    stage_issue<T, Cfg::SH, Cfg::SW, Cfg::NT, false, badapt(K)>(static_cast<const T *>(d.in), d.h, d.w,
+    stage_issue<T, Cfg::SH, Cfg::SW, Cfg::NT, false, badapt(K, sizeof(T))>(static_cast<const T *>(d.in), d.h, d.w,
                                                                 y0 - Cfg::AH, x0 - Cfg::P, d.vec_ok,
                                                                 slot + Slot<K, V>::KF,
                                                                 reinterpret_cast<T *>(slot + Slot<K, V>::f16_off(sizeof(T))));
@@ -139,11 +140,11 @@ __device__ __forceinline__ void compute_tile(const BatchImage &d, int y0, int x0
     using Cfg = BCfg<K, V>;
     const T *s16 = reinterpret_cast<const T *>(slot + Slot<K, V>::f16_off(sizeof(T)));
     if constexpr (bhalfw(K, sizeof(T))) {
-        direct_compute<T, K, K, btx(K), bty(K, V), brows(K, V), bg(K), T, badapt(K)>(s16, slot, static_cast<T *>(d.out),
+        direct_compute<T, K, K, btx(K), bty(K, V), brows(K, V), bg(K), T, badapt(K, sizeof(T))>(s16, slot, static_cast<T *>(d.out),
                                                                                      d.h, d.w, d.vec_ok, y0, x0);
     } else {
         stage_widen<T, Cfg::SH, Cfg::SW, Cfg::NT>(slot + Slot<K, V>::KF, s16);
-        direct_compute<T, K, K, btx(K), bty(K, V), brows(K, V), bg(K), float, badapt(K)>(
+        direct_compute<T, K, K, btx(K), bty(K, V), brows(K, V), bg(K), float, badapt(K, sizeof(T))>(
             slot + Slot<K, V>::KF, slot, static_cast<T *>(d.out), d.h, d.w, d.vec_ok, y0, x0);
     }
 }
