@@ -148,7 +148,9 @@ int pencil_conv2d(int h, int w, PENCIL_ARR2(const float, in, h, w), int kh, int 
  * Speed, not results, depends on alignment: images whose rows are 16-byte
  * aligned (w a multiple of 4 for FP32, of 8 for binary16, and in and out
  * 16-byte aligned) with the clamp or zero border load their tiles with the
- * tensor memory accelerator; others use cp.async copies.  The call may be
+ * tensor memory accelerator; others use cp.async copies as wide as each row
+ * allows (large planar images of odd width at filter sides up to 5: one
+ * tensor-memory-accelerator copy per staged row).  The call may be
  * captured in a CUDA graph.  Errors: ARG, NULL, ALIAS, PTR, CUDA. */
 int pencil_conv2d_ex(int c, int h, int w, const void *in, int kh, int kw, const float *k,
                      void *out, int dtype, int flags, void *stream);

@@ -615,16 +615,18 @@ bool try_direct_tma(int c, int h, int w, const T *in, const float *k, T *out, bo
 
 // Planar rows that are not 16-byte aligned take the row staging on images
 // of at least 2^20 elements (smaller ones are latency-bound, and there the
-// cp.async staging measured faster): binary16 images at every side, FP32 at
-// sides up to 5 when the rows are not 8-byte aligned either (odd widths).
-// Elsewhere the cp.async kernel compiled for unaligned rows, with its 8-byte
-// copies where a row allows them, measured faster (3 x 4096 x 4094: 3x3
-// 0.083 -> 0.078 ms, 5x5 0.101 -> 0.095, 7x7 0.140 -> 0.130; 3 x 4096 x 4095:
-// 7x7 0.141 -> 0.137).
+// cp.async staging measured faster) at sides up to 5, when the rows are not
+// even 8-byte (FP32) or 4-byte (binary16) aligned: odd widths.  Elsewhere the
+// cp.async kernel compiled for unaligned rows, with the widest copies each
+// row allows, measured faster (3 x 4096 x 4094: FP32 3x3 0.083 -> 0.078 ms,
+// 5x5 0.101 -> 0.095, 7x7 0.140 -> 0.130; binary16 3x3 0.071 -> 0.060, 7x7
+// 0.143 -> 0.125, 11x11 0.292 -> 0.260, 15x15 0.476 -> 0.461, and more at
+// 3 x 4096 x 4092; odd widths, 3 x 4096 x 4095: FP32 7x7 0.141 -> 0.137,
+// binary16 7x7 0.142 -> 0.140, 11x11 0.295 -> 0.280, 15x15 0.523 -> 0.515).
 constexpr long long kRowsMin = 1ll << 20;
 template <typename T, int K>
 constexpr bool rows_pay() {
-    return sizeof(T) == 2 || K <= 5;
+    return K <= 5;
 }
 
 template <typename T, int K, int TX, int TY, int R, int G = 1, int MINB = 1, bool HALFW = false, int CS = 1,
@@ -636,27 +638,29 @@ cudaError_t run_direct(int c, int h, int w, const T *in, const float *k, T *out,
     if (try_direct_tma<T, K, TX, TY, R, G, MINB, HALFW, CS, C>(c, h, w, in, k, out, vec_ok, border, s, &err))
         return err;
     if constexpr (CS == 1 && rows_pay<T, K>()) {
-        const bool rows8 = sizeof(T) == 4 && w % 2 == 0 && (uintptr_t)in % 8 == 0 && (uintptr_t)out % 8 == 0;
-        if (!vec_ok && !rows8 && (long long)c * h * w >= kRowsMin &&
+        // rows at least 8-byte (FP32) or 4-byte (binary16) aligned
+        const unsigned a = sizeof(T) == 4 ? 8u : 4u;
+        const bool wide = w % 2 == 0 && (uintptr_t)in % a == 0 && (uintptr_t)out % a == 0;
+        if (!vec_ok && !wide && (long long)c * h * w >= kRowsMin &&
             try_direct_rows<T, K, TX, TY, R, G, MINB, HALFW, C>(c, h, w, in, k, out, border, s, &err))
             return err;
     }
     // sides up to 5 (memory-bound): an aligned-row kernel and an adaptive
     // any-row kernel; larger sides: one kernel with vec_ok at run time, and
-    // for FP32 rows that are not aligned (clamp border) a kernel compiled for
-    // them: adaptive copies and stores at side 7 and from side 11, 4-byte ones
-    // at side 9 (3 x 4096 x 4095 / 4094: 2-12% faster than the run-time
-    // kernel, the same bits)
+    // for rows that are not aligned (clamp border) a kernel compiled for them:
+    // adaptive copies and stores, but 4-byte ones at FP32 side 9 (3 x 4096 x
+    // 4095 / 4094: 2-12% faster than the run-time kernel, the same bits)
     using Kern = void (*)(const T *, const float *, T *, int, int, bool, int);
     Kern kern;
     if constexpr (K <= 5 && CS == 1)
         kern = border != 0 ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, true, HALFW, 2, 1, C>
                : vec_ok    ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 1, 1, C>
                            : conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 2, 1, C>;
-    else if constexpr (K >= 7 && CS == 1 && sizeof(T) == 4)
+    else if constexpr (K >= 7 && CS == 1)
         kern = border != 0 ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, true, HALFW, 0, 1, C>
                : vec_ok    ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 0, 1, C>
-                           : conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, K == 9 ? 3 : 2, 1, C>;
+                           : conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW,
+                                                  sizeof(T) == 4 && K == 9 ? 3 : 2, 1, C>;
     else  // interleaved images keep to one kernel per border class (their aligned rows take TMA)
         kern = border != 0 ? conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, true, HALFW, 0, CS, C>
                            : conv2d_direct_kernel<T, K, K, TX, TY, R, G, MINB, false, HALFW, 0, CS, C>;

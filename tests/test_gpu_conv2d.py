@@ -66,9 +66,10 @@ def test_specialised_and_generic_kernels_agree_bitwise(K, shape):
 
 
 # Planar images of at least 2^20 elements whose rows are not 16-byte aligned
-# (w % 4 = 1, 2, 3) take the row-staged TMA kernels (binary16 at every side,
-# FP32 up to side 7); the generic kernel shares the per-pixel order, so the
-# two agree bit for bit, and the oracle checks both.
+# (w % 4 = 1, 2, 3) take the row-staged TMA kernels (odd widths, sides up to
+# 5) or the cp.async kernels compiled for unaligned rows (even widths, larger
+# sides); the generic kernel shares the per-pixel order, so each agrees with
+# it bit for bit, and the oracle checks both.
 ROW_SHAPES = [(1, 1031, 1029), (2, 767, 1366), (1, 1100, 1023)]
 
 
