@@ -711,6 +711,17 @@ cudaError_t run_sep(int c, int h, int w, const T *in, const float *gx, const flo
     } else {
         kern = border != 0 ? conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, true, PAIR, 0, CS, HALFR, CR>
                            : conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 0, CS, HALFR, CR>;
+        if constexpr (CS == 1) {
+            // planar rows that are not aligned (clamp border): the kernel
+            // compiled for them, with the widest copies each row allows, except
+            // FP32 rows not even 8-byte aligned from side 9 (3 x 4096 x 4094:
+            // FP32 7x7 0.124 -> 0.092 ms, 15x15 0.142 -> 0.128, binary16 15x15
+            // 0.124 -> 0.107; odd width 4095: FP32 7x7 0.122 -> 0.110 but 15x15
+            // 0.141 -> 0.149, binary16 15x15 0.142 -> 0.132)
+            const bool rows8 = w % 2 == 0 && (uintptr_t)in % 8 == 0 && (uintptr_t)out % 8 == 0;
+            if (border == 0 && !vec_ok && (sizeof(T) == 2 || K == 7 || rows8))
+                kern = conv2d_sep_kernel<T, K, K, TX, TY, R, MINB, INPLACE, false, PAIR, 2, 1, HALFR, CR>;
+        }
     }
     const size_t smem = Cfg::smem(sizeof(T));
     cudaError_t e = set_smem(kern, smem);

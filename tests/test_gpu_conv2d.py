@@ -140,7 +140,7 @@ def test_nan_footprint_matches_oracle(K, p, q):
 
 
 @pytest.mark.parametrize("K", [3, 5, 7, 9, 11, 13, 15])
-@pytest.mark.parametrize("shape", [(2, 75, 301), (1, 200, 520), (1, 2, 3)])
+@pytest.mark.parametrize("shape", [(2, 75, 301), (1, 200, 520), (1, 2, 3), (1, 130, 258)])
 def test_separable_matches_oracle(K, shape):
     c, h, w = shape
     gx = synth.gaussian_taps_f32(K // 2, 1.0 + K / 5)
