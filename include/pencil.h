@@ -430,8 +430,8 @@ typedef struct pencil_op2_plan pencil_op2_plan;
 
 /* Build the per-cell contribution lists of a mesh: e2c is host memory,
  * 2*nedges cell indices in [0, ncells) (edge i joins e2c[2i] and e2c[2i+1]);
- * the plan keeps device copies.  Errors: NULL, ARG (an index out of range,
- * sizes), NOMEM, CUDA. */
+ * the plan keeps device copies (lists of at most 8 per cell as a fixed-width
+ * table).  Errors: NULL, ARG (an index out of range, sizes), NOMEM, CUDA. */
 int pencil_op2_plan_create(int ncells, int nedges, const int *e2c, pencil_op2_plan **out);
 
 /* Stream-ordered: cell[c] += sum of its edges' values.  edge (nedges doubles)

@@ -9,10 +9,15 @@
 //              starts from the cell's value and adds its edges in list order in
 //              FP64, so the result is the same bits as the sequential loop and
 //              does not depend on the launch (the reproducible reading of the
-//              loop, Sec. 3.1).
+//              loop, Sec. 3.1).  Where no cell has more than 8 contributions
+//              (and the table stays within twice the list's size), the lists
+//              are stored as D = 4 or 8 slots per cell, slot-major, padded with
+//              -1: a thread's index loads are then coalesced and need no row
+//              pointer first, one dependent load fewer.
 //   atomic  -- one thread per edge, two FP64 atomicAdds: no plan, but the
 //              order of the additions (and so the rounding) varies from run to
 //              run -- the precision-for-speed switch Sec. 3.1 anticipates.
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -45,6 +50,27 @@ __global__ void __launch_bounds__(256)
     cell[c] = acc;
 }
 
+// The same additions from the slot-major table: slot s of cell c at
+// ell[s * ncells + c], -1 past the cell's last contribution.
+template <int D>
+__global__ void __launch_bounds__(256)
+    op2_ordered_ell_kernel(const int *__restrict__ ell, const double *__restrict__ edge, double *__restrict__ cell,
+                           int ncells) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    double acc = cell[c];
+    int e[D];
+#pragma unroll
+    for (int s = 0; s < D; ++s) e[s] = __ldg(ell + (size_t)s * ncells + c);
+    double v[D];
+#pragma unroll
+    for (int s = 0; s < D; ++s) v[s] = e[s] >= 0 ? __ldg(edge + e[s]) : 0.0;
+#pragma unroll
+    for (int s = 0; s < D; ++s)
+        if (e[s] >= 0) acc = __dadd_rn(acc, v[s]);
+    cell[c] = acc;
+}
+
 __global__ void __launch_bounds__(256)
     op2_atomic_kernel(const int *__restrict__ e2c, const double *__restrict__ edge,
                       double *__restrict__ cell, int nedges) {
@@ -63,8 +89,10 @@ using namespace pencil;
 
 struct pencil_op2_plan {
     int ncells = 0, nedges = 0;
-    int *rowptr = nullptr;  // device, ncells + 1
-    int *col = nullptr;     // device, 2 * nedges edge indices, per cell in sequential order
+    int ell_d = 0;          // slots per cell of the table (4 or 8), or 0: the lists below
+    int *ell = nullptr;     // device, ell_d * ncells edge indices, slot-major, -1 padded
+    int *rowptr = nullptr;  // device, ncells + 1 (without the table)
+    int *col = nullptr;     // device, 2 * nedges edge indices, per cell in sequential order (without the table)
     int *e2c = nullptr;     // device, 2 * nedges
 };
 
@@ -88,19 +116,37 @@ int pencil_op2_plan_create(int ncells, int nedges, const int *e2c, pencil_op2_pl
         col[(size_t)pos[e2c[2 * i + 1]]++] = i;
         col[(size_t)pos[e2c[2 * i]]++] = i;
     }
+    int maxdeg = 0;
+    for (int c = 0; c < ncells; ++c) maxdeg = std::max(maxdeg, count[(size_t)c + 1] - count[c]);
+    const int d = maxdeg == 0 ? 0 : (maxdeg <= 4 ? 4 : (maxdeg <= 8 ? 8 : 0));
+    std::vector<int> ell;
+    if (d > 0 && (size_t)d * ncells <= (size_t)4 * nedges) {
+        ell.assign((size_t)d * ncells, -1);
+        for (int c = 0; c < ncells; ++c)
+            for (int j = count[c]; j < count[(size_t)c + 1]; ++j)
+                ell[(size_t)(j - count[c]) * ncells + c] = col[(size_t)j];
+    }
     pencil_op2_plan *p = new (std::nothrow) pencil_op2_plan;
     if (!p) return PENCIL_ERR_NOMEM;
     p->ncells = ncells;
     p->nedges = nedges;
-    cudaError_t e = cudaMalloc(&p->rowptr, sizeof(int) * ((size_t)ncells + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&p->col, sizeof(int) * col.size());
+    cudaError_t e = cudaSuccess;
+    if (!ell.empty()) {
+        p->ell_d = d;
+        e = cudaMalloc(&p->ell, sizeof(int) * ell.size());
+        if (e == cudaSuccess) e = cudaMemcpy(p->ell, ell.data(), sizeof(int) * ell.size(), cudaMemcpyHostToDevice);
+    } else {
+        e = cudaMalloc(&p->rowptr, sizeof(int) * ((size_t)ncells + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&p->col, sizeof(int) * col.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->rowptr, count.data(), sizeof(int) * ((size_t)ncells + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&p->e2c, sizeof(int) * ((size_t)2 * nedges + 2));
-    if (e == cudaSuccess)
-        e = cudaMemcpy(p->rowptr, count.data(), sizeof(int) * ((size_t)ncells + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(p->col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && nedges > 0)
         e = cudaMemcpy(p->e2c, e2c, sizeof(int) * (size_t)2 * nedges, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
+        cudaFree(p->ell);
         cudaFree(p->rowptr);
         cudaFree(p->col);
         cudaFree(p->e2c);
@@ -127,7 +173,13 @@ int pencil_op2_inc(const pencil_op2_plan *p, const double *edge, double *cell, i
     }
     cudaStream_t s = (cudaStream_t)stream;
     if (mode == PENCIL_OP2_ORDERED) {
-        op2_ordered_kernel<<<(p->ncells + 255) / 256, 256, 0, s>>>(p->rowptr, p->col, edge, cell, p->ncells);
+        const unsigned blocks = (unsigned)((p->ncells + 255) / 256);
+        if (p->ell_d == 4)
+            op2_ordered_ell_kernel<4><<<blocks, 256, 0, s>>>(p->ell, edge, cell, p->ncells);
+        else if (p->ell_d == 8)
+            op2_ordered_ell_kernel<8><<<blocks, 256, 0, s>>>(p->ell, edge, cell, p->ncells);
+        else
+            op2_ordered_kernel<<<blocks, 256, 0, s>>>(p->rowptr, p->col, edge, cell, p->ncells);
     } else if (p->nedges > 0) {
         op2_atomic_kernel<<<(p->nedges + 255) / 256, 256, 0, s>>>(p->e2c, edge, cell, p->nedges);
     }
@@ -137,6 +189,7 @@ int pencil_op2_inc(const pencil_op2_plan *p, const double *edge, double *cell, i
 
 int pencil_op2_plan_destroy(pencil_op2_plan *p) {
     if (!p) return PENCIL_OK;
+    cudaFree(p->ell);
     cudaFree(p->rowptr);
     cudaFree(p->col);
     cudaFree(p->e2c);

@@ -107,6 +107,31 @@ def test_irregular_degrees_self_loops_and_isolated_cells():
     np.testing.assert_array_equal(got[2700:], cells[2700:])
 
 
+def test_ordered_is_bit_exact_on_an_eight_neighbour_mesh():
+    """Cells joined to their side and diagonal neighbours (interior cells have
+    eight contributions), self-loops on the corners, shuffled: the plan's
+    eight-slot table, against the oracle bit for bit."""
+    dev()
+    nx, ny = 61, 47
+    idx = np.arange(nx * ny).reshape(ny, nx)
+    pairs = [np.stack([idx[:, :-1].ravel(), idx[:, 1:].ravel()], axis=1),
+             np.stack([idx[:-1, :].ravel(), idx[1:, :].ravel()], axis=1),
+             np.stack([idx[:-1, :-1].ravel(), idx[1:, 1:].ravel()], axis=1),
+             np.stack([idx[:-1, 1:].ravel(), idx[1:, :-1].ravel()], axis=1),
+             np.repeat(np.array([idx[0, 0], idx[0, -1], idx[-1, 0], idx[-1, -1]])[:, None], 2, axis=1)]
+    r = np.random.default_rng(9)
+    e2c = np.concatenate(pairs)
+    e2c = e2c[r.permutation(len(e2c))]
+    sw = r.integers(0, 2, len(e2c)).astype(bool)
+    e2c[sw] = e2c[sw][:, ::-1]
+    e2c = np.ascontiguousarray(e2c, dtype=np.int32)
+    assert np.bincount(e2c.ravel()).max() == 8
+    edge = r.standard_normal(len(e2c))
+    cells = r.standard_normal(nx * ny)
+    want = oracle.op2_inc(cells, e2c, edge)
+    np.testing.assert_array_equal(_run(e2c, nx * ny, edge, cells, pg.PENCIL_OP2_ORDERED), want)
+
+
 def test_no_edges_leaves_cells_unchanged():
     dev()
     cells = synth.u01_f64(2, 37)
