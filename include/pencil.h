@@ -318,9 +318,9 @@ void pencil_arena_destroy(pencil_arena *a);
  * the points of one sweep are independent (Sec. 2.2.3).
  *
  * Residual of an iterate: sqrt(sum over the interior of r^2),
- * r = 4u[i][j] - ((u[i-1][j] + u[i+1][j]) + (u[i][j-1] + u[i][j+1])), r in FP32,
- * r^2 formed exactly and summed per thread with compensation, then across
- * threads and blocks in FP64 in a fixed order (the `reduction` directive,
+ * r = 4u[i][j] - ((u[i-1][j] + u[i+1][j]) + (u[i][j-1] + u[i][j+1])), r and
+ * r^2 in FP32, summed per thread with compensation, then across threads and
+ * blocks in FP64 in a fixed order (the `reduction` directive,
  * Sec. 2.2.3).  Grids with h < 3 or w < 3 have no interior: sweeps change
  * nothing and residuals are 0.
  */

@@ -7,11 +7,11 @@
 //
 // Residual (the `reduction` directive, Sec. 2.2.3):
 //   sqrt(sum_interior r^2),  r = 4u[i][j] - ((up + down) + (left + right)),
-// r in FP32 (4u is exact); r^2 is split exactly into p + e (p = r*r rounded,
-// e = fma(r, r, -p)) and added per thread into a compensated FP32 pair
-// (Knuth's TwoSum), which is exact to about 2^-44 of the sum; the per-thread
-// pairs are then added in FP64: warp butterfly, block, and one fixed-order
-// pass over the per-block partials.  The order depends only on the grid
+// r in FP32 (one rounding: 4u is exact, so fma(4, u, -s) is 4u - s rounded
+// once), r^2 rounded to FP32 and added per thread into a compensated FP32
+// pair (Knuth's TwoSum), which holds the sum of the rounded squares to about
+// 2^-44 of it; the per-thread pairs are then added in FP64: warp butterfly,
+// block, and one fixed-order pass over the per-block partials.  The order depends only on the grid
 // shape, so the same iterate always gives the same residual bits.
 //
 // Layout: a thread owns 4 adjacent columns (one float4) and JR rows of a
@@ -127,10 +127,10 @@ __global__ void __launch_bounds__(JT)
                 V[(size_t)i * w4 + q] = n;
             }
             if (RESID && colok) {
-                if (j0 > 0) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.x), sx), hi, lo);
-                acc_sq(__fsub_rn(__fmul_rn(4.f, cur.y), sy), hi, lo);
-                acc_sq(__fsub_rn(__fmul_rn(4.f, cur.z), sz), hi, lo);
-                if (j0 + 3 < w - 1) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.w), sw), hi, lo);
+                if (j0 > 0) acc_sq(__fmaf_rn(4.f, cur.x, -sx), hi, lo);
+                acc_sq(__fmaf_rn(4.f, cur.y, -sy), hi, lo);
+                acc_sq(__fmaf_rn(4.f, cur.z, -sz), hi, lo);
+                if (j0 + 3 < w - 1) acc_sq(__fmaf_rn(4.f, cur.w, -sw), hi, lo);
             }
         } else if (STORE && colok) {
             V[(size_t)i * w4 + q] = cur;  // boundary row
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(JT)
         if (i > 0 && i < h - 1 && j > 0 && j < w - 1) {
             const float s = nsum(__ldg(u + p - w), __ldg(u + p + w), __ldg(u + p - 1), __ldg(u + p + 1));
             if (STORE) v[p] = __fmul_rn(0.25f, s);
-            if (RESID) acc_sq(__fsub_rn(__fmul_rn(4.f, c), s), hi, lo);
+            if (RESID) acc_sq(__fmaf_rn(4.f, c, -s), hi, lo);
         } else if (STORE) {
             v[p] = c;
         }

@@ -12,14 +12,16 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Add r^2, rounded to FP32, to the compensated pair (hi, lo): Knuth's TwoSum
+// keeps the rounding error of each addition in lo, so hi + lo holds the sum
+// of the rounded squares to about 2^-44 of it.
 __device__ __forceinline__ void acc_sq(float r, float &hi, float &lo) {
-    const float p = __fmul_rn(r, r);
-    const float e = __fmaf_rn(r, r, -p);  // p + e == r*r exactly
+    const float p = __fmul_rn(r, r);  // r^2 rounded to FP32
     const float t = __fadd_rn(hi, p);
     const float bp = __fsub_rn(t, hi);
     const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));
     hi = t;
-    lo = __fadd_rn(lo, __fadd_rn(err, e));
+    lo = __fadd_rn(lo, err);
 }
 
 __device__ __forceinline__ float nsum(float up, float dn, float lf, float rt) {
@@ -92,10 +94,10 @@ __device__ __forceinline__ void reg_sweep(float4 (&y)[RS + 1], const float4 abov
             nv.w = (rint && cint[3]) ? nv.w : cur.w;
         }
         if (RESID && core_cols && g >= core_lo && g < core_hi && g >= 1 && g <= h - 2) {
-            if (cint[0]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.x), sx), hi, lo);
-            if (cint[1]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.y), sy), hi, lo);
-            if (cint[2]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.z), sz), hi, lo);
-            if (cint[3]) acc_sq(__fsub_rn(__fmul_rn(4.f, cur.w), sw), hi, lo);
+            if (cint[0]) acc_sq(__fmaf_rn(4.f, cur.x, -sx), hi, lo);
+            if (cint[1]) acc_sq(__fmaf_rn(4.f, cur.y, -sy), hi, lo);
+            if (cint[2]) acc_sq(__fmaf_rn(4.f, cur.z, -sz), hi, lo);
+            if (cint[3]) acc_sq(__fmaf_rn(4.f, cur.w, -sw), hi, lo);
         }
         y[DOWN ? OFF + r - 1 : OFF + r + 1] = nv;
     }

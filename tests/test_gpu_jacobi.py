@@ -50,14 +50,18 @@ def residual_gpu(d_u):
 
 
 def residual_sq_bound(u: np.ndarray):
-    """(exact sum of r^2 over u in FP64, bound on |gpu sum - exact sum|)."""
+    """(exact sum of r^2 over u in FP64, bound on |gpu sum - exact sum|).
+    The GPU forms r in FP32 (|r_gpu - r| <= e) and rounds r_gpu^2 to FP32
+    (relative error <= u, on r_gpu^2 <= (|r| + e)^2), then sums the rounded
+    squares to about 2^-44 of the total."""
     d = u.astype(np.float64)
     up, dn, lf, rt = d[:-2, 1:-1], d[2:, 1:-1], d[1:-1, :-2], d[1:-1, 2:]
     r = 4 * d[1:-1, 1:-1] - up - dn - lf - rt
     m = np.abs(up) + np.abs(dn) + np.abs(lf) + np.abs(rt)
     e = (2 * U32 + U32 ** 2) * (1 + U32) * m + U32 * np.abs(r)
     s = float(np.sum(r * r))
-    return s, float(np.sum(e * (2 * np.abs(r) + e))) + 2.0 ** -40 * s + 1e-300
+    sq = e * (2 * np.abs(r) + e) + U32 * (np.abs(r) + e) ** 2
+    return s, float(np.sum(sq)) + 2.0 ** -40 * s + 1e-300
 
 
 def check_residual(res_gpu, u_gpu_host):
