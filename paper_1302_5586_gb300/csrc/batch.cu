@@ -14,7 +14,8 @@
 // kernel, so every batched pixel is the same bits as pencil_conv2d_ex on that
 // image alone.  One kernel per side and tile variant keeps each kernel's code
 // small (one tile body) and gives it its own register budget and
-// shared-memory slot size, so small filters run more CTAs per SM.  Each side has one or two staging slots (two: the copies of a
+// shared-memory slot size, so small filters run more CTAs per SM.  Each side
+// of a persistent variant has one or two staging slots (two: the copies of a
 // CTA's next tile run while the current one is computed), chosen per side by
 // measurement, as is its CTA count per SM.  Kernels read the tile counts
 // from the device headers, so the graph captured for a set of sides serves
@@ -128,10 +129,9 @@ template <typename T, int K, int V>
 __device__ __forceinline__ void issue_tile(const BatchImage &d, int y0, int x0, float *slot) {
     using Cfg = BCfg<K, V>;
     stage_filter_async<K, K, Cfg::KWP, Cfg::NT>(d.k, slot);
-    stage_issue<T, Cfg::SH, Cfg::SW, Cfg::NT, false, badapt(K, sizeof(T))>(static_cast<const T *>(d.in), d.h, d.w,
-                                                                y0 - Cfg::AH, x0 - Cfg::P, d.vec_ok,
-                                                                slot + Slot<K, V>::KF,
-                                                                reinterpret_cast<T *>(slot + Slot<K, V>::f16_off(sizeof(T))));
+    stage_issue<T, Cfg::SH, Cfg::SW, Cfg::NT, false, badapt(K, sizeof(T))>(
+        static_cast<const T *>(d.in), d.h, d.w, y0 - Cfg::AH, x0 - Cfg::P, d.vec_ok, slot + Slot<K, V>::KF,
+        reinterpret_cast<T *>(slot + Slot<K, V>::f16_off(sizeof(T))));
 }
 
 // Widen (binary16, unless read directly) and compute one staged tile.
@@ -140,8 +140,8 @@ __device__ __forceinline__ void compute_tile(const BatchImage &d, int y0, int x0
     using Cfg = BCfg<K, V>;
     const T *s16 = reinterpret_cast<const T *>(slot + Slot<K, V>::f16_off(sizeof(T)));
     if constexpr (bhalfw(K, sizeof(T))) {
-        direct_compute<T, K, K, btx(K), bty(K, V), brows(K, V), bg(K), T, badapt(K, sizeof(T))>(s16, slot, static_cast<T *>(d.out),
-                                                                                     d.h, d.w, d.vec_ok, y0, x0);
+        direct_compute<T, K, K, btx(K), bty(K, V), brows(K, V), bg(K), T, badapt(K, sizeof(T))>(
+            s16, slot, static_cast<T *>(d.out), d.h, d.w, d.vec_ok, y0, x0);
     } else {
         stage_widen<T, Cfg::SH, Cfg::SW, Cfg::NT>(slot + Slot<K, V>::KF, s16);
         direct_compute<T, K, K, btx(K), bty(K, V), brows(K, V), bg(K), float, badapt(K, sizeof(T))>(
